@@ -1,0 +1,439 @@
+"""Benchmark of the HLBM mean-flow adjoint hot path on B300.
+
+One step = the whole hot path over one synthetic case (default: the D2Q9
+unsteady Karman case, 1100x410, Re 100, FP32 populations): porosity upload,
+primal warm-up, primal averaging window with the tracking averages of f,
+J, dJ/df and dJ/dd, then for the drag (J_FFA) and the dissipation (J_DISS)
+objectives: linearisation, mean-flow adjoint to tolerance and gradient.
+
+Prints one JSON line (see the contract in the repository documentation):
+value = whole-job lattice updates per second (primal steps + adjoint
+iterations, x cells) in MLUPS, measured with CUDA events on the device with
+inputs resident; e2e = the same metric through the C ABI with host buffers
+and the host<->device copies inside the timed region; roofline of the
+dominant kernel against the measured HBM copy bandwidth; cpu_baseline = the
+FP64 oracle on a bounded sample of the same workload.
+
+``--impl reference`` times the oracle itself (the only reference there is),
+on the host cores, on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+if "--impl" in sys.argv and "reference" in sys.argv:
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import make_workload  # noqa: E402
+
+L2_BYTES = 126 * 2 ** 20
+CS2 = 1.0 / 3.0
+
+
+def tau_of(wl):
+    # nu = u0 L / Re, tau = nu / c_s^2 + 1/2 (viscosity-relaxation relation)
+    return (wl.u0 * wl.L / wl.Re) / CS2 + 0.5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="karman2d_re100")
+    ap.add_argument("--primal-steps", type=int, default=None,
+                    help="override the workload's primal step count (testing only)")
+    ap.add_argument("--avg-window", type=int, default=None)
+    ap.add_argument("--adjoint-tol", type=float, default=1e-6)
+    ap.add_argument("--adjoint-max-iter", type=int, default=20000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def storage_code(H, wl):
+    return {"fp64": H.FP64, "fp32": H.FP32, "fp16dev": H.FP16DEV, "bf16dev": H.BF16DEV}[wl.storage]
+
+
+def job_shape(wl, args):
+    steps = args.primal_steps or wl.steps
+    W = args.avg_window if args.avg_window is not None else min(wl.avg_window, steps)
+    return steps, W
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per lattice update
+# ---------------------------------------------------------------------------
+
+def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False):
+    q = wl.q
+    nx, ny, nz = wl.dims
+    N = nx * ny * nz
+    plain = 2 * q * storage_bytes + real_bytes
+    r = wl.regions
+    ffa_cells = (r.ffa_y[1] - r.ffa_y[0]) * (r.ffa_z[1] - r.ffa_z[0])
+    b = r.diss_box
+    diss_cells = (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
+    les = wl.Cs > 0
+    acc = plain + 2 * q * 8 + (16 if les else 0)
+    acc += (ffa_cells * 2 * q * 8 + diss_cells * (2 * q * 8 + 16)) / N
+    D = 2 if q == 9 else 3
+    rec = q if exact_rec else D + 2
+    adj_ffa = (2 * q + rec + 1) * real_bytes + ffa_cells * q * real_bytes / N
+    adj_diss = (2 * q + rec + 1) * real_bytes + diss_cells * q * real_bytes / N
+    return dict(plain=plain, acc=acc, adj_ffa=adj_ffa, adj_diss=adj_diss)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, flags in rows for k, v in enumerate(flags)
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_2606_31707_b300 import Solver
+    from paper_2606_31707_b300 import hlbm as H
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    wl = make_workload(args.workload, seed=rank)
+    steps, W = job_shape(wl, args)
+    n_warm = steps - W
+    stream = torch.cuda.Stream(device=dev)
+    s = Solver(wl.q, wl.dims, tau_of(wl), wl.Cs, storage=storage_code(H, wl), u_in=wl.u0,
+               regions=wl.regions, stream=stream)
+    N = wl.cells
+    D = 2 if wl.q == 9 else 3
+    d_dev = torch.from_numpy(np.ascontiguousarray(wl.porosity.ravel())).to(dev)
+    up = wl.u_perturb if wl.u_perturb is not None else np.zeros((3,) + wl.porosity.shape)
+    u0 = up.copy()
+    u0[0] += wl.u0
+    u_host = np.ascontiguousarray(u0[:D].reshape(D, -1))
+    u_dev = torch.from_numpy(u_host).to(dev)
+    b = wl.regions.design_box
+    gvol = (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
+    g_dev = torch.empty((2, gvol), dtype=torch.float64, device=dev)
+    g_host = np.empty((2, gvol))
+    flush = torch.empty(int(2 * L2_BYTES // 4), dtype=torch.float32, device=dev)
+    objectives = (H.OBJ_DRAG_FFA, H.OBJ_DISSIPATION)
+
+    phase = dict(plain_ms=0.0, plain_launch=0, acc_ms=0.0, acc_launch=0, adj_ms=[0.0, 0.0],
+                 adj_launch=[0, 0], adj_iters=[0, 0])
+
+    def one_step(host: bool, record: bool):
+        if host:
+            s.set_porosity(wl.porosity.ravel())
+            H.hlbm_init_equilibrium(s.ctx, None, u_host)
+        else:
+            s.set_porosity(d_dev)
+            H.hlbm_init_equilibrium(s.ctx, None, u_dev)
+        lups = 0
+        if n_warm > 0:
+            s.run_primal(n_warm, 0)
+            st = s.stats()
+            if record:
+                phase["plain_ms"] += st.primal_ms
+                phase["plain_launch"] += st.primal_launches
+        s.run_primal(W, W)
+        st = s.stats()
+        if record:
+            phase["acc_ms"] += st.primal_ms
+            phase["acc_launch"] += st.primal_launches
+        lups += steps * N
+        Js = []
+        for k, o in enumerate(objectives):
+            Js.append(s.objective(o))
+            _, it, res = s.solve_adjoint(o, H.ADJ_EXACT, args.adjoint_tol, args.adjoint_max_iter)
+            st = s.stats()
+            if record:
+                phase["adj_ms"][k] += st.adjoint_ms
+                phase["adj_launch"][k] += st.adjoint_launches
+                phase["adj_iters"][k] += it
+            lups += it * N
+            if host:
+                H.hlbm_gradient(s.ctx, g_host[k])
+            else:
+                H.hlbm_gradient(s.ctx, g_dev[k])
+        return lups, Js
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(host: bool):
+        for _ in range(args.warmup):
+            one_step(host, False)
+        phase.update(plain_ms=0.0, plain_launch=0, acc_ms=0.0, acc_launch=0,
+                     adj_ms=[0.0, 0.0], adj_launch=[0, 0], adj_iters=[0, 0])
+        k0 = s.stats().kernels_total
+        total_lups = 0
+        ms = 0.0
+        barrier()
+        for _ in range(args.steps):
+            flush.zero_()                       # L2 flush between timed steps
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            e0.record(stream)
+            lups, Js = one_step(host, True)
+            e1.record(stream)
+            e1.synchronize()
+            wall = (time.perf_counter() - t0) * 1e3
+            gpu = e0.elapsed_time(e1)
+            ms += wall if host else gpu
+            total_lups += lups
+        barrier()
+        launches = s.stats().kernels_total - k0
+        return total_lups, ms, launches, Js
+
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    lups, ms, launches, Js = timed(False)
+    clocks = sampler.stop()
+    phase_dev = {k: (list(v) if isinstance(v, list) else v) for k, v in phase.items()}
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * lups / (ms * 1e-3) / 1e6
+    e2e = None
+    if not args.no_e2e:
+        lups_h, ms_h, _, _ = timed(True)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms_h], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_h = float(t.item())
+        e2e = {"value": world * lups_h / (ms_h * 1e-3) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": int(N * 8 + D * N * 8),
+               "d2h_bytes_per_step": int(2 * gvol * 8 + 2 * 8)}
+    s.close()
+    return dict(wl=wl, steps=steps, W=W, value=value, ms=ms, lups=lups, e2e=e2e,
+                launches=launches, phase=phase_dev, clocks=clocks, Js=Js)
+
+
+def roofline_of(res, args, H_storage_bytes, real_bytes):
+    wl = res["wl"]
+    N = wl.cells
+    bm = bytes_model(wl, H_storage_bytes, real_bytes)
+    ph = res["phase"]
+    cand = []
+    if ph["plain_launch"]:
+        cand.append(("primal_step_plain", ph["plain_ms"], ph["plain_launch"], bm["plain"]))
+    if ph["acc_launch"]:
+        cand.append(("primal_step_accumulate", ph["acc_ms"], ph["acc_launch"], bm["acc"]))
+    for k, key in enumerate(("adj_ffa", "adj_diss")):
+        if ph["adj_launch"][k]:
+            cand.append((f"adjoint_step_{key[4:]}", ph["adj_ms"][k], ph["adj_launch"][k], bm[key]))
+    name, ms, launches, bpl = max(cand, key=lambda c: c[1])
+    per_launch_s = ms * 1e-3 / launches
+    achieved = bpl * N / per_launch_s / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6400.0)
+    share = {c[0]: c[1] for c in cand}
+    tot = sum(share.values())
+    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "bytes_per_lup": round(bpl, 2), "launch_us": round(per_launch_s * 1e6, 3),
+            "time_share": {k: round(v / tot, 4) for k, v in share.items()},
+            "phase_mlups": {c[0]: round(N * c[2] / (c[1] * 1e-3) / 1e6, 1) for c in cand}}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on a bounded sample (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(wl, steps, W, adj_iters, n_plain=10, n_acc=2, n_adj=20):
+    """Time the oracle on a bounded sample of the workload and extrapolate the
+    whole job's LUP mix; returns (MLUPS, seconds spent, description)."""
+    from threadpoolctl import threadpool_limits
+
+    from oracle import adjoint as oadj
+    from oracle import hlbm as ohlbm
+    from oracle import meanflow as omf
+
+    t_start = time.perf_counter()
+    with threadpool_limits(1):
+        P = ohlbm.Params(wl.q, wl.dims, tau0=ohlbm.tau_from_reynolds(wl.u0, wl.L, wl.Re),
+                         Cs=wl.Cs, u_in=wl.u0)
+        f = ohlbm.initial_state(P, wl.u_perturb)
+        d = wl.porosity
+        t = time.perf_counter()
+        for _ in range(n_plain):
+            f = ohlbm.step(f, d, P)
+        t_plain = (time.perf_counter() - t) / n_plain
+        t = time.perf_counter()
+        out = omf.run_primal(f, d, P, n_acc, n_acc, wl.regions, 3)
+        t_acc = (time.perf_counter() - t) / n_acc
+        t = time.perf_counter()
+        lin = oadj.Linearisation(out["fbar"], d, P, oadj.EXACT, None, out["tau_t_bar"])
+        t_lin = time.perf_counter() - t
+        g = out[("gbar", 2)]
+        t = time.perf_counter()
+        oadj.solve_adjoint(lin, g, tol=0.0, max_iter=n_adj)
+        t_adj = (time.perf_counter() - t) / n_adj
+    spent = time.perf_counter() - t_start
+    N = wl.cells
+    job_s = (steps - W) * t_plain + W * t_acc + 2 * t_lin + sum(adj_iters) * t_adj
+    lups = N * (steps + sum(adj_iters))
+    desc = (f"full {wl.dims[0]}x{wl.dims[1]}x{wl.dims[2]} grid: {n_plain} plain steps "
+            f"({t_plain:.3f} s each), {n_acc} averaging steps ({t_acc:.3f} s), one "
+            f"linearisation ({t_lin:.2f} s), {n_adj} adjoint iterations ({t_adj:.3f} s); "
+            f"extrapolated to {steps} primal steps ({W} averaging) + {sum(adj_iters)} adjoint "
+            f"iterations + 2 linearisations")
+    return lups / job_s / 1e6, spent, desc
+
+
+def run_reference(args):
+    wl = make_workload(args.workload)
+    steps, W = job_shape(wl, args)
+    adj = [args.adjoint_max_iter, args.adjoint_max_iter]
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v, spent, desc = oracle_sample(wl, steps, W, adj, n_plain=4, n_acc=1, n_adj=8)
+        if k >= args.warmup:
+            vals.append((v, spent))
+    value = statistics.median(v for v, _ in vals)
+    ms = statistics.median(sp for _, sp in vals) * 1e3
+    line = {"impl": "reference", "metric": "primal/adjoint MLUPS (whole job)", "value": value,
+            "unit": "MLUPS", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "grid": list(wl.dims), "lattice": f"D{2 if wl.q == 9 else 3}Q{wl.q}",
+                       "primal_steps": steps, "avg_window": W,
+                       "adjoint_iters_assumed": adj},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank != 0:
+        return
+    wl = res["wl"]
+    sb = {"fp64": 8, "fp32": 4, "fp16dev": 2, "bf16dev": 2}[wl.storage]
+    rb = 8 if wl.storage == "fp64" else 4
+    roof = roofline_of(res, args, sb, rb)
+    ph = res["phase"]
+    it_per_step = [ph["adj_iters"][k] / max(1, args.steps) for k in range(2)]
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, spent, desc = oracle_sample(wl, res["steps"], res["W"], it_per_step)
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": round(spent, 1)}
+    line = {
+        "metric": "primal/adjoint MLUPS (whole job) and % HBM roofline",
+        "value": res["value"], "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if rb == 4 else "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "grid": list(wl.dims),
+                   "lattice": f"D{2 if wl.q == 9 else 3}Q{wl.q}", "storage": wl.storage,
+                   "Re": wl.Re, "u0": wl.u0, "primal_steps": res["steps"],
+                   "avg_window": res["W"], "objectives": ["drag_ffa", "dissipation"],
+                   "adjoint": {"mode": "exact", "tol": args.adjoint_tol,
+                               "max_iter": args.adjoint_max_iter,
+                               "iters_per_step": it_per_step},
+                   "l2": "flushed between timed steps (252 MB write)",
+                   "parallelism": f"replicas{args.gpus}"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": res["e2e"],
+        "gpu_launches": res["launches"], "clocks": res["clocks"],
+        "gradients_per_s": 2 * args.steps / (res["ms"] * 1e-3),
+        "J": {"drag_ffa": res["Js"][0], "dissipation": res["Js"][1]},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

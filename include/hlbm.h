@@ -1,0 +1,210 @@
+/*
+ * hlbm.h -- C ABI of the B300 (sm_103a) HLBM mean-flow adjoint hot path.
+ *
+ * The library computes, on one GPU, the three steps of the paper's
+ * Algorithm 1 (Ito et al., "Mean-Flow Adjoint Sensitivity Analysis of
+ * Unsteady Flow Around Porous Cylinders Using a Homogenized Lattice
+ * Boltzmann Method"):
+ *   1. the primal homogenized LBM (Sec. 2.1, Eq. hlbm with the porous
+ *      equilibrium; Smagorinsky tau_eff of Sec. 2.2) with on-device
+ *      tracking averages (Sec. 3.3, Eq. averageObjective);
+ *   2. the steady / mean-flow adjoint LBM (Eq. adjoint_steady,
+ *      Eq. adjoint_unsteady), exact or frozen-turbulence (Sec. 5.4);
+ *   3. the gradient contraction dJ/dd (Eq. gradients_steady,
+ *      Eq. gradients_unsteady)
+ * for the far-field drag J_FFA (Sec. 4.2) and the dissipation J_DISS
+ * (Sec. 4.3).
+ *
+ * Conventions (all entry points):
+ *  - Lattice units (dx = dt = 1).  Grids are (nx, ny, nz), nz = 1 for D2Q9;
+ *    cell index = x + nx*(y + ny*z) ("canonical order").  x = 0 is an
+ *    equilibrium inflow node, x = nx-1 an outflow node; y and z are
+ *    periodic.  nx >= 4, ny >= 1, nz >= 1.
+ *  - Multi-component fields are component-major: component c of cell k is
+ *    at [c*N + k], N = nx*ny*nz.
+ *  - Every call returns a status: HLBM_OK (0), HLBM_NOT_CONVERGED (1, a
+ *    warning), or a negative error.  After an error other than HLBM_ECUDA
+ *    the context stays usable; hlbm_last_error() gives a message.
+ *  - Host pointers are only read/written during the call; no caller pointer
+ *    is retained.  Device pointers (on_device = 1) must be device memory of
+ *    the context's GPU, readable/writable by the context's stream.
+ *  - A context is not thread-safe; it issues all work on one CUDA stream
+ *    (the caller's, or its own).  Calls return after their GPU work is
+ *    complete unless stated otherwise.
+ *  - The library allocates device memory with cudaMalloc (or the caller's
+ *    allocator hooks) at create time and lazily at the first adjoint solve.
+ */
+#ifndef HLBM_H
+#define HLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hlbm_ctx hlbm_ctx;
+
+enum { HLBM_D2Q9 = 9, HLBM_D3Q19 = 19 };
+
+/* population storage (spec precision forms) */
+enum {
+  HLBM_FP64 = 0,    /* double storage and double arithmetic */
+  HLBM_FP32 = 1,    /* float storage, float arithmetic */
+  HLBM_FP16DEV = 2, /* IEEE half storage of f_i - w_i, float arithmetic */
+  HLBM_BF16DEV = 3  /* bfloat16 storage of f_i - w_i, float arithmetic */
+};
+
+/* objectives: bit mask for accumulation, single value for solve/gradient */
+enum { HLBM_OBJ_DRAG_FFA = 1, HLBM_OBJ_DISSIPATION = 2 };
+
+/* adjoint linearisation: full Jacobian or frozen turbulence (Sec. 5.4) */
+enum { HLBM_ADJ_EXACT = 0, HLBM_ADJ_FTA = 1 };
+
+/* element types of caller buffers */
+enum { HLBM_DTYPE_F64 = 0, HLBM_DTYPE_F32 = 1 };
+
+/* fields for hlbm_get_field / hlbm_set_field */
+enum {
+  HLBM_FIELD_RHO = 0,    /* get: density of the current canonical state (N) */
+  HLBM_FIELD_U = 1,      /* get: velocity u = sum xi f / rho (dim x N) */
+  HLBM_FIELD_F = 2,      /* get/set: canonical populations (q x N) */
+  HLBM_FIELD_FBAR = 3,   /* get/set: averaged populations (q x N) */
+  HLBM_FIELD_GBAR_FFA = 4,   /* get/set: averaged dJ_FFA/df (q x N) */
+  HLBM_FIELD_GBAR_DISS = 5,  /* get/set: averaged dJ_DISS/df (q x N) */
+  HLBM_FIELD_DJDD_FFA = 6,   /* get/set: averaged dJ_FFA/dd (N) */
+  HLBM_FIELD_DJDD_DISS = 7,  /* get/set: averaged dJ_DISS/dd (N) */
+  HLBM_FIELD_TAU_T = 8,      /* get/set: averaged tau_eff - tau0 (N) */
+  HLBM_FIELD_LAMBDA = 9,     /* get: mu = S^T B^T lambda (q x N), the adjoint pulled
+                                back through streaming and the boundary nodes, i.e.
+                                the vector contracted with dC/dd in the gradient */
+  HLBM_FIELD_POROSITY = 10   /* get: porosity d (N) */
+};
+
+enum {
+  HLBM_OK = 0,
+  HLBM_NOT_CONVERGED = 1, /* adjoint hit max_iter; results are the last iterate */
+  HLBM_EINVAL = -1,       /* bad argument */
+  HLBM_ENOMEM = -2,       /* device allocation failed */
+  HLBM_ESTATE = -3,       /* call out of order (e.g. adjoint before primal) */
+  HLBM_ECUDA = -4,        /* CUDA runtime error; context unusable */
+  HLBM_ENONFINITE = -5,   /* NaN/Inf or non-positive density detected */
+  HLBM_EDIVERGED = -6,    /* adjoint residual grew by > 1e6 over its minimum */
+  HLBM_ETIMEOUT = -7      /* reserved: bounded device wait expired */
+};
+
+typedef struct {
+  int storage;          /* HLBM_FP64 / FP32 / FP16DEV / BF16DEV (default FP32) */
+  double u_in;          /* inflow velocity (default 0.05) */
+  double u_solid[3];    /* solid velocity u_s blended by (1 - d) (default 0) */
+  double tau_adj;       /* adjoint relaxation time replacing tau0 in the
+                           linearised operator (Sec. 5.4); 0 = tau0 */
+  int objectives;       /* mask of objectives averaged during the window */
+  int ffa_x;            /* x index of the far-field plane Gamma_J */
+  int ffa_y0, ffa_y1;   /* y extent [y0, y1) of Gamma_J */
+  int ffa_z0, ffa_z1;   /* z extent [z0, z1) of Gamma_J */
+  int diss_box[6];      /* Omega_J: x0, x1, y0, y1, z0, z1 (half-open) */
+  int design_box[6];    /* Omega_alpha: region returned by hlbm_gradient */
+  int accum_stride;     /* sample every k-th step of the window (>= 1) */
+  int check_every;      /* adjoint residual check interval, even (>= 2) */
+  void* stream;         /* cudaStream_t to issue work on; NULL = own stream */
+  void* (*dev_alloc)(size_t bytes, void* user); /* NULL = cudaMalloc */
+  void (*dev_free)(void* ptr, void* user);      /* NULL = cudaFree */
+  void* alloc_user;
+} hlbm_options;
+
+/* Velocity set of the library's direction order: xi (q x 3 ints, may be
+ * NULL) and weights w (q doubles, may be NULL).  Returns q (9 or 19) or
+ * HLBM_EINVAL.  Population fields (HLBM_FIELD_F, FBAR, GBAR_*, LAMBDA) are
+ * indexed in this order. */
+int hlbm_velocity_set(int lattice, int* xi, double* w);
+
+/* Fill *opt with defaults for a grid of dims[3] (regions: Gamma_J at
+ * x = nx/2 over the full height, Omega_J and Omega_alpha the whole domain,
+ * both objectives, stride 1, check every 100 iterations). */
+void hlbm_default_options(hlbm_options* opt, const int dims[3]);
+
+/* Create a context: lattice HLBM_D2Q9 or HLBM_D3Q19, grid dims[3],
+ * molecular relaxation time tau > 0.5 (nu = (tau - 1/2)/3, Sec. 2.1),
+ * Smagorinsky constant Cs >= 0 (0 = plain BGK; Sec. 2.2).  The state is
+ * set to f = f^eq(1, u_in e_x) and the porosity to 1.  opt may be NULL
+ * (defaults).  On error *out is NULL. */
+int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau,
+                double Cs, const hlbm_options* opt);
+
+/* Set the lattice porosity d(x) in [0, 1] (Sec. 2.1; the control of
+ * Sec. 3.1), N values of dtype, host or device.  Values outside [0, 1]
+ * or non-finite give HLBM_EINVAL (checked on the device). */
+int hlbm_set_porosity(hlbm_ctx* ctx, const void* d, int dtype, int on_device);
+
+/* Initialise the state to f = f^eq(rho, u) with the inflow/outflow nodes
+ * applied.  rho (N) may be NULL (= 1); u (dim x N) may be NULL
+ * (= u_in e_x).  Clears averages and the step counter. */
+int hlbm_init_equilibrium(hlbm_ctx* ctx, const void* rho, const void* u,
+                          int dtype, int on_device);
+
+/* Advance `steps` time steps.  The last `avg_window` steps (1 <= avg_window
+ * <= steps; 0 = no averaging) sample the canonical state they start from
+ * every accum_stride-th step into the running averages of f, J, dJ/df,
+ * dJ/dd and tau_eff - tau0 (a new window restarts the averages).
+ * avg_window = 1 is the steady case.  Returns HLBM_ENONFINITE if the state
+ * became non-finite. */
+int hlbm_run_primal(hlbm_ctx* ctx, long steps, long avg_window);
+
+/* Time-averaged objective J_bar over the last window (HLBM_ESTATE if the
+ * objective was not in the accumulation mask or no window was run). */
+int hlbm_objective(hlbm_ctx* ctx, int objective, double* J_out);
+
+/* Solve the adjoint lambda = A^T lambda + g_bar, A the step Jacobian at
+ * the averaged state (Eq. adjoint_unsteady; Eq. adjoint_steady for window
+ * 1), from lambda = 0, until ||lambda^{k+1} - lambda^k||_2 / ||g_bar||_2
+ * <= tol (checked every check_every iterations) or max_iter iterations.
+ * mode is HLBM_ADJ_EXACT or HLBM_ADJ_FTA.  iters_out / residual_out may
+ * be NULL.  Returns HLBM_NOT_CONVERGED at max_iter, HLBM_EDIVERGED or
+ * HLBM_ENONFINITE on blow-up. */
+int hlbm_solve_adjoint(hlbm_ctx* ctx, int objective, int mode, double tol,
+                       long max_iter, long* iters_out, double* residual_out);
+
+/* Gradient dJ/dd over the design box, x fastest (Eq. gradients_unsteady),
+ * for the objective of the last solve: dJ/dd_bar + sum_i mu_i dC_i/dd.
+ * out holds box-volume values of dtype, host or device. */
+int hlbm_gradient(hlbm_ctx* ctx, void* out, int dtype, int on_device);
+
+/* Read a field (see HLBM_FIELD_*) in canonical order into out. */
+int hlbm_get_field(hlbm_ctx* ctx, int which, void* out, int dtype, int on_device);
+
+/* Overwrite the state (HLBM_FIELD_F) or an averaged field (FBAR, GBAR_*,
+ * DJDD_*, TAU_T; the sample count becomes 1).  Used to feed the same
+ * averaged state to the adjoint that another implementation produced. */
+int hlbm_set_field(hlbm_ctx* ctx, int which, const void* data, int dtype, int on_device);
+
+/* Counters of the work done so far and the GPU time of the two hot loops,
+ * measured with CUDA events on the context's stream. */
+typedef struct {
+  long primal_steps;      /* total primal steps run */
+  long adjoint_iters;     /* adjoint iterations of the last solve */
+  double primal_ms;       /* GPU time of the last hlbm_run_primal */
+  double adjoint_ms;      /* GPU time of the last hlbm_solve_adjoint */
+  long primal_launches;   /* kernel launches of the last run_primal */
+  long adjoint_launches;  /* kernel launches of the last solve */
+  double primal_bytes_per_lup_plain;  /* algorithmic bytes of a plain step */
+  double adjoint_bytes_per_lup;       /* algorithmic bytes of an iteration */
+  long kernels_total;     /* all kernels this context launched since creation */
+} hlbm_stats;
+int hlbm_get_stats(const hlbm_ctx* ctx, hlbm_stats* out);
+
+/* Checkpoint the state, averages and step counter to a file / restore them
+ * into a context created with the same lattice, dims and storage. */
+int hlbm_save(hlbm_ctx* ctx, const char* path);
+int hlbm_load(hlbm_ctx* ctx, const char* path);
+
+/* Message of the last error on this context (never NULL). */
+const char* hlbm_last_error(const hlbm_ctx* ctx);
+
+/* Release all device memory and the own stream.  NULL is a no-op. */
+void hlbm_destroy(hlbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HLBM_H */

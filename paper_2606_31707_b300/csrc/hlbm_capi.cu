@@ -1,0 +1,928 @@
+// C ABI of the HLBM mean-flow adjoint hot path (see include/hlbm.h).
+//
+// Host-side orchestration only: argument checks, device memory, the order of
+// kernel launches that realises Algorithm 1 of Ito et al. (primal with
+// tracking averages -> linearisation -> adjoint iteration -> gradient), and
+// copies in and out.  Every arithmetic step of the method runs in the
+// kernels of hlbm_primal.cu and hlbm_adjoint.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/hlbm.h"
+#include "hlbm_internal.h"
+
+using namespace hlbm;
+
+struct hlbm_ctx {
+  int q = 9, D = 2, storage = HLBM_FP32;
+  Grid g{};
+  double tau0 = 0.6, Cs = 0, kles = 0, nu0 = 0;
+  hlbm_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  // primal state
+  void* f = nullptr;
+  void* d = nullptr;
+  int phase = 0;  // 0: natural layout, next primal kernel is even
+  long steps_done = 0;
+  // averages
+  double* fsum = nullptr;
+  double* tsum = nullptr;
+  double* gsum[2] = {nullptr, nullptr};
+  double* ddsum[2] = {nullptr, nullptr};
+  double* jblk[2] = {nullptr, nullptr};
+  long long nblk = 0;
+  long nsamples = 0;
+  int acc_mask = 0;
+  long generation = 0;  // bumps whenever the averaged state changes
+  // adjoint
+  void* lam = nullptr;
+  void* snap = nullptr;
+  void* rec = nullptr;
+  size_t rec_bytes = 0;
+  void* src = nullptr;
+  size_t src_bytes = 0;
+  double* red = nullptr;
+  long long red_n = 0;
+  int rec_mode = -1;
+  double rec_taub = 0;
+  long rec_generation = -1;
+  int last_obj = 0;
+  int last_mode = 0;
+  bool have_adjoint = false;
+  // scalars
+  unsigned* err_dev = nullptr;
+  unsigned* err_host = nullptr;
+  double* scal_dev = nullptr;
+  double* scal_host = nullptr;
+  // staging
+  double* stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  hlbm_stats stats{};
+  std::string msg;
+};
+
+namespace {
+
+// count a kernel launch of context c, then call the launcher
+#define CNT(c, fn) ((c)->stats.kernels_total++, fn)
+
+int set_err(hlbm_ctx* c, int code, const char* fmt, const char* extra = nullptr) {
+  if (c) {
+    char buf[512];
+    std::snprintf(buf, sizeof buf, fmt, extra ? extra : "");
+    c->msg = buf;
+  }
+  return code;
+}
+
+int cuda_check(hlbm_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return HLBM_OK;
+  char buf[512];
+  std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  if (c) c->msg = buf;
+  return e == cudaErrorMemoryAllocation ? HLBM_ENOMEM : HLBM_ECUDA;
+}
+
+#define HLBM_TRY(c, expr, what)                          \
+  do {                                                   \
+    int rc__ = cuda_check((c), (expr), (what));          \
+    if (rc__ != HLBM_OK) return rc__;                    \
+  } while (0)
+
+void* dalloc(hlbm_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (c->opt.dev_alloc) {
+    p = c->opt.dev_alloc(bytes, c->opt.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+void dfree(hlbm_ctx* c, void* p) {
+  if (!p) return;
+  if (c->opt.dev_free) c->opt.dev_free(p, c->opt.alloc_user);
+  else cudaFree(p);
+}
+
+size_t pop_elem_bytes(int storage) {
+  switch (storage) {
+    case HLBM_FP64: return 8;
+    case HLBM_FP32: return 4;
+    default: return 2;
+  }
+}
+bool real_is_double(const hlbm_ctx* c) { return c->storage == HLBM_FP64; }
+size_t real_bytes(const hlbm_ctx* c) { return real_is_double(c) ? 8 : 4; }
+
+int ensure_stage(hlbm_ctx* c, size_t bytes) {
+  if (c->stage_bytes >= bytes) return HLBM_OK;
+  dfree(c, c->stage);
+  c->stage = static_cast<double*>(dalloc(c, bytes));
+  c->stage_bytes = c->stage ? bytes : 0;
+  return c->stage ? HLBM_OK : set_err(c, HLBM_ENOMEM, "staging allocation failed");
+}
+
+// caller data (dtype, host/device) -> c->stage as doubles (n values)
+int stage_in(hlbm_ctx* c, const void* data, int dtype, int on_device, long long n) {
+  if (dtype != HLBM_DTYPE_F64 && dtype != HLBM_DTYPE_F32) return set_err(c, HLBM_EINVAL, "bad dtype");
+  int rc = ensure_stage(c, (size_t)n * 8 * (dtype == HLBM_DTYPE_F32 ? 2 : 1));
+  if (rc) return rc;
+  if (dtype == HLBM_DTYPE_F64) {
+    HLBM_TRY(c, cudaMemcpyAsync(c->stage, data, (size_t)n * 8,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                c->stream), "copy in");
+  } else {
+    float* tmp = reinterpret_cast<float*>(c->stage + n);
+    HLBM_TRY(c, cudaMemcpyAsync(tmp, data, (size_t)n * 4,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                c->stream), "copy in");
+    HLBM_TRY(c, CNT(c, launch_convert_f32_to_f64)(tmp, c->stage, n, c->stream), "convert");
+  }
+  return HLBM_OK;
+}
+
+// c->stage (n doubles) -> caller buffer
+int stage_out(hlbm_ctx* c, void* out, int dtype, int on_device, long long n) {
+  if (dtype == HLBM_DTYPE_F64) {
+    HLBM_TRY(c, cudaMemcpyAsync(out, c->stage, (size_t)n * 8,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream), "copy out");
+  } else if (dtype == HLBM_DTYPE_F32) {
+    int rc = ensure_stage(c, (size_t)n * 12);
+    if (rc) return rc;
+    float* tmp = reinterpret_cast<float*>(c->stage + n);
+    HLBM_TRY(c, CNT(c, launch_convert_f64_to_f32)(c->stage, tmp, n, c->stream), "convert");
+    HLBM_TRY(c, cudaMemcpyAsync(out, tmp, (size_t)n * 4,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream), "copy out");
+  } else {
+    return set_err(c, HLBM_EINVAL, "bad dtype");
+  }
+  HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+  return HLBM_OK;
+}
+
+int check_box(const hlbm_ctx* c, const int b[6]) {
+  return b[0] >= 0 && b[1] <= c->g.nx && b[0] < b[1] && b[2] >= 0 && b[3] <= c->g.ny &&
+         b[2] < b[3] && b[4] >= 0 && b[5] <= c->g.nz && b[4] < b[5];
+}
+
+void objective_box(const hlbm_ctx* c, int obj, int box[6]) {
+  if (obj == HLBM_OBJ_DRAG_FFA) {
+    box[0] = c->opt.ffa_x; box[1] = c->opt.ffa_x + 1;
+    box[2] = c->opt.ffa_y0; box[3] = c->opt.ffa_y1;
+    box[4] = c->opt.ffa_z0; box[5] = c->opt.ffa_z1;
+  } else {
+    std::memcpy(box, c->opt.diss_box, sizeof(int) * 6);
+  }
+}
+
+int obj_slot(int obj) { return obj == HLBM_OBJ_DRAG_FFA ? 0 : (obj == HLBM_OBJ_DISSIPATION ? 1 : -1); }
+
+int ensure_averages(hlbm_ctx* c, int mask) {
+  const long long N = c->g.N;
+  const size_t qN = (size_t)c->q * N * 8;
+  if (!c->fsum && !(c->fsum = (double*)dalloc(c, qN))) return set_err(c, HLBM_ENOMEM, "fsum");
+  if (!c->tsum && !(c->tsum = (double*)dalloc(c, (size_t)N * 8))) return set_err(c, HLBM_ENOMEM, "tsum");
+  for (int o = 0; o < 2; ++o) {
+    if (!(mask & (1 << o))) continue;
+    if (!c->gsum[o] && !(c->gsum[o] = (double*)dalloc(c, qN))) return set_err(c, HLBM_ENOMEM, "gsum");
+    if (!c->ddsum[o] && !(c->ddsum[o] = (double*)dalloc(c, (size_t)N * 8))) return set_err(c, HLBM_ENOMEM, "ddsum");
+    if (!c->jblk[o] && !(c->jblk[o] = (double*)dalloc(c, (size_t)c->nblk * 8))) return set_err(c, HLBM_ENOMEM, "jblk");
+  }
+  return HLBM_OK;
+}
+
+int reset_averages(hlbm_ctx* c, int mask) {
+  int rc = ensure_averages(c, mask);
+  if (rc) return rc;
+  const long long N = c->g.N;
+  HLBM_TRY(c, cudaMemsetAsync(c->fsum, 0, (size_t)c->q * N * 8, c->stream), "memset");
+  HLBM_TRY(c, cudaMemsetAsync(c->tsum, 0, (size_t)N * 8, c->stream), "memset");
+  for (int o = 0; o < 2; ++o) {
+    if (!(mask & (1 << o))) continue;
+    HLBM_TRY(c, cudaMemsetAsync(c->gsum[o], 0, (size_t)c->q * N * 8, c->stream), "memset");
+    HLBM_TRY(c, cudaMemsetAsync(c->ddsum[o], 0, (size_t)N * 8, c->stream), "memset");
+    HLBM_TRY(c, cudaMemsetAsync(c->jblk[o], 0, (size_t)c->nblk * 8, c->stream), "memset");
+  }
+  c->nsamples = 0;
+  c->acc_mask = mask;
+  c->generation++;
+  return HLBM_OK;
+}
+
+int read_err(hlbm_ctx* c, unsigned* out) {
+  HLBM_TRY(c, cudaMemcpyAsync(c->err_host, c->err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                              c->stream), "err readback");
+  HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+  *out = *c->err_host;
+  HLBM_TRY(c, cudaMemsetAsync(c->err_dev, 0, sizeof(unsigned), c->stream), "memset");
+  return HLBM_OK;
+}
+
+PrimalArgs primal_args(hlbm_ctx* c) {
+  PrimalArgs a{};
+  a.f = c->f;
+  a.d = c->d;
+  a.g = c->g;
+  a.tau0 = c->tau0;
+  a.kles = c->kles;
+  a.u_in = c->opt.u_in;
+  for (int k = 0; k < 3; ++k) a.us[k] = c->opt.u_solid[k];
+  a.nu0 = c->nu0;
+  a.fsum = c->fsum;
+  a.tsum = c->tsum;
+  for (int o = 0; o < 2; ++o) {
+    a.gsum[o] = c->gsum[o];
+    a.ddsum[o] = c->ddsum[o];
+    a.jblk[o] = c->jblk[o];
+  }
+  a.obj_mask = c->acc_mask;
+  a.ffa[0] = c->opt.ffa_x;
+  a.ffa[1] = c->opt.ffa_y0;
+  a.ffa[2] = c->opt.ffa_y1;
+  a.ffa[3] = c->opt.ffa_z0;
+  a.ffa[4] = c->opt.ffa_z1;
+  std::memcpy(a.db, c->opt.diss_box, sizeof a.db);
+  a.err = c->err_dev;
+  return a;
+}
+
+double bytes_plain(const hlbm_ctx* c) {
+  return 2.0 * c->q * pop_elem_bytes(c->storage) + real_bytes(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hlbm_velocity_set(int lattice, int* xi, double* w) {
+  if (lattice == 9) {
+    for (int i = 0; i < 9; ++i) {
+      if (xi) { xi[3 * i] = Lat<9>::cx(i); xi[3 * i + 1] = Lat<9>::cy(i); xi[3 * i + 2] = 0; }
+      if (w) w[i] = Lat<9>::w(i);
+    }
+    return 9;
+  }
+  if (lattice == 19) {
+    for (int i = 0; i < 19; ++i) {
+      if (xi) { xi[3 * i] = Lat<19>::cx(i); xi[3 * i + 1] = Lat<19>::cy(i); xi[3 * i + 2] = Lat<19>::cz(i); }
+      if (w) w[i] = Lat<19>::w(i);
+    }
+    return 19;
+  }
+  return HLBM_EINVAL;
+}
+
+void hlbm_default_options(hlbm_options* o, const int dims[3]) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->storage = HLBM_FP32;
+  o->u_in = 0.05;
+  o->objectives = HLBM_OBJ_DRAG_FFA | HLBM_OBJ_DISSIPATION;
+  int nx = dims ? dims[0] : 1, ny = dims ? dims[1] : 1, nz = dims ? dims[2] : 1;
+  o->ffa_x = nx / 2;
+  o->ffa_y0 = 0; o->ffa_y1 = ny;
+  o->ffa_z0 = 0; o->ffa_z1 = nz;
+  int box[6] = {0, nx, 0, ny, 0, nz};
+  std::memcpy(o->diss_box, box, sizeof box);
+  std::memcpy(o->design_box, box, sizeof box);
+  o->accum_stride = 1;
+  o->check_every = 100;
+}
+
+int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau, double Cs,
+                const hlbm_options* opt) {
+  if (!out) return HLBM_EINVAL;
+  *out = nullptr;
+  if ((lattice != 9 && lattice != 19) || !dims) return HLBM_EINVAL;
+  if (dims[0] < 4 || dims[1] < 1 || dims[2] < 1) return HLBM_EINVAL;
+  if (lattice == 9 && dims[2] != 1) return HLBM_EINVAL;
+  if (dims[1] > 65535 || dims[2] > 65535) return HLBM_EINVAL;
+  if (!(tau > 0.5) || !(Cs >= 0.0) || !std::isfinite(tau) || !std::isfinite(Cs)) return HLBM_EINVAL;
+  hlbm_ctx* c = new hlbm_ctx();
+  if (opt) c->opt = *opt;
+  else hlbm_default_options(&c->opt, dims);
+  if (c->opt.storage < HLBM_FP64 || c->opt.storage > HLBM_BF16DEV) { delete c; return HLBM_EINVAL; }
+  if (c->opt.accum_stride < 1) c->opt.accum_stride = 1;
+  if (c->opt.check_every < 2) c->opt.check_every = 100;
+  if (c->opt.check_every & 1) c->opt.check_every += 1;
+  c->q = lattice;
+  c->D = lattice == 9 ? 2 : 3;
+  c->storage = c->opt.storage;
+  c->g.nx = dims[0]; c->g.ny = dims[1]; c->g.nz = dims[2];
+  c->g.N = (long long)dims[0] * dims[1] * dims[2];
+  c->g.pitch = (c->g.N + 63) / 64 * 64;
+  c->tau0 = tau;
+  c->Cs = Cs;
+  c->kles = 4.5 * std::sqrt(2.0) * Cs * Cs;
+  c->nu0 = (tau - 0.5) / 3.0;
+  c->nblk = (long long)((dims[0] + NT - 1) / NT) * dims[1] * dims[2];
+  int ffa[6] = {c->opt.ffa_x, c->opt.ffa_x + 1, c->opt.ffa_y0, c->opt.ffa_y1, c->opt.ffa_z0, c->opt.ffa_z1};
+  if (!check_box(c, ffa) || !check_box(c, c->opt.diss_box) || !check_box(c, c->opt.design_box)) {
+    delete c;
+    return HLBM_EINVAL;
+  }
+  if (cudaGetDevice(&c->device) != cudaSuccess) { cudaGetLastError(); delete c; return HLBM_ECUDA; }
+  if (c->opt.stream) {
+    c->stream = static_cast<cudaStream_t>(c->opt.stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return HLBM_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  const size_t popb = (size_t)c->q * c->g.pitch * pop_elem_bytes(c->storage);
+  c->f = dalloc(c, popb);
+  c->d = dalloc(c, (size_t)c->g.N * real_bytes(c));
+  if (!c->f || !c->d) { hlbm_destroy(c); return HLBM_ENOMEM; }
+  if (cudaMalloc(&c->err_dev, 64) != cudaSuccess || cudaMallocHost(&c->err_host, 64) != cudaSuccess ||
+      cudaMalloc(&c->scal_dev, 64) != cudaSuccess || cudaMallocHost(&c->scal_host, 64) != cudaSuccess ||
+      cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    hlbm_destroy(c);
+    return HLBM_ENOMEM;
+  }
+  cudaMemsetAsync(c->err_dev, 0, 64, c->stream);
+  // porosity 1 everywhere, uniform inflow equilibrium
+  int rc = cuda_check(c, CNT(c, launch_fill_real)(c->d, real_is_double(c), c->g.N, 1.0, c->stream), "porosity");
+  if (rc == HLBM_OK)
+    rc = cuda_check(c, CNT(c, launch_init_eq)(c->f, c->g, c->q, c->storage, nullptr, nullptr, c->opt.u_in, c->stream), "init");
+  if (rc == HLBM_OK) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "sync");
+  if (rc != HLBM_OK) { hlbm_destroy(c); return rc; }
+  c->stats.primal_bytes_per_lup_plain = bytes_plain(c);
+  *out = c;
+  return HLBM_OK;
+}
+
+int hlbm_set_porosity(hlbm_ctx* c, const void* d, int dtype, int on_device) {
+  if (!c || !d) return HLBM_EINVAL;
+  int rc = stage_in(c, d, dtype, on_device, c->g.N);
+  if (rc) return rc;
+  HLBM_TRY(c, CNT(c, launch_set_porosity)(c->d, real_is_double(c), c->stage, c->g.N, c->err_dev, c->stream), "porosity");
+  unsigned e = 0;
+  rc = read_err(c, &e);
+  if (rc) return rc;
+  c->generation++;
+  if (e & 2u) return set_err(c, HLBM_EINVAL, "porosity outside [0, 1] or not finite");
+  return HLBM_OK;
+}
+
+int hlbm_init_equilibrium(hlbm_ctx* c, const void* rho, const void* u, int dtype, int on_device) {
+  if (!c) return HLBM_EINVAL;
+  const long long N = c->g.N;
+  double* rd = nullptr;
+  double* ud = nullptr;
+  int rc;
+  if (rho || u) {
+    rc = ensure_stage(c, (size_t)N * 8 * (1 + c->D) * 2);
+    if (rc) return rc;
+  }
+  // stage layout: [rho (N)] [u (D N)] [f32 scratch]
+  if (rho) {
+    rc = stage_in(c, rho, dtype, on_device, N);
+    if (rc) return rc;
+    rd = c->stage;
+  }
+  if (u) {
+    // place u after rho in the staging buffer
+    double* dst = c->stage + N;
+    if (dtype == HLBM_DTYPE_F64) {
+      HLBM_TRY(c, cudaMemcpyAsync(dst, u, (size_t)N * c->D * 8,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  c->stream), "copy u");
+    } else if (dtype == HLBM_DTYPE_F32) {
+      float* tmp = reinterpret_cast<float*>(c->stage + N * (1 + c->D));
+      HLBM_TRY(c, cudaMemcpyAsync(tmp, u, (size_t)N * c->D * 4,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  c->stream), "copy u");
+      HLBM_TRY(c, CNT(c, launch_convert_f32_to_f64)(tmp, dst, N * c->D, c->stream), "convert");
+    } else {
+      return set_err(c, HLBM_EINVAL, "bad dtype");
+    }
+    ud = dst;
+  }
+  HLBM_TRY(c, CNT(c, launch_init_eq)(c->f, c->g, c->q, c->storage, rd, ud, c->opt.u_in, c->stream), "init");
+  HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+  c->phase = 0;
+  c->steps_done = 0;
+  c->nsamples = 0;
+  c->acc_mask = 0;
+  c->generation++;
+  c->have_adjoint = false;
+  return HLBM_OK;
+}
+
+int hlbm_run_primal(hlbm_ctx* c, long steps, long W) {
+  if (!c) return HLBM_EINVAL;
+  if (steps < 0 || W < 0 || W > steps) return set_err(c, HLBM_EINVAL, "need 0 <= avg_window <= steps");
+  int rc;
+  const int mask = c->opt.objectives & 3;
+  if (W > 0) {
+    rc = reset_averages(c, mask);
+    if (rc) return rc;
+  }
+  PrimalArgs a = primal_args(c);
+  const bool les = c->Cs > 0.0;
+  const long first = steps - W;
+  const long stride = c->opt.accum_stride;
+  HLBM_TRY(c, cudaEventRecord(c->ev0, c->stream), "event");
+  long launches = 0, samples = 0;
+  for (long n = 0; n < steps; ++n) {
+    const bool acc = W > 0 && n >= first && ((n - first) % stride) == 0;
+    cudaError_t e = CNT(c, launch_primal)(a, c->q, c->storage, c->phase == 1, les, acc, c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "primal launch");
+    c->phase ^= 1;
+    ++launches;
+    if (acc) ++samples;
+  }
+  HLBM_TRY(c, cudaEventRecord(c->ev1, c->stream), "event");
+  unsigned err = 0;
+  rc = read_err(c, &err);
+  if (rc) return rc;
+  float ms = 0;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  c->stats.primal_ms = ms;
+  c->stats.primal_launches = launches;
+  c->stats.primal_steps += steps;
+  c->steps_done += steps;
+  if (W > 0) {
+    c->nsamples = samples;
+    c->generation++;
+    c->have_adjoint = false;
+  }
+  if (err & 1u) return set_err(c, HLBM_ENONFINITE, "primal state became non-finite");
+  return HLBM_OK;
+}
+
+int hlbm_objective(hlbm_ctx* c, int obj, double* J) {
+  if (!c || !J) return HLBM_EINVAL;
+  const int o = obj_slot(obj);
+  if (o < 0) return set_err(c, HLBM_EINVAL, "unknown objective");
+  if (c->nsamples < 1 || !(c->acc_mask & obj)) return set_err(c, HLBM_ESTATE, "objective not averaged");
+  HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->jblk[o], c->nblk, c->scal_dev, c->stream), "reduce");
+  HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
+  HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+  *J = c->scal_host[0] / (double)c->nsamples;
+  return HLBM_OK;
+}
+
+static int prepare_linearisation(hlbm_ctx* c, int mode) {
+  const bool exact_les = (mode == HLBM_ADJ_EXACT) && c->Cs > 0.0;
+  const double tau_b = c->opt.tau_adj > 0.0 ? c->opt.tau_adj : c->tau0;
+  const int want = exact_les ? 1 : 0;
+  const int rec_mode_key = exact_les ? 1 : (mode == HLBM_ADJ_FTA && c->Cs > 0.0 ? 2 : 0);
+  if (c->rec && c->rec_mode == rec_mode_key && c->rec_taub == tau_b && c->rec_generation == c->generation)
+    return HLBM_OK;
+  const int planes = want ? c->q : c->D + 2;
+  const size_t bytes = (size_t)planes * c->g.N * real_bytes(c);
+  if (c->rec_bytes < bytes) {
+    dfree(c, c->rec);
+    c->rec = dalloc(c, bytes);
+    c->rec_bytes = c->rec ? bytes : 0;
+    if (!c->rec) return set_err(c, HLBM_ENOMEM, "record");
+  }
+  PrepArgs p{};
+  p.fsum = c->fsum;
+  p.tsum = (mode == HLBM_ADJ_FTA && c->Cs > 0.0) ? c->tsum : nullptr;
+  p.inv_n = 1.0 / (double)c->nsamples;
+  p.rec = c->rec;
+  p.rec_pitch = c->g.N;
+  p.g = c->g;
+  p.tau_b = tau_b;
+  p.exact = want;
+  HLBM_TRY(c, CNT(c, launch_prep)(p, c->q, real_is_double(c), c->stream), "prep");
+  c->rec_mode = rec_mode_key;
+  c->rec_taub = tau_b;
+  c->rec_generation = c->generation;
+  return HLBM_OK;
+}
+
+static AdjointArgs adjoint_args(hlbm_ctx* c, int mode, const int sb[6]) {
+  AdjointArgs a{};
+  a.lam = c->lam;
+  a.g = c->g;
+  a.d = c->d;
+  a.rec = c->rec;
+  a.rec_pitch = c->g.N;
+  a.tau_b = c->rec_taub;
+  a.kles = c->kles;
+  for (int k = 0; k < 3; ++k) a.us[k] = c->opt.u_solid[k];
+  a.src = c->src;
+  std::memcpy(a.sb, sb, sizeof a.sb);
+  a.src_pitch = (long long)(sb[1] - sb[0]) * (sb[3] - sb[2]) * (sb[5] - sb[4]);
+  a.snap = c->snap;
+  a.red = c->red;
+  (void)mode;
+  return a;
+}
+
+int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter, long* iters_out,
+                       double* res_out) {
+  if (!c) return HLBM_EINVAL;
+  const int o = obj_slot(obj);
+  if (o < 0 || (mode != HLBM_ADJ_EXACT && mode != HLBM_ADJ_FTA) || !(tol >= 0) || max_iter < 2)
+    return set_err(c, HLBM_EINVAL, "bad objective, mode, tol or max_iter");
+  if (c->nsamples < 1 || !(c->acc_mask & obj)) return set_err(c, HLBM_ESTATE, "run the primal with this objective averaged first");
+  const bool dbl = real_is_double(c);
+  const size_t lam_bytes = (size_t)c->q * c->g.pitch * real_bytes(c);
+  if (!c->lam && !(c->lam = dalloc(c, lam_bytes))) return set_err(c, HLBM_ENOMEM, "lambda");
+  if (!c->snap && !(c->snap = dalloc(c, lam_bytes))) return set_err(c, HLBM_ENOMEM, "snapshot");
+  const long long nb_adj = adjoint_blocks(c->g);
+  int sb[6];
+  objective_box(c, obj, sb);
+  const long long vol = (long long)(sb[1] - sb[0]) * (sb[3] - sb[2]) * (sb[5] - sb[4]);
+  const long long nb_src = (long long)((sb[1] - sb[0] + NT - 1) / NT) * (sb[3] - sb[2]) * (sb[5] - sb[4]);
+  const long long need_red = nb_adj > nb_src ? nb_adj : nb_src;
+  if (c->red_n < need_red) {
+    dfree(c, c->red);
+    c->red = (double*)dalloc(c, (size_t)need_red * 8);
+    c->red_n = c->red ? need_red : 0;
+    if (!c->red) return set_err(c, HLBM_ENOMEM, "reduction buffer");
+  }
+  const size_t src_bytes = (size_t)c->q * vol * real_bytes(c);
+  if (c->src_bytes < src_bytes) {
+    dfree(c, c->src);
+    c->src = dalloc(c, src_bytes);
+    c->src_bytes = c->src ? src_bytes : 0;
+    if (!c->src) return set_err(c, HLBM_ENOMEM, "source");
+  }
+  int rc = prepare_linearisation(c, mode);
+  if (rc) return rc;
+  const bool exact = c->rec_mode == 1;
+
+  HLBM_TRY(c, cudaEventRecord(c->ev0, c->stream), "event");
+  SourceArgs sa{};
+  sa.gsum = c->gsum[o];
+  sa.inv_n = 1.0 / (double)c->nsamples;
+  sa.src = c->src;
+  std::memcpy(sa.box, sb, sizeof sa.box);
+  sa.g = c->g;
+  sa.red = c->red;
+  int nbs = 0;
+  HLBM_TRY(c, CNT(c, launch_source)(sa, c->q, dbl, &nbs, c->stream), "source");
+  HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, nbs, c->scal_dev, c->stream), "reduce");
+  HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
+  HLBM_TRY(c, cudaMemsetAsync(c->lam, 0, lam_bytes, c->stream), "memset");
+  HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+  double gnorm = std::sqrt(c->scal_host[0]);
+  if (!(gnorm > 0.0)) gnorm = 1.0;
+
+  AdjointArgs a = adjoint_args(c, mode, sb);
+  const long m = c->opt.check_every;
+  long k = 0, launches = 0;
+  double r = INFINITY, rmin = INFINITY;
+  int status = HLBM_NOT_CONVERGED;
+  while (k < max_iter) {
+    long chunk = max_iter - k < m ? max_iter - k : m;
+    if (chunk & 1) chunk += 1;
+    if (chunk < 2) chunk = 2;
+    for (long j = 0; j < chunk; ++j) {
+      const bool odd = (j & 1) != 0;
+      const int res = j == chunk - 2 ? 1 : (j == chunk - 1 ? 2 : 0);
+      cudaError_t e = CNT(c, launch_adjoint)(a, c->q, dbl, odd, exact, res, c->stream);
+      if (e != cudaSuccess) return cuda_check(c, e, "adjoint launch");
+      ++launches;
+    }
+    k += chunk;
+    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, nb_adj, c->scal_dev, c->stream), "reduce");
+    HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
+    HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+    r = std::sqrt(c->scal_host[0]) / gnorm;
+    if (!std::isfinite(r)) { status = HLBM_ENONFINITE; break; }
+    if (r < rmin) rmin = r;
+    if (r <= tol) { status = HLBM_OK; break; }
+    if (r > 1e6 * rmin && rmin > 0) { status = HLBM_EDIVERGED; break; }
+  }
+  HLBM_TRY(c, cudaEventRecord(c->ev1, c->stream), "event");
+  HLBM_TRY(c, cudaEventSynchronize(c->ev1), "sync");
+  float ms = 0;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  c->stats.adjoint_ms = ms;
+  c->stats.adjoint_iters = k;
+  c->stats.adjoint_launches = launches;
+  {
+    const int recp = exact ? c->q : c->D + 2;
+    const double rb = (double)real_bytes(c);
+    c->stats.adjoint_bytes_per_lup = (2.0 * c->q + recp + 1) * rb;
+  }
+  if (iters_out) *iters_out = k;
+  if (res_out) *res_out = r;
+  c->last_obj = obj;
+  c->last_mode = mode;
+  c->have_adjoint = (status == HLBM_OK || status == HLBM_NOT_CONVERGED);
+  if (status == HLBM_ENONFINITE) return set_err(c, status, "adjoint became non-finite");
+  if (status == HLBM_EDIVERGED) return set_err(c, status, "adjoint residual diverged");
+  if (status == HLBM_NOT_CONVERGED) set_err(c, status, "adjoint reached max_iter");
+  return status;
+}
+
+static int run_gradient(hlbm_ctx* c, const int box[6], double* out, double* mu_out) {
+  const int o = obj_slot(c->last_obj);
+  GradArgs ga{};
+  ga.lam = c->lam;
+  ga.g = c->g;
+  ga.d = c->d;
+  ga.rec = c->rec;
+  ga.rec_pitch = c->g.N;
+  ga.tau_b = c->rec_taub;
+  ga.kles = c->kles;
+  for (int k = 0; k < 3; ++k) ga.us[k] = c->opt.u_solid[k];
+  ga.ddsum = c->ddsum[o];
+  ga.inv_n = 1.0 / (double)c->nsamples;
+  std::memcpy(ga.box, box, sizeof ga.box);
+  ga.out = out;
+  ga.mu_out = mu_out;
+  HLBM_TRY(c, CNT(c, launch_gradient)(ga, c->q, real_is_double(c), c->rec_mode == 1, c->stream), "gradient");
+  return HLBM_OK;
+}
+
+int hlbm_gradient(hlbm_ctx* c, void* out, int dtype, int on_device) {
+  if (!c || !out) return HLBM_EINVAL;
+  if (!c->have_adjoint || c->rec_generation != c->generation)
+    return set_err(c, HLBM_ESTATE, "solve the adjoint first");
+  const int* b = c->opt.design_box;
+  const long long vol = (long long)(b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]);
+  int rc = ensure_stage(c, (size_t)vol * 12);
+  if (rc) return rc;
+  rc = run_gradient(c, b, c->stage, nullptr);
+  if (rc) return rc;
+  return stage_out(c, out, dtype, on_device, vol);
+}
+
+int hlbm_get_field(hlbm_ctx* c, int which, void* out, int dtype, int on_device) {
+  if (!c || !out) return HLBM_EINVAL;
+  const long long N = c->g.N;
+  const long long qN = (long long)c->q * N;
+  long long n = 0;
+  int rc;
+  switch (which) {
+    case HLBM_FIELD_RHO:
+    case HLBM_FIELD_U:
+    case HLBM_FIELD_F: {
+      n = which == HLBM_FIELD_RHO ? N : (which == HLBM_FIELD_U ? (long long)c->D * N : qN);
+      rc = ensure_stage(c, (size_t)n * 12);
+      if (rc) return rc;
+      HLBM_TRY(c, CNT(c, launch_readout)(c->f, c->d, c->g, c->q, c->storage, c->phase == 1, c->opt.u_in,
+                                 which == HLBM_FIELD_F ? c->stage : nullptr,
+                                 which == HLBM_FIELD_RHO ? c->stage : nullptr,
+                                 which == HLBM_FIELD_U ? c->stage : nullptr, c->stream), "readout");
+      break;
+    }
+    case HLBM_FIELD_FBAR:
+    case HLBM_FIELD_GBAR_FFA:
+    case HLBM_FIELD_GBAR_DISS:
+    case HLBM_FIELD_DJDD_FFA:
+    case HLBM_FIELD_DJDD_DISS:
+    case HLBM_FIELD_TAU_T: {
+      if (c->nsamples < 1) return set_err(c, HLBM_ESTATE, "no averages");
+      const double* src = nullptr;
+      if (which == HLBM_FIELD_FBAR) { src = c->fsum; n = qN; }
+      if (which == HLBM_FIELD_GBAR_FFA) { src = c->gsum[0]; n = qN; }
+      if (which == HLBM_FIELD_GBAR_DISS) { src = c->gsum[1]; n = qN; }
+      if (which == HLBM_FIELD_DJDD_FFA) { src = c->ddsum[0]; n = N; }
+      if (which == HLBM_FIELD_DJDD_DISS) { src = c->ddsum[1]; n = N; }
+      if (which == HLBM_FIELD_TAU_T) { src = c->tsum; n = N; }
+      if (!src) return set_err(c, HLBM_ESTATE, "field not averaged");
+      rc = ensure_stage(c, (size_t)n * 12);
+      if (rc) return rc;
+      HLBM_TRY(c, cudaMemcpyAsync(c->stage, src, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream), "copy");
+      HLBM_TRY(c, CNT(c, launch_scale)(c->stage, n, 1.0 / (double)c->nsamples, c->stream), "scale");
+      break;
+    }
+    case HLBM_FIELD_LAMBDA: {
+      if (!c->have_adjoint) return set_err(c, HLBM_ESTATE, "no adjoint");
+      n = qN;
+      rc = ensure_stage(c, (size_t)(n + N) * 12);
+      if (rc) return rc;
+      int box[6] = {0, c->g.nx, 0, c->g.ny, 0, c->g.nz};
+      rc = run_gradient(c, box, c->stage + n, c->stage);
+      if (rc) return rc;
+      break;
+    }
+    case HLBM_FIELD_POROSITY: {
+      n = N;
+      rc = ensure_stage(c, (size_t)n * 12);
+      if (rc) return rc;
+      HLBM_TRY(c, CNT(c, launch_real_to_f64)(c->d, real_is_double(c), c->stage, N, c->stream), "copy");
+      break;
+    }
+    default:
+      return set_err(c, HLBM_EINVAL, "unknown field");
+  }
+  return stage_out(c, out, dtype, on_device, n);
+}
+
+int hlbm_set_field(hlbm_ctx* c, int which, const void* data, int dtype, int on_device) {
+  if (!c || !data) return HLBM_EINVAL;
+  const long long N = c->g.N;
+  const long long qN = (long long)c->q * N;
+  int rc;
+  if (which == HLBM_FIELD_F) {
+    rc = stage_in(c, data, dtype, on_device, qN);
+    if (rc) return rc;
+    HLBM_TRY(c, CNT(c, launch_set_state)(c->f, c->g, c->q, c->storage, c->stage, c->stream), "set state");
+    HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+    c->phase = 0;
+    return HLBM_OK;
+  }
+  double* dst = nullptr;
+  long long n = 0;
+  int need_mask = 0;
+  switch (which) {
+    case HLBM_FIELD_FBAR: n = qN; break;
+    case HLBM_FIELD_GBAR_FFA: n = qN; need_mask = 1; break;
+    case HLBM_FIELD_GBAR_DISS: n = qN; need_mask = 2; break;
+    case HLBM_FIELD_DJDD_FFA: n = N; need_mask = 1; break;
+    case HLBM_FIELD_DJDD_DISS: n = N; need_mask = 2; break;
+    case HLBM_FIELD_TAU_T: n = N; break;
+    default: return set_err(c, HLBM_EINVAL, "field cannot be set");
+  }
+  rc = ensure_averages(c, need_mask | c->acc_mask);
+  if (rc) return rc;
+  // a set field defines a window of one sample: rescale existing sums
+  if (c->nsamples > 1) {
+    const double s = 1.0 / (double)c->nsamples;
+    CNT(c, launch_scale)(c->fsum, qN, s, c->stream);
+    CNT(c, launch_scale)(c->tsum, N, s, c->stream);
+    for (int o = 0; o < 2; ++o) {
+      if (!(c->acc_mask & (1 << o))) continue;
+      CNT(c, launch_scale)(c->gsum[o], qN, s, c->stream);
+      CNT(c, launch_scale)(c->ddsum[o], N, s, c->stream);
+      CNT(c, launch_scale)(c->jblk[o], c->nblk, s, c->stream);
+    }
+  }
+  if (c->nsamples < 1) {
+    // fresh window: clear everything first
+    rc = reset_averages(c, need_mask | c->acc_mask);
+    if (rc) return rc;
+  }
+  if (need_mask && !(c->acc_mask & need_mask)) {
+    const int o = need_mask - 1;
+    HLBM_TRY(c, cudaMemsetAsync(c->gsum[o], 0, (size_t)qN * 8, c->stream), "memset");
+    HLBM_TRY(c, cudaMemsetAsync(c->ddsum[o], 0, (size_t)N * 8, c->stream), "memset");
+    HLBM_TRY(c, cudaMemsetAsync(c->jblk[o], 0, (size_t)c->nblk * 8, c->stream), "memset");
+    c->acc_mask |= need_mask;
+  }
+  switch (which) {
+    case HLBM_FIELD_FBAR: dst = c->fsum; break;
+    case HLBM_FIELD_GBAR_FFA: dst = c->gsum[0]; break;
+    case HLBM_FIELD_GBAR_DISS: dst = c->gsum[1]; break;
+    case HLBM_FIELD_DJDD_FFA: dst = c->ddsum[0]; break;
+    case HLBM_FIELD_DJDD_DISS: dst = c->ddsum[1]; break;
+    case HLBM_FIELD_TAU_T: dst = c->tsum; break;
+  }
+  rc = stage_in(c, data, dtype, on_device, n);
+  if (rc) return rc;
+  HLBM_TRY(c, cudaMemcpyAsync(dst, c->stage, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+  c->nsamples = 1;
+  c->generation++;
+  c->have_adjoint = false;
+  return HLBM_OK;
+}
+
+int hlbm_get_stats(const hlbm_ctx* c, hlbm_stats* out) {
+  if (!c || !out) return HLBM_EINVAL;
+  *out = c->stats;
+  return HLBM_OK;
+}
+
+// checkpoint file: header, then the raw population array and the FP64 sums
+struct CkptHeader {
+  char magic[8];
+  int q, storage, nx, ny, nz, phase, acc_mask, pad;
+  long long steps_done, nsamples;
+};
+
+int hlbm_save(hlbm_ctx* c, const char* path) {
+  if (!c || !path) return HLBM_EINVAL;
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return set_err(c, HLBM_EINVAL, "cannot open %s", path);
+  CkptHeader h{};
+  std::memcpy(h.magic, "HLBMCK1", 8);
+  h.q = c->q; h.storage = c->storage; h.nx = c->g.nx; h.ny = c->g.ny; h.nz = c->g.nz;
+  h.phase = c->phase; h.acc_mask = c->nsamples > 0 ? c->acc_mask : 0;
+  h.steps_done = c->steps_done; h.nsamples = c->nsamples;
+  std::fwrite(&h, sizeof h, 1, fp);
+  auto dump = [&](const void* dptr, size_t bytes) -> int {
+    const size_t chunk = 64u << 20;
+    std::string buf;
+    buf.resize(chunk);
+    for (size_t off = 0; off < bytes; off += chunk) {
+      size_t n = bytes - off < chunk ? bytes - off : chunk;
+      if (cudaMemcpy(&buf[0], (const char*)dptr + off, n, cudaMemcpyDeviceToHost) != cudaSuccess) return HLBM_ECUDA;
+      if (std::fwrite(buf.data(), 1, n, fp) != n) return HLBM_EINVAL;
+    }
+    return HLBM_OK;
+  };
+  cudaStreamSynchronize(c->stream);
+  int rc = dump(c->f, (size_t)c->q * c->g.pitch * pop_elem_bytes(c->storage));
+  if (!rc) rc = dump(c->d, (size_t)c->g.N * real_bytes(c));
+  if (!rc && h.nsamples > 0) {
+    rc = dump(c->fsum, (size_t)c->q * c->g.N * 8);
+    if (!rc) rc = dump(c->tsum, (size_t)c->g.N * 8);
+    for (int o = 0; o < 2 && !rc; ++o) {
+      if (!(h.acc_mask & (1 << o))) continue;
+      rc = dump(c->gsum[o], (size_t)c->q * c->g.N * 8);
+      if (!rc) rc = dump(c->ddsum[o], (size_t)c->g.N * 8);
+      if (!rc) rc = dump(c->jblk[o], (size_t)c->nblk * 8);
+    }
+  }
+  std::fclose(fp);
+  if (rc) return set_err(c, rc, "checkpoint write failed");
+  return HLBM_OK;
+}
+
+int hlbm_load(hlbm_ctx* c, const char* path) {
+  if (!c || !path) return HLBM_EINVAL;
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return set_err(c, HLBM_EINVAL, "cannot open %s", path);
+  CkptHeader h{};
+  if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "HLBMCK1", 8) != 0 ||
+      h.q != c->q || h.storage != c->storage || h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz) {
+    std::fclose(fp);
+    return set_err(c, HLBM_EINVAL, "checkpoint does not match this context");
+  }
+  auto load = [&](void* dptr, size_t bytes) -> int {
+    const size_t chunk = 64u << 20;
+    std::string buf;
+    buf.resize(chunk);
+    for (size_t off = 0; off < bytes; off += chunk) {
+      size_t n = bytes - off < chunk ? bytes - off : chunk;
+      if (std::fread(&buf[0], 1, n, fp) != n) return HLBM_EINVAL;
+      if (cudaMemcpy((char*)dptr + off, buf.data(), n, cudaMemcpyHostToDevice) != cudaSuccess) return HLBM_ECUDA;
+    }
+    return HLBM_OK;
+  };
+  cudaStreamSynchronize(c->stream);
+  int rc = load(c->f, (size_t)c->q * c->g.pitch * pop_elem_bytes(c->storage));
+  if (!rc) rc = load(c->d, (size_t)c->g.N * real_bytes(c));
+  if (!rc && h.nsamples > 0) {
+    rc = ensure_averages(c, h.acc_mask);
+    if (!rc) rc = load(c->fsum, (size_t)c->q * c->g.N * 8);
+    if (!rc) rc = load(c->tsum, (size_t)c->g.N * 8);
+    for (int o = 0; o < 2 && !rc; ++o) {
+      if (!(h.acc_mask & (1 << o))) continue;
+      rc = load(c->gsum[o], (size_t)c->q * c->g.N * 8);
+      if (!rc) rc = load(c->ddsum[o], (size_t)c->g.N * 8);
+      if (!rc) rc = load(c->jblk[o], (size_t)c->nblk * 8);
+    }
+  }
+  std::fclose(fp);
+  if (rc) return set_err(c, rc, "checkpoint read failed");
+  c->phase = h.phase;
+  c->steps_done = h.steps_done;
+  c->nsamples = h.nsamples;
+  c->acc_mask = h.acc_mask;
+  c->generation++;
+  c->have_adjoint = false;
+  return HLBM_OK;
+}
+
+const char* hlbm_last_error(const hlbm_ctx* c) {
+  if (!c) return "null context";
+  return c->msg.c_str();
+}
+
+void hlbm_destroy(hlbm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  dfree(c, c->f);
+  dfree(c, c->d);
+  dfree(c, c->fsum);
+  dfree(c, c->tsum);
+  for (int o = 0; o < 2; ++o) {
+    dfree(c, c->gsum[o]);
+    dfree(c, c->ddsum[o]);
+    dfree(c, c->jblk[o]);
+  }
+  dfree(c, c->lam);
+  dfree(c, c->snap);
+  dfree(c, c->rec);
+  dfree(c, c->src);
+  dfree(c, c->red);
+  dfree(c, c->stage);
+  if (c->err_dev) cudaFree(c->err_dev);
+  if (c->err_host) cudaFreeHost(c->err_host);
+  if (c->scal_dev) cudaFree(c->scal_dev);
+  if (c->scal_host) cudaFreeHost(c->scal_host);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

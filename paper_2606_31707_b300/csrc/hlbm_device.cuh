@@ -1,0 +1,304 @@
+// Device-side building blocks of the HLBM hot path: velocity sets, population
+// storage formats, per-cell moments / porous equilibrium / Smagorinsky
+// relaxation time, the AA-pattern addressing, and block reductions.
+//
+// Method (Ito et al., Sec. 2): BGK relaxation towards the porous equilibrium
+//   f_i^eq(rho, u~) = w_i rho (1 + 3 xi_i.u~ + 9/2 (xi_i.u~)^2 - 3/2 u~.u~),
+//   u~ = d u + (1 - d) u_s                                        (Sec. 2.1)
+// with the local relaxation time of the Smagorinsky model (Sec. 2.2)
+//   tau_eff = (nu0 + nu_t)/c_s^2 + 1/2,  nu_t = Cs^2 |S|,
+//   S = -Pi/(2 tau_eff c_s^2),  |S| = sqrt(2 S:S),  Pi = sum xi xi (f - f^eq),
+// which is a quadratic in tau_eff with the positive root
+//   tau_eff = (tau0 + sqrt(tau0^2 + 18 sqrt(2) Cs^2 |Pi|)) / 2.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hlbm {
+
+// ----------------------------------------------------------------------------
+// velocity sets.  Direction order of the library (exported through
+// hlbm_velocity_set): rest first, then opposite pairs (2k+1, 2k+2).
+// ----------------------------------------------------------------------------
+template <int Q> struct Lat;
+
+template <> struct Lat<9> {
+  static constexpr int D = 2;
+  __host__ __device__ static constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 7) ? 1 : (i == 2 || i == 6 || i == 8) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return (i == 3 || i == 5 || i == 8) ? 1 : (i == 4 || i == 6 || i == 7) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr int cz(int) { return 0; }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+  }
+};
+
+template <> struct Lat<19> {
+  static constexpr int D = 3;
+  // 1,2: +-x  3,4: +-y  5,6: +-z
+  // 7..10:  (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0)
+  // 11..14: (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
+  // 15..18: (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+  __host__ __device__ static constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+           : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+           : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+           : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+  }
+};
+
+// ----------------------------------------------------------------------------
+// population storage formats (spec precision form (1)): the arithmetic
+// type R is double for FP64 storage and float otherwise.  The 16-bit formats
+// hold the deviation f_i - w_i from the rest-state equilibrium.
+// ----------------------------------------------------------------------------
+enum StorageKind { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+
+template <int S> struct Store;
+template <> struct Store<ST_F64> {
+  using mem = double; using real = double;
+  static __device__ __forceinline__ real ld(const mem* p, double) { return *p; }
+  static __device__ __forceinline__ void st(mem* p, real v, double) { *p = v; }
+};
+template <> struct Store<ST_F32> {
+  using mem = float; using real = float;
+  static __device__ __forceinline__ real ld(const mem* p, double) { return *p; }
+  static __device__ __forceinline__ void st(mem* p, real v, double) { *p = v; }
+};
+template <> struct Store<ST_F16> {
+  using mem = __half; using real = float;
+  static __device__ __forceinline__ real ld(const mem* p, double w) {
+    return __half2float(*p) + (float)w;
+  }
+  static __device__ __forceinline__ void st(mem* p, real v, double w) {
+    *p = __float2half_rn(v - (float)w);
+  }
+};
+template <> struct Store<ST_BF16> {
+  using mem = __nv_bfloat16; using real = float;
+  static __device__ __forceinline__ real ld(const mem* p, double w) {
+    return __bfloat162float(*p) + (float)w;
+  }
+  static __device__ __forceinline__ void st(mem* p, real v, double w) {
+    *p = __float2bfloat16_rn(v - (float)w);
+  }
+};
+
+template <class R> __device__ __forceinline__ R sqrt_r(R v);
+template <> __device__ __forceinline__ double sqrt_r(double v) { return sqrt(v); }
+template <> __device__ __forceinline__ float sqrt_r(float v) { return sqrtf(v); }
+
+// ----------------------------------------------------------------------------
+// grid geometry and the AA access pattern
+//
+// One array A holds q planes of `pitch` elements.  Canonical ("natural")
+// layout: A[i][cell] = f_i(cell).  Even kernels read A[i][x] and write the
+// relaxed value of direction i to A[opp(i)][x]; odd kernels read
+// A[opp(i)][x - s xi_i] and write to A[i][x + s xi_i].  s = +1 streams
+// along xi (primal), s = -1 against it (adjoint).  After an odd kernel the
+// array is back in natural layout.  Every slot is read and written by the
+// same thread in a kernel, so the update is in place without races.
+// Targets outside 0 <= x < nx are skipped (boundary columns are recomputed
+// by their owner threads); y and z wrap periodically.
+// ----------------------------------------------------------------------------
+struct Grid {
+  int nx, ny, nz;
+  long long N;      // cells
+  long long pitch;  // plane stride (elements) of population arrays
+};
+
+__device__ __forceinline__ long long cell_of(const Grid& g, int x, int y, int z) {
+  return (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+}
+
+// neighbour (x + dx, y + dy, z + dz); returns -1 when x leaves the domain
+__device__ __forceinline__ long long nbr(const Grid& g, int x, int y, int z, int dx, int dy,
+                                         int dz) {
+  int xn = x + dx;
+  if (xn < 0 || xn >= g.nx) return -1;
+  int yn = y + dy;
+  yn = yn < 0 ? yn + g.ny : (yn >= g.ny ? yn - g.ny : yn);
+  int zn = z + dz;
+  zn = zn < 0 ? zn + g.nz : (zn >= g.nz ? zn - g.nz : zn);
+  return cell_of(g, xn, yn, zn);
+}
+
+template <int Q, int S, bool ODD, int SIGN>
+__device__ __forceinline__ void aa_load(const typename Store<S>::mem* A, const Grid& g, int x,
+                                        int y, int z, long long cell,
+                                        typename Store<S>::real (&f)[Q]) {
+  using L = Lat<Q>;
+  using St = Store<S>;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (!ODD) {
+      f[i] = St::ld(A + (long long)i * g.pitch + cell, L::w(i));
+    } else {
+      long long c = (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0)
+                        ? cell
+                        : nbr(g, x, y, z, -SIGN * L::cx(i), -SIGN * L::cy(i), -SIGN * L::cz(i));
+      f[i] = c >= 0 ? St::ld(A + (long long)L::opp(i) * g.pitch + c, L::w(L::opp(i)))
+                    : typename St::real(0);
+    }
+  }
+}
+
+template <int Q, int S, bool ODD, int SIGN>
+__device__ __forceinline__ void aa_store(typename Store<S>::mem* A, const Grid& g, int x, int y,
+                                         int z, long long cell,
+                                         const typename Store<S>::real (&f)[Q]) {
+  using L = Lat<Q>;
+  using St = Store<S>;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (!ODD) {
+      St::st(A + (long long)L::opp(i) * g.pitch + cell, f[i], L::w(L::opp(i)));
+    } else {
+      long long c = (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0)
+                        ? cell
+                        : nbr(g, x, y, z, SIGN * L::cx(i), SIGN * L::cy(i), SIGN * L::cz(i));
+      if (c >= 0) St::st(A + (long long)i * g.pitch + c, f[i], L::w(i));
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// per-cell physics
+// ----------------------------------------------------------------------------
+template <class R> struct Vec3 { R x, y, z; };
+
+template <int Q, class R>
+__device__ __forceinline__ void moments(const R (&f)[Q], R& rho, Vec3<R>& u) {
+  using L = Lat<Q>;
+  R r = 0, mx = 0, my = 0, mz = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    r += f[i];
+    if (L::cx(i)) mx += L::cx(i) > 0 ? f[i] : -f[i];
+    if (L::cy(i)) my += L::cy(i) > 0 ? f[i] : -f[i];
+    if (L::cz(i)) mz += L::cz(i) > 0 ? f[i] : -f[i];
+  }
+  rho = r;
+  R inv = R(1) / r;
+  u.x = mx * inv;
+  u.y = my * inv;
+  u.z = mz * inv;
+}
+
+template <int Q, class R>
+__device__ __forceinline__ R xi_dot(int i, const Vec3<R>& v) {
+  using L = Lat<Q>;
+  R s = 0;
+  if (L::cx(i)) s += L::cx(i) > 0 ? v.x : -v.x;
+  if (L::cy(i)) s += L::cy(i) > 0 ? v.y : -v.y;
+  if (L::cz(i)) s += L::cz(i) > 0 ? v.z : -v.z;
+  return s;
+}
+
+// f_i^eq(rho, u) (Sec. 2.1)
+template <int Q, class R>
+__device__ __forceinline__ R feq_i(int i, R rho, const Vec3<R>& u, R uu) {
+  R cu = xi_dot<Q>(i, u);
+  return R(Lat<Q>::w(i)) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+}
+
+// symmetric 3x3 tensor (xx, yy, zz, xy, xz, yz)
+template <class R> struct Sym { R xx, yy, zz, xy, xz, yz; };
+
+template <int Q, class R>
+__device__ __forceinline__ Sym<R> second_moment(const R (&g)[Q]) {
+  using L = Lat<Q>;
+  Sym<R> P{0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int a = L::cx(i), b = L::cy(i), c = L::cz(i);
+    if (a) P.xx += g[i];
+    if (b) P.yy += g[i];
+    if (c) P.zz += g[i];
+    if (a && b) P.xy += (a * b > 0) ? g[i] : -g[i];
+    if (a && c) P.xz += (a * c > 0) ? g[i] : -g[i];
+    if (b && c) P.yz += (b * c > 0) ? g[i] : -g[i];
+  }
+  return P;
+}
+
+template <class R> __device__ __forceinline__ R sym_norm2(const Sym<R>& P) {
+  return P.xx * P.xx + P.yy * P.yy + P.zz * P.zz +
+         R(2) * (P.xy * P.xy + P.xz * P.xz + P.yz * P.yz);
+}
+template <class R> __device__ __forceinline__ Vec3<R> sym_mul(const Sym<R>& P, const Vec3<R>& v) {
+  return Vec3<R>{P.xx * v.x + P.xy * v.y + P.xz * v.z, P.xy * v.x + P.yy * v.y + P.yz * v.z,
+                 P.xz * v.x + P.yz * v.y + P.zz * v.z};
+}
+template <class R> __device__ __forceinline__ R dot3(const Vec3<R>& a, const Vec3<R>& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+// xi_i . P . xi_i
+template <int Q, class R> __device__ __forceinline__ R xi_P_xi(int i, const Sym<R>& P) {
+  using L = Lat<Q>;
+  const int a = L::cx(i), b = L::cy(i), c = L::cz(i);
+  R s = 0;
+  if (a) s += P.xx;
+  if (b) s += P.yy;
+  if (c) s += P.zz;
+  if (a && b) s += (a * b > 0) ? R(2) * P.xy : -R(2) * P.xy;
+  if (a && c) s += (a * c > 0) ? R(2) * P.xz : -R(2) * P.xz;
+  if (b && c) s += (b * c > 0) ? R(2) * P.yz : -R(2) * P.yz;
+  return s;
+}
+
+// positive root of tau^2 - tb tau - kles |Pi| = 0, kles = (9 sqrt 2 / 2) Cs^2
+template <class R> __device__ __forceinline__ R tau_smagorinsky(R tb, R kles, R normPi) {
+  return R(0.5) * (tb + sqrt_r<R>(tb * tb + R(4) * kles * normPi));
+}
+
+// ----------------------------------------------------------------------------
+// reductions (FP64): warp shuffle, then shared memory across warps
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) r += sh[k];
+  }
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+__device__ __forceinline__ long long block_linear() {
+  return (long long)blockIdx.x + (long long)gridDim.x * ((long long)blockIdx.y + (long long)gridDim.y * blockIdx.z);
+}
+
+}  // namespace hlbm

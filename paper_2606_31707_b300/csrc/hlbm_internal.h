@@ -1,0 +1,122 @@
+// Internal interface between the C ABI (hlbm_capi.cu) and the kernel
+// translation units (hlbm_primal.cu, hlbm_adjoint.cu).  Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hlbm_device.cuh"
+
+namespace hlbm {
+
+constexpr int NT = 128;  // threads per block along x for all cell kernels
+
+// --------------------------------------------------------------------------
+// primal
+// --------------------------------------------------------------------------
+struct PrimalArgs {
+  void* f;            // population array (storage type), q planes of g.pitch
+  const void* d;      // porosity, real type (double for FP64 storage, else float)
+  Grid g;
+  double tau0;        // molecular relaxation time
+  double kles;        // (9 sqrt(2) / 2) Cs^2 ; 0 disables LES
+  double u_in;        // inflow velocity
+  double us[3];       // solid velocity u_s
+  double nu0;         // molecular viscosity (tau0 - 1/2)/3
+  // averaging (only read when the ACC variant runs)
+  double* fsum;       // q x N running sum of f
+  double* tsum;       // N running sum of tau_eff - tau0 (LES only)
+  double* gsum[2];    // q x N running sums of dJ/df (FFA, DISS); may be null
+  double* ddsum[2];   // N running sums of dJ/dd
+  double* jblk[2];    // per-block running sums of J
+  int obj_mask;
+  int ffa[5];         // x, y0, y1, z0, z1 of Gamma_J
+  int db[6];          // Omega_J box
+  unsigned* err;      // bit 0: non-finite or non-positive density
+};
+
+// launch one primal step kernel; storage 0..3, odd/les/acc select variants
+cudaError_t launch_primal(const PrimalArgs& a, int q, int storage, bool odd, bool les, bool acc,
+                          cudaStream_t s);
+
+// readout of the canonical state: f (q x N), rho (N), u (3 x N); any may be null
+cudaError_t launch_readout(const void* f, const void* d, const Grid& g, int q, int storage,
+                           bool odd, double u_in, double* fout, double* rho, double* u,
+                           cudaStream_t s);
+// write a canonical state (q x N doubles) in natural layout
+cudaError_t launch_set_state(void* f, const Grid& g, int q, int storage, const double* in,
+                             cudaStream_t s);
+// f = f^eq(rho, u); rho / u may be null (1, u_in e_x)
+cudaError_t launch_init_eq(void* f, const Grid& g, int q, int storage, const double* rho,
+                           const double* u, double u_in, cudaStream_t s);
+// d (real type) from doubles; sets err bit 1 when a value is outside [0, 1]
+cudaError_t launch_set_porosity(void* d, bool dbl, const double* in, long long n,
+                                unsigned* err, cudaStream_t s);
+cudaError_t launch_convert_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s);
+cudaError_t launch_convert_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s);
+cudaError_t launch_real_to_f64(const void* in, bool dbl, double* out, long long n, cudaStream_t s);
+// out = sum of v[0..n) in a fixed order (one block)
+cudaError_t launch_finalize_sum(const double* v, long long n, double* out, cudaStream_t s);
+cudaError_t launch_scale(double* v, long long n, double s_, cudaStream_t s);
+cudaError_t launch_fill_real(void* v, bool dbl, long long n, double value, cudaStream_t s);
+
+// --------------------------------------------------------------------------
+// adjoint
+// --------------------------------------------------------------------------
+struct PrepArgs {
+  const double* fsum;  // q x N
+  const double* tsum;  // N (FTA with LES) or null
+  double inv_n;        // 1 / number of samples
+  void* rec;           // real planes: BGK/FTA (rho, ux, uy[, uz], omega); EXACT: q planes of f_bar
+  long long rec_pitch;
+  Grid g;
+  double tau_b;        // tau0 or tau_adj
+  int exact;           // 1: EXACT with LES (store f_bar), 0: compact record
+};
+cudaError_t launch_prep(const PrepArgs& a, int q, bool dbl, cudaStream_t s);
+
+struct SourceArgs {
+  const double* gsum;  // q x N
+  double inv_n;
+  void* src;           // real, q planes of box volume
+  int box[6];
+  Grid g;
+  double* red;         // per-block partial sums of src^2
+};
+cudaError_t launch_source(const SourceArgs& a, int q, bool dbl, int* nblocks, cudaStream_t s);
+
+struct AdjointArgs {
+  void* lam;           // AA array of the adjoint (real), q planes of g.pitch
+  Grid g;
+  const void* d;       // porosity (real)
+  const void* rec;     // linearisation record (see PrepArgs)
+  long long rec_pitch;
+  double tau_b, kles;
+  double us[3];
+  const void* src;     // g_bar restricted to the source box (real)
+  int sb[6];
+  long long src_pitch;
+  void* snap;          // residual snapshot (real, q planes of g.pitch)
+  double* red;         // per-block partial of the residual
+};
+// res: 0 plain, 1 write the snapshot (even kernels), 2 compare (odd kernels)
+cudaError_t launch_adjoint(const AdjointArgs& a, int q, bool dbl, bool odd, bool exact, int res,
+                           cudaStream_t s);
+int adjoint_blocks(const Grid& g);
+
+struct GradArgs {
+  const void* lam;     // adjoint AA array in natural layout (next kernel even)
+  Grid g;
+  const void* d;
+  const void* rec;
+  long long rec_pitch;
+  double tau_b, kles;
+  double us[3];
+  const double* ddsum; // N, may be null
+  double inv_n;
+  int box[6];          // design box
+  double* out;         // box volume, x fastest
+  double* mu_out;      // optional q x N output of mu (whole grid when box is the domain)
+};
+cudaError_t launch_gradient(const GradArgs& a, int q, bool dbl, bool exact, cudaStream_t s);
+
+}  // namespace hlbm

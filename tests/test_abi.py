@@ -1,0 +1,60 @@
+"""The C-ABI library loads on a machine without a GPU and exports every
+entry point that include/hlbm.h declares; host-side argument checks."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hlbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hlbm_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2606_31707_b300 import hlbm as H
+    lib = H.lib()
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(H.EXPORTED)
+
+
+def test_velocity_sets_match_the_paper_lattices():
+    # D2Q9 / D3Q19 (Sec. 2.1) in the library's order: same set as the oracle's
+    from oracle.lattice import velocity_set
+    from paper_2606_31707_b300 import hlbm as H
+    for q in (9, 19):
+        xi, w = H.hlbm_velocity_set(q)
+        oxi, ow, _ = velocity_set(q)
+        got = sorted((tuple(v), round(x, 15)) for v, x in zip(xi, w))
+        ref = sorted((tuple(v), round(x, 15)) for v, x in zip(oxi, ow))
+        assert got == ref
+        # opposite pairs (2k+1, 2k+2)
+        for k in range(1, q, 2):
+            assert (xi[k] == -xi[k + 1]).all()
+
+
+def test_default_options_and_argument_checks_without_gpu():
+    from paper_2606_31707_b300 import hlbm as H
+    o = H.hlbm_default_options((200, 80, 1))
+    assert o.ffa_x == 100 and list(o.diss_box) == [0, 200, 0, 80, 0, 1]
+    assert o.accum_stride == 1 and o.check_every == 100
+    # invalid arguments are rejected before any CUDA call
+    for lattice, dims, tau in ((7, (10, 4, 1), 0.6), (9, (3, 4, 1), 0.6), (9, (10, 4, 2), 0.6),
+                               (9, (10, 4, 1), 0.5), (19, (10, 4, 4), float("nan"))):
+        with pytest.raises(H.HlbmError) as e:
+            H.hlbm_create(lattice, dims, tau, 0.0)
+        assert e.value.status == H.EINVAL
+
+
+def test_header_cites_the_paper_and_states_errors():
+    src = open(os.path.join(ROOT, "include", "hlbm.h")).read()
+    for key in ("Eq. adjoint_unsteady", "Eq. gradients_unsteady", "Sec. 4.2", "Sec. 4.3",
+                "HLBM_EINVAL", "HLBM_ESTATE", "HLBM_ENONFINITE"):
+        assert key in src

@@ -1,0 +1,223 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Element-wise comparisons on seeded synthetic inputs at sizes the oracle
+finishes in seconds, spanning several 128-cell tiles along x and a ragged
+tail.  Tolerances: FP64 storage -- primal fields 1e-12, gradients 1e-9
+relative L2; FP32 storage -- primal fields 1e-5, gradients 1e-4 relative L2
+(the benchmark spec's bounds); 16-bit deviation storage -- stated looser bounds.
+"""
+import numpy as np
+import pytest
+
+from oracle import adjoint as oadj
+from oracle import hlbm as ohlbm
+from oracle import meanflow as omf
+from oracle import objectives as oobj
+from tests.hlbm_cases import direction_perm, oracle_pipeline, rel_l2, to_lib
+from workloads import Regions, cylinder_porosity
+
+pytestmark = pytest.mark.gpu
+
+H = pytest.importorskip("paper_2606_31707_b300.hlbm")
+from paper_2606_31707_b300 import Solver  # noqa: E402
+
+
+def _case(q=9, dims=(300, 24, 1), Cs=0.0, tau=0.7, u_in=0.05, seed=0, R=4.0, sym=False):
+    P = ohlbm.Params(q, dims, tau0=tau, Cs=Cs, u_in=u_in)
+    nx, ny, nz = dims
+    d = cylinder_porosity(dims, 30.0, ny / 2.0, R, 1.5, jitter=0.0 if sym else 0.01, seed=seed)
+    regions = Regions(ffa_x=nx // 2 + 7, ffa_y=(0, ny), ffa_z=(0, nz),
+                      diss_box=(3, nx - 37, 1, ny - 2, 0, nz),
+                      design_box=(5, nx - 3, 0, ny, 0, nz))
+    return P, d, regions
+
+
+def _solver(P, regions, storage, tau_adj=0.0, check_every=100):
+    return Solver(P.q, P.dims, P.tau0, P.Cs, storage=storage, u_in=P.u_in, regions=regions,
+                  tau_adj=tau_adj, check_every=check_every)
+
+
+def _perturbed_state(P, seed=1, amp=0.01):
+    rng = np.random.default_rng(seed)
+    u = np.zeros((3,) + P.shape)
+    u[0] = P.u_in * (1 + 0.2 * rng.standard_normal(P.shape))
+    u[1] = 0.01 * rng.standard_normal(P.shape)
+    if P.q == 19:
+        u[2] = 0.01 * rng.standard_normal(P.shape)
+    rho = 1 + 0.01 * rng.standard_normal(P.shape)
+    f = ohlbm.equilibrium(rho, u, P) * (1 + amp * rng.standard_normal((P.q,) + P.shape))
+    return ohlbm.apply_boundary(f, P)
+
+
+@pytest.mark.parametrize("q,dims,Cs,storage,tol", [
+    (9, (300, 24, 1), 0.0, H.FP64, 1e-13),
+    (9, (300, 24, 1), 0.2, H.FP64, 1e-13),
+    (19, (150, 10, 6), 0.15, H.FP64, 1e-13),
+    (9, (300, 24, 1), 0.0, H.FP32, 1e-6),
+    (19, (150, 10, 6), 0.15, H.FP32, 1e-6),
+])
+@pytest.mark.parametrize("steps", [1, 2, 7])
+def test_primal_steps_match_oracle(q, dims, Cs, storage, tol, steps):
+    P, d, R = _case(q, dims, Cs)
+    f0 = _perturbed_state(P)
+    s = _solver(P, R, storage)
+    perm = direction_perm(s.xi, P)
+    s.set_porosity(d)
+    s.set_field(H.FIELD_F, to_lib(f0, perm))
+    s.run_primal(steps, 0)
+    f = f0
+    for _ in range(steps):
+        f = ohlbm.step(f, d, P)
+    got = s.field(H.FIELD_F)
+    assert rel_l2(got, to_lib(f, perm)) <= tol
+    rho, u = ohlbm.moments(f, P)
+    assert rel_l2(s.field(H.FIELD_RHO), rho) <= tol
+    assert rel_l2(s.field(H.FIELD_U), u[: s.dim]) <= tol * 10
+    s.close()
+
+
+@pytest.mark.parametrize("storage,tol", [(H.FP16DEV, 3e-3), (H.BF16DEV, 3e-2)])
+def test_primal_16bit_deviation_storage_bound(storage, tol):
+    # 16-bit storage of f_i - w_i with FP32 arithmetic: stated looser bound
+    P, d, R = _case(9, (300, 24, 1), 0.0)
+    f0 = _perturbed_state(P, amp=0.0)
+    s = _solver(P, R, storage)
+    perm = direction_perm(s.xi, P)
+    s.set_porosity(d)
+    s.set_field(H.FIELD_F, to_lib(f0, perm))
+    s.run_primal(20, 0)
+    f = f0
+    for _ in range(20):
+        f = ohlbm.step(f, d, P)
+    got = s.field(H.FIELD_F)
+    dev_ref = to_lib(f, perm) - s.w[:, None, None, None]
+    assert rel_l2(got - s.w[:, None, None, None], dev_ref) <= tol
+    s.close()
+
+
+@pytest.mark.parametrize("q,dims,Cs", [(9, (300, 24, 1), 0.0), (9, (300, 24, 1), 0.2),
+                                      (19, (150, 10, 6), 0.15)])
+def test_averages_match_oracle(q, dims, Cs):
+    P, d, R = _case(q, dims, Cs)
+    f0 = _perturbed_state(P)
+    s = Solver(P.q, P.dims, P.tau0, P.Cs, storage=H.FP64, u_in=P.u_in, regions=R, accum_stride=2)
+    perm = direction_perm(s.xi, P)
+    s.set_porosity(d)
+    s.set_field(H.FIELD_F, to_lib(f0, perm))
+    s.run_primal(12, 7)
+    out = omf.run_primal(f0, d, P, 12, 7, R, 3, stride=2)
+    assert out["nsamples"] == 4
+    assert rel_l2(s.field(H.FIELD_FBAR), to_lib(out["fbar"], perm)) <= 1e-13
+    for o, gf, df in ((oobj.FFA, H.FIELD_GBAR_FFA, H.FIELD_DJDD_FFA),
+                      (oobj.DISS, H.FIELD_GBAR_DISS, H.FIELD_DJDD_DISS)):
+        assert rel_l2(s.field(gf), to_lib(out[("gbar", o)], perm)) <= 1e-11
+        if o == oobj.DISS:
+            assert rel_l2(s.field(df), out[("dJdd_bar", o)]) <= 1e-11
+        J = s.objective(o)
+        assert abs(J - out[("Jbar", o)]) <= 1e-12 * max(1.0, abs(out[("Jbar", o)]))
+    if Cs > 0:
+        assert rel_l2(s.field(H.FIELD_TAU_T), out["tau_t_bar"]) <= 1e-11
+    s.close()
+
+
+def _steady_gpu_vs_oracle(q, dims, Cs, storage, objective, mode, tau_adj=None, steps=3000):
+    P, d, R = _case(q, dims, Cs, tau=0.8, u_in=0.04)
+    f0 = ohlbm.initial_state(P)
+    s = _solver(P, R, storage, tau_adj=tau_adj or 0.0)
+    perm = direction_perm(s.xi, P)
+    s.set_porosity(d)
+    s.run_primal(steps, 1)
+    # the oracle linearises at the same averaged state (kernel-level parity)
+    fbar_lib = s.field(H.FIELD_FBAR)
+    inv = np.argsort(perm)
+    fbar = fbar_lib[inv]
+    out = omf.run_primal(fbar, d, P, 1, 1, R, 3)
+    lin = oadj.Linearisation(fbar, d, P, mode, tau_adj, out["tau_t_bar"])
+    lam = oadj.solve_adjoint_direct(lin, out[("gbar", objective)])
+    G = oadj.gradient(lin, lam, out[("dJdd_bar", objective)])
+    st, it, res = s.solve_adjoint(objective, mode, 1e-13 if storage == H.FP64 else 1e-7, 400000)
+    Gg = s.gradient()
+    b = R.design_box
+    Gref = G[b[4]:b[5], b[2]:b[3], b[0]:b[1]]
+    mu = s.field(H.FIELD_LAMBDA)
+    s.close()
+    return Gg, Gref, mu, to_lib(lin.mu(lam), perm), st
+
+
+@pytest.mark.parametrize("objective", [oobj.FFA, oobj.DISS])
+@pytest.mark.parametrize("q,dims,Cs,mode", [
+    (9, (300, 24, 1), 0.0, oadj.EXACT),
+    (9, (300, 24, 1), 0.15, oadj.EXACT),
+    (9, (300, 24, 1), 0.15, oadj.FTA),
+    (19, (140, 10, 4), 0.1, oadj.EXACT),
+])
+def test_adjoint_gradient_fp64_matches_oracle(q, dims, Cs, mode, objective):
+    Gg, Gref, mu, mu_ref, st = _steady_gpu_vs_oracle(q, dims, Cs, H.FP64, objective, mode)
+    assert st == H.OK
+    assert rel_l2(Gg, Gref) <= 1e-9
+    assert rel_l2(mu, mu_ref) <= 1e-9
+
+
+@pytest.mark.parametrize("objective", [oobj.FFA, oobj.DISS])
+def test_adjoint_gradient_fp32_matches_oracle(objective):
+    Gg, Gref, mu, mu_ref, st = _steady_gpu_vs_oracle(9, (300, 24, 1), 0.0, H.FP32, objective,
+                                                    oadj.EXACT)
+    assert st in (H.OK, H.NOT_CONVERGED)
+    assert rel_l2(Gg, Gref) <= 1e-4
+
+
+def test_tau_adj_replaces_tau0_in_adjoint_only():
+    Gg, Gref, _, _, st = _steady_gpu_vs_oracle(9, (300, 24, 1), 0.1, H.FP64, oobj.DISS,
+                                               oadj.FTA, tau_adj=0.9)
+    assert rel_l2(Gg, Gref) <= 1e-9
+
+
+def test_full_pipeline_steady_fp64_vs_oracle_gradient_sign_and_directional_fd():
+    # Algorithm 1 end to end on both sides from the same initial state
+    P, d, R = _case(9, (160, 20, 1), 0.0, tau=0.8, u_in=0.04)
+    s = _solver(P, R, H.FP64)
+    s.set_porosity(d)
+    s.run_primal(4000, 1)
+    st, it, res = s.solve_adjoint(oobj.DISS, H.ADJ_EXACT, 1e-13, 400000)
+    Gg = s.gradient()
+    ref = oracle_pipeline(P, d, R, ohlbm.initial_state(P), 4000, 1, oobj.DISS)
+    b = R.design_box
+    assert rel_l2(Gg, ref["G"][b[4]:b[5], b[2]:b[3], b[0]:b[1]]) <= 1e-8
+    assert abs(s.objective(oobj.DISS) - ref["out"][("Jbar", oobj.DISS)]) <= 1e-10 * abs(ref["out"][("Jbar", oobj.DISS)])
+    s.close()
+
+
+def test_errors_are_reported_not_faulted():
+    P, d, R = _case(9, (64, 8, 1))
+    s = _solver(P, R, H.FP32)
+    with pytest.raises(H.HlbmError) as e:
+        s.solve_adjoint(oobj.FFA)
+    assert e.value.status == H.ESTATE
+    bad = d.copy()
+    bad[0, 0, 3] = 1.5
+    with pytest.raises(H.HlbmError) as e:
+        s.set_porosity(bad)
+    assert e.value.status == H.EINVAL
+    with pytest.raises(H.HlbmError):
+        s.gradient()
+    s.close()
+
+
+def test_checkpoint_resume_is_bitwise():
+    P, d, R = _case(9, (200, 16, 1), 0.1)
+    a = _solver(P, R, H.FP32)
+    a.set_porosity(d)
+    a.run_primal(101, 0)
+    import tempfile, os
+    path = os.path.join(tempfile.mkdtemp(), "ck.bin")
+    a.save(path)
+    a.run_primal(50, 10)
+    fa = a.field(H.FIELD_F)
+    ga = a.field(H.FIELD_GBAR_DISS)
+    b = _solver(P, R, H.FP32)
+    b.load(path)
+    b.run_primal(50, 10)
+    assert np.array_equal(b.field(H.FIELD_F), fa)
+    assert np.array_equal(b.field(H.FIELD_GBAR_DISS), ga)
+    a.close()
+    b.close()
