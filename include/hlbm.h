@@ -90,7 +90,8 @@ enum {
   HLBM_ECUDA = -4,        /* CUDA runtime error; context unusable */
   HLBM_ENONFINITE = -5,   /* NaN/Inf or non-positive density detected */
   HLBM_EDIVERGED = -6,    /* adjoint residual grew by > 1e6 over its minimum */
-  HLBM_ETIMEOUT = -7      /* reserved: bounded device wait expired */
+  HLBM_ETIMEOUT = -7,     /* reserved: bounded device wait expired */
+  HLBM_ESCRATCH = -8      /* problem needs more than a fixed scratch area holds */
 };
 
 typedef struct {
@@ -203,6 +204,41 @@ const char* hlbm_last_error(const hlbm_ctx* ctx);
 
 /* Release all device memory and the own stream.  NULL is a no-op. */
 void hlbm_destroy(hlbm_ctx* ctx);
+
+/* ---------------------------------------------------------------------
+ * Objective evaluation without allocation.  The paper has no counterpart
+ * to this entry point; it exists for callers that must not allocate device
+ * memory (a component inside a fixed memory arena or pool that may not
+ * grow, a latency-critical loop where an allocation's implicit device
+ * synchronisation is not acceptable, or a plug-in host that forbids its
+ * plug-ins to allocate).  It needs no context.
+ *
+ * Evaluates objective HLBM_OBJ_DRAG_FFA or HLBM_OBJ_DISSIPATION of the
+ * canonical population field f (q x N doubles, device, direction order of
+ * hlbm_velocity_set) with porosity d (N doubles, device) over `region`
+ * (x0, x1, y0, y1, z0, z1, half-open; for the drag a plane, x1 = x0 + 1),
+ * with the same definitions as the averages of hlbm_run_primal.  Writes J
+ * (one double, device) and, when not NULL, dJ/df (q x N, device) and dJ/dd
+ * (N, device) at the cells of the region; other cells are not written.
+ * tau, Cs, u_in and u_solid (may be NULL = 0) are as in hlbm_create.  Work
+ * is enqueued on `stream` (cudaStream_t, NULL = legacy default stream); the
+ * call returns without waiting for it.
+ *
+ * No cudaMalloc / cudaFree or other allocating call is made.  Scratch is a
+ * fixed device array of HLBM_NOALLOC_MAX_BLOCKS doubles (512 KiB per GPU,
+ * held until the process exits) shared by all calls: a region of more than
+ * HLBM_NOALLOC_MAX_BLOCKS blocks (ceil((x1-x0)/128) * (y1-y0) * (z1-z0))
+ * returns HLBM_ESCRATCH.  Calls that overlap on the GPU race on the scratch
+ * array; order them on one stream.  The first call on a device looks up
+ * the scratch address (cudaGetSymbolAddress, that device current); make it
+ * before any stream capture.  Errors: HLBM_EINVAL (bad argument),
+ * HLBM_ESCRATCH, HLBM_ECUDA.
+ * --------------------------------------------------------------------- */
+#define HLBM_NOALLOC_MAX_BLOCKS 65536
+int hlbm_objective_noalloc(int lattice, const int dims[3], double tau, double Cs, double u_in,
+                           const double u_solid[3], int objective, const int region[6],
+                           const double* f, const double* d, double* J, double* dJdf,
+                           double* dJdd, void* stream);
 
 #ifdef __cplusplus
 }

@@ -1,6 +1,7 @@
 """Build the CUDA shared library ``libhlbm.so`` in-tree for sm_103a.
 
-Usage: ``python -m paper_2606_31707_b300.build`` (or ``build()`` from Python).
+Usage: ``python paper_2606_31707_b300/build.py [--force]`` (or ``build()``;
+the package itself cannot be imported before the library exists).
 Sources are compiled in parallel with nvcc and linked into the package
 directory, next to this file.
 """
@@ -16,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libhlbm.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["hlbm_primal.cu", "hlbm_adjoint.cu", "hlbm_capi.cu"]
+SOURCES = ["hlbm_primal.cu", "hlbm_adjoint.cu", "hlbm_capi.cu", "hlbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-v"]

@@ -28,8 +28,10 @@ DTYPE_F64, DTYPE_F32 = 0, 1
  FIELD_DJDD_DISS, FIELD_TAU_T, FIELD_LAMBDA, FIELD_POROSITY) = range(11)
 OK, NOT_CONVERGED = 0, 1
 EINVAL, ENOMEM, ESTATE, ECUDA, ENONFINITE, EDIVERGED, ETIMEOUT = -1, -2, -3, -4, -5, -6, -7
+ESCRATCH = -8
+NOALLOC_MAX_BLOCKS = 65536
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "EINVAL", -2: "ENOMEM", -3: "ESTATE",
-                -4: "ECUDA", -5: "ENONFINITE", -6: "EDIVERGED", -7: "ETIMEOUT"}
+                -4: "ECUDA", -5: "ENONFINITE", -6: "EDIVERGED", -7: "ETIMEOUT", -8: "ESCRATCH"}
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -79,7 +81,7 @@ class HlbmError(RuntimeError):
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
-            f"{LIB_PATH} is missing: build it with `python -m paper_2606_31707_b300.build`")
+            f"{LIB_PATH} is missing: build it with `python paper_2606_31707_b300/build.py`")
     lib = C.CDLL(LIB_PATH)
     P = C.c_void_p
     sig = {
@@ -101,6 +103,9 @@ def _load():
         "hlbm_load": (C.c_int, [P, C.c_char_p]),
         "hlbm_last_error": (C.c_char_p, [P]),
         "hlbm_destroy": (None, [P]),
+        "hlbm_objective_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_double, C.c_double,
+                                             C.c_double, C.POINTER(C.c_double), C.c_int,
+                                             C.POINTER(C.c_int), P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -113,7 +118,7 @@ _lib = _load()
 EXPORTED = ("hlbm_velocity_set", "hlbm_default_options", "hlbm_create", "hlbm_set_porosity",
             "hlbm_init_equilibrium", "hlbm_run_primal", "hlbm_objective", "hlbm_solve_adjoint",
             "hlbm_gradient", "hlbm_get_field", "hlbm_set_field", "hlbm_get_stats", "hlbm_save",
-            "hlbm_load", "hlbm_last_error", "hlbm_destroy")
+            "hlbm_load", "hlbm_last_error", "hlbm_destroy", "hlbm_objective_noalloc")
 
 
 def lib():
@@ -269,3 +274,15 @@ def hlbm_last_error(ctx) -> str:
 
 def hlbm_destroy(ctx):
     _lib.hlbm_destroy(ctx)
+
+
+def hlbm_objective_noalloc(lattice: int, dims: Sequence[int], tau: float, Cs: float, u_in: float,
+                           objective: int, region: Sequence[int], f, d, J, dJdf=None, dJdd=None,
+                           stream: int = 0, u_solid=(0.0, 0.0, 0.0)) -> int:
+    """Objective of a device-resident state without any allocation in the
+    library (see include/hlbm.h).  f, d, J, dJdf, dJdd are CUDA float64
+    tensors; returns the status (negative on error) without raising."""
+    ptr = [C.c_void_p(t.data_ptr()) if t is not None else None for t in (f, d, J, dJdf, dJdd)]
+    return _lib.hlbm_objective_noalloc(lattice, (C.c_int * 3)(*dims), tau, Cs, u_in,
+                                       (C.c_double * 3)(*u_solid), objective,
+                                       (C.c_int * 6)(*region), *ptr, C.c_void_p(stream))
