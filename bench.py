@@ -28,9 +28,10 @@ import sys
 import tempfile
 import time
 
-if "--impl" in sys.argv and "reference" in sys.argv:
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ.setdefault(k, "1")
+# the CPU oracle (cpu_baseline and the reference arm) runs on one host thread:
+# numpy elementwise work is single-threaded and BLAS is pinned to one thread here
+for _k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_k, "1")
 
 import numpy as np
 
@@ -322,7 +323,13 @@ def roofline_of(res, args, H_storage_bytes, real_bytes):
 def oracle_sample(wl, steps, W, adj_iters, n_plain=10, n_acc=2, n_adj=20):
     """Time the oracle on a bounded sample of the workload and extrapolate the
     whole job's LUP mix; returns (MLUPS, seconds spent, description)."""
-    from threadpoolctl import threadpool_limits
+    import contextlib
+
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:  # BLAS is already pinned to one thread by the environment
+        def threadpool_limits(_n):
+            return contextlib.nullcontext()
 
     from oracle import adjoint as oadj
     from oracle import hlbm as ohlbm
