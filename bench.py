@@ -81,18 +81,25 @@ def job_shape(wl, args):
 # ---------------------------------------------------------------------------
 
 def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False):
+    """Algorithmic bytes per lattice update of each kernel (reads + writes).
+
+    Averaging step: the populations and porosity of a plain step, a
+    read-modify-write (16 B) of each FP64 running sum it updates: density and
+    momentum (1 + D), all q populations when Cs > 0, tau_eff - tau0 when Cs > 0,
+    and inside the objective regions the dJ/df coefficients (2 for the drag
+    plane, 1 + D + D(D+1)/2 for the dissipation box) and dJ/dd."""
     q = wl.q
     nx, ny, nz = wl.dims
     N = nx * ny * nz
+    D = 2 if q == 9 else 3
     plain = 2 * q * storage_bytes + real_bytes
     r = wl.regions
     ffa_cells = (r.ffa_y[1] - r.ffa_y[0]) * (r.ffa_z[1] - r.ffa_z[0])
     b = r.diss_box
     diss_cells = (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
     les = wl.Cs > 0
-    acc = plain + 2 * q * 8 + (16 if les else 0)
-    acc += (ffa_cells * 2 * q * 8 + diss_cells * (2 * q * 8 + 16)) / N
-    D = 2 if q == 9 else 3
+    acc = plain + 16 * (1 + D) + (16 * q + 16 if les else 0)
+    acc += (ffa_cells * 16 * 2 + diss_cells * (16 * (1 + D + D * (D + 1) // 2) + 16)) / N
     rec = q if exact_rec else D + 2
     adj_ffa = (2 * q + rec + 1) * real_bytes + ffa_cells * q * real_bytes / N
     adj_diss = (2 * q + rec + 1) * real_bytes + diss_cells * q * real_bytes / N
@@ -155,6 +162,22 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(lups_per_rank: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput: every rank processes its own replica (weak scaling)."""
+    return world * lups_per_rank / (ms_max * 1e-3) / 1e6
+
 
 def run_ours(args, rank, world):
     import torch
@@ -262,21 +285,13 @@ def run_ours(args, rank, world):
     lups, ms, launches, Js = timed(False)
     clocks = sampler.stop()
     phase_dev = {k: (list(v) if isinstance(v, list) else v) for k, v in phase.items()}
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * lups / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms, world, dev)
+    value = job_mlups(lups, ms, world)
     e2e = None
     if not args.no_e2e:
         lups_h, ms_h, _, _ = timed(True)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms_h], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_h = float(t.item())
-        e2e = {"value": world * lups_h / (ms_h * 1e-3) / 1e6, "unit": "MLUPS",
+        ms_h = max_over_ranks(ms_h, world, dev)
+        e2e = {"value": job_mlups(lups_h, ms_h, world), "unit": "MLUPS",
                "h2d_bytes_per_step": int(N * 8 + D * N * 8),
                "d2h_bytes_per_step": int(2 * gvol * 8 + 2 * 8)}
     s.close()

@@ -69,9 +69,13 @@ enum {
   HLBM_FIELD_RHO = 0,    /* get: density of the current canonical state (N) */
   HLBM_FIELD_U = 1,      /* get: velocity u = sum xi f / rho (dim x N) */
   HLBM_FIELD_F = 2,      /* get/set: canonical populations (q x N) */
-  HLBM_FIELD_FBAR = 3,   /* get/set: averaged populations (q x N) */
+  HLBM_FIELD_FBAR = 3,   /* get/set: averaged populations (q x N); get needs
+                            average_full_f or Cs > 0 */
   HLBM_FIELD_GBAR_FFA = 4,   /* get/set: averaged dJ_FFA/df (q x N) */
-  HLBM_FIELD_GBAR_DISS = 5,  /* get/set: averaged dJ_DISS/df (q x N) */
+  HLBM_FIELD_GBAR_DISS = 5,  /* get/set: averaged dJ_DISS/df (q x N); both are kept
+                                as coefficients of a quadratic polynomial in xi
+                                (the form every objective derivative has), so a
+                                set value is projected onto that form */
   HLBM_FIELD_DJDD_FFA = 6,   /* get/set: averaged dJ_FFA/dd (N) */
   HLBM_FIELD_DJDD_DISS = 7,  /* get/set: averaged dJ_DISS/dd (N) */
   HLBM_FIELD_TAU_T = 8,      /* get/set: averaged tau_eff - tau0 (N) */
@@ -108,6 +112,11 @@ typedef struct {
   int design_box[6];    /* Omega_alpha: region returned by hlbm_gradient */
   int accum_stride;     /* sample every k-th step of the window (>= 1) */
   int check_every;      /* adjoint residual check interval, even (>= 2) */
+  int average_full_f;   /* 1: also average all q populations (HLBM_FIELD_FBAR);
+                           always on when Cs > 0, where the exact LES adjoint
+                           linearises at f_bar itself.  Otherwise only the
+                           density and momentum of f are averaged, which is
+                           all the BGK / frozen-turbulence linearisation reads */
   void* stream;         /* cudaStream_t to issue work on; NULL = own stream */
   void* (*dev_alloc)(size_t bytes, void* user); /* NULL = cudaMalloc */
   void (*dev_free)(void* ptr, void* user);      /* NULL = cudaFree */

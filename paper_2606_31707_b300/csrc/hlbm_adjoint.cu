@@ -47,6 +47,7 @@ __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R
   const R* rec = static_cast<const R*>(a.rec);
   const long long rp = a.rec_pitch;
   c.d = d;
+  R drho = 0;
   if constexpr (!EXACT) {
     c.rho = rec[cell];
     c.u.x = rec[rp + cell];
@@ -54,22 +55,25 @@ __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R
     c.u.z = Lat<Q>::D == 3 ? rec[3 * rp + cell] : R(0);
     c.om = rec[(Lat<Q>::D + 1) * rp + cell];
   } else {
-    R fb[Q];
+    // the record holds f_bar - w
+    R gb[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fb[i] = rec[(long long)i * rp + cell];
-    moments<Q>(fb, c.rho, c.u);
+    for (int i = 0; i < Q; ++i) gb[i] = rec[(long long)i * rp + cell];
+    Vec3<R> m;
+    moments_dev<Q>(gb, drho, c.rho, m, c.u);
   }
   const R one_d = R(1) - d;
-  c.ut = Vec3<R>{d * c.u.x + one_d * R(a.us[0]), d * c.u.y + one_d * R(a.us[1]),
-                 d * c.u.z + one_d * R(a.us[2])};
+  const Vec3<R> us{par<R>(a.us[0], a.us_f[0]), par<R>(a.us[1], a.us_f[1]),
+                   par<R>(a.us[2], a.us_f[2])};
+  c.ut = Vec3<R>{d * c.u.x + one_d * us.x, d * c.u.y + one_d * us.y, d * c.u.z + one_d * us.z};
   if constexpr (EXACT) {
     const R uu = dot3(c.ut, c.ut);
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-      c.fneq[i] = rec[(long long)i * rp + cell] - feq_i<Q>(i, c.rho, c.ut, uu);
+      c.fneq[i] = rec[(long long)i * rp + cell] - geq_i<Q>(i, drho, c.rho, c.ut, uu);
     c.P = second_moment<Q, R>(c.fneq);
     c.nP = sqrt_r<R>(sym_norm2(c.P));
-    c.tau = tau_smagorinsky<R>(R(a.tau_b), R(a.kles), c.nP);
+    c.tau = tau_smagorinsky<R>(par<R>(a.tau_b, a.tau_b_f), par<R>(a.kles, a.kles_f), c.nP);
     c.om = R(1) / c.tau;
   }
 }
@@ -115,7 +119,8 @@ __device__ __forceinline__ void transpose_collide(const LinCell<Q, R, EXACT>& c,
 #pragma unroll
       for (int i = 0; i < Q; ++i) sn += mu[i] * c.fneq[i];
       // sum mu_i (f^eq_i - f_i) = -sn
-      E = om * om * sn * R(a.kles) / ((R(2) * c.tau - R(a.tau_b)) * c.nP);
+      E = om * om * sn * par<R>(a.kles, a.kles_f) /
+          ((R(2) * c.tau - par<R>(a.tau_b, a.tau_b_f)) * c.nP);
     }
     PU = sym_mul(c.P, c.ut);
     uPu = dot3(c.ut, PU);
@@ -177,16 +182,18 @@ __device__ __forceinline__ void residual_io(const AdjointArgs& a, long long cell
                                             double& rp) {
   if (RES == 0) return;
   R* sn = static_cast<R*>(a.snap);
+  R acc = 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     R* p = sn + (long long)i * a.g.pitch + cell;
     if (RES == 1) {
       *p = v[i];
     } else {
-      const double dlt = (double)v[i] - (double)*p;
-      rp += dlt * dlt;
+      const R dlt = v[i] - *p;
+      acc += dlt * dlt;
     }
   }
+  if (RES == 2) rp += (double)acc;
 }
 
 template <int Q, class R, bool ODD, bool EXACT, int RES>
@@ -275,18 +282,15 @@ __global__ void __launch_bounds__(NT) k_prep(PrepArgs a) {
       rec[(long long)i * rp + cell] = (R)(a.fsum[(long long)i * g.N + cell] * a.inv_n);
     return;
   }
-  double fb[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) fb[i] = a.fsum[(long long)i * g.N + cell] * a.inv_n;
-  double rho;
-  Vec3<double> u;
-  moments<Q, double>(fb, rho, u);
+  // density and velocity of f_bar from the averaged moments (rho - 1, rho u)
+  const double rho = 1.0 + a.msum[cell] * a.inv_n;
+  const double ir = 1.0 / rho;
   double tau = a.tau_b;
   if (a.tsum) tau += a.tsum[cell] * a.inv_n;
   rec[cell] = (R)rho;
-  rec[rp + cell] = (R)u.x;
-  rec[2 * rp + cell] = (R)u.y;
-  if (Lat<Q>::D == 3) rec[3 * rp + cell] = (R)u.z;
+  rec[rp + cell] = (R)(a.msum[g.N + cell] * a.inv_n * ir);
+  rec[2 * rp + cell] = (R)(a.msum[2 * g.N + cell] * a.inv_n * ir);
+  if (Lat<Q>::D == 3) rec[3 * rp + cell] = (R)(a.msum[3 * g.N + cell] * a.inv_n * ir);
   rec[(Lat<Q>::D + 1) * rp + cell] = (R)(1.0 / tau);
 }
 
@@ -300,6 +304,7 @@ cudaError_t launch_prep(const PrepArgs& a, int q, bool dbl, cudaStream_t s) {
 
 template <int Q, class R>
 __global__ void __launch_bounds__(NT) k_source(SourceArgs a) {
+  constexpr int D = Lat<Q>::D;
   const int bx = a.box[1] - a.box[0], by = a.box[3] - a.box[2];
   const int xl = blockIdx.x * NT + threadIdx.x;
   const int yl = blockIdx.y, zl = blockIdx.z;
@@ -308,10 +313,16 @@ __global__ void __launch_bounds__(NT) k_source(SourceArgs a) {
     const long long bc = (long long)xl + (long long)bx * ((long long)yl + (long long)by * zl);
     const long long vol = (long long)bx * by * (a.box[5] - a.box[4]);
     const long long cell = cell_of(a.g, a.box[0] + xl, a.box[2] + yl, a.box[4] + zl);
+    const int nc = ncoef(a.obj_slot, D);
+    double cf[10];
+    for (int k = 0; k < nc; ++k) cf[k] = a.gsum[(long long)k * a.g.N + cell] * a.inv_n;
     R* src = static_cast<R*>(a.src);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const R v = (R)(a.gsum[(long long)i * a.g.N + cell] * a.inv_n);
+      double gv = 0.0;
+      for (int k = 0; k < nc; ++k)
+        gv += cf[k] * coef_basis(a.obj_slot, D, k, Lat<Q>::cx(i), Lat<Q>::cy(i), Lat<Q>::cz(i));
+      const R v = (R)gv;
       src[(long long)i * vol + bc] = v;
       acc += (double)v * (double)v;
     }
@@ -354,13 +365,16 @@ __global__ void __launch_bounds__(NT) k_gradient(GradArgs ga) {
   a.rec_pitch = ga.rec_pitch;
   a.tau_b = ga.tau_b;
   a.kles = ga.kles;
-  a.us[0] = ga.us[0]; a.us[1] = ga.us[1]; a.us[2] = ga.us[2];
+  a.tau_b_f = ga.tau_b_f;
+  a.kles_f = ga.kles_f;
+  for (int k = 0; k < 3; ++k) { a.us[k] = ga.us[k]; a.us_f[k] = ga.us_f[k]; }
   LinCell<Q, R, EXACT> c;
   load_lin<Q, R, EXACT>(a, cell, static_cast<const R*>(ga.d)[cell], c);
   R s0, m0;
   Vec3<R> s;
   contract<Q, R>(mu, c.ut, s0, s, m0);
-  const Vec3<R> v{c.u.x - R(ga.us[0]), c.u.y - R(ga.us[1]), c.u.z - R(ga.us[2])};
+  const Vec3<R> v{c.u.x - par<R>(ga.us[0], ga.us_f[0]), c.u.y - par<R>(ga.us[1], ga.us_f[1]),
+                  c.u.z - par<R>(ga.us[2], ga.us_f[2])};
   const Vec3<R> gv{s.x - R(3) * c.ut.x * s0, s.y - R(3) * c.ut.y * s0, s.z - R(3) * c.ut.z * s0};
   R val = c.om * c.rho * dot3(gv, v);
   if constexpr (EXACT) {
@@ -370,7 +384,8 @@ __global__ void __launch_bounds__(NT) k_gradient(GradArgs ga) {
       for (int i = 0; i < Q; ++i) sn += mu[i] * c.fneq[i];
       const R pdd = -R(2) * c.rho * dot3(v, sym_mul(c.P, c.ut));
       // (sum mu (feq - f)) * (-om^2) * k pdd / ((2 tau - tau_b) |Pi|)
-      val += sn * c.om * c.om * R(ga.kles) * pdd / ((R(2) * c.tau - R(ga.tau_b)) * c.nP);
+      val += sn * c.om * c.om * par<R>(ga.kles, ga.kles_f) * pdd /
+             ((R(2) * c.tau - par<R>(ga.tau_b, ga.tau_b_f)) * c.nP);
     }
   }
   double G = (double)val;

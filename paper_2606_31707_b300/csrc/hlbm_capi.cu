@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <utility>
 #include <string>
 
 #include "../../include/hlbm.h"
@@ -31,7 +32,10 @@ struct hlbm_ctx {
   int phase = 0;  // 0: natural layout, next primal kernel is even
   long steps_done = 0;
   // averages
-  double* fsum = nullptr;
+  double* msum = nullptr;   // (1 + D) x N sums of rho, rho u
+  double* fsum = nullptr;   // q x N sums of f (full_f only, or set by the caller)
+  bool full_f = false;
+  double pmat[2][10 * 19] = {};  // least-squares inverse of the dJ/df coefficient basis
   double* tsum = nullptr;
   double* gsum[2] = {nullptr, nullptr};
   double* ddsum[2] = {nullptr, nullptr};
@@ -64,6 +68,13 @@ struct hlbm_ctx {
   double* stage = nullptr;
   size_t stage_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // captured CUDA graphs of kGraphSteps consecutive primal steps, one per
+  // (averaging variant, phase of the first step)
+  struct PrimalGraph {
+    cudaGraphExec_t exec = nullptr;
+    PrimalArgs args{};
+  } pgraph[3][2];
+  bool graphs_ok = true;
   hlbm_stats stats{};
   std::string msg;
 };
@@ -189,14 +200,18 @@ void objective_box(const hlbm_ctx* c, int obj, int box[6]) {
 
 int obj_slot(int obj) { return obj == HLBM_OBJ_DRAG_FFA ? 0 : (obj == HLBM_OBJ_DISSIPATION ? 1 : -1); }
 
+size_t coef_bytes(const hlbm_ctx* c, int o) { return (size_t)ncoef(o, c->D) * c->g.N * 8; }
+
 int ensure_averages(hlbm_ctx* c, int mask) {
   const long long N = c->g.N;
   const size_t qN = (size_t)c->q * N * 8;
-  if (!c->fsum && !(c->fsum = (double*)dalloc(c, qN))) return set_err(c, HLBM_ENOMEM, "fsum");
+  if (!c->msum && !(c->msum = (double*)dalloc(c, (size_t)(1 + c->D) * N * 8)))
+    return set_err(c, HLBM_ENOMEM, "msum");
+  if (c->full_f && !c->fsum && !(c->fsum = (double*)dalloc(c, qN))) return set_err(c, HLBM_ENOMEM, "fsum");
   if (!c->tsum && !(c->tsum = (double*)dalloc(c, (size_t)N * 8))) return set_err(c, HLBM_ENOMEM, "tsum");
   for (int o = 0; o < 2; ++o) {
     if (!(mask & (1 << o))) continue;
-    if (!c->gsum[o] && !(c->gsum[o] = (double*)dalloc(c, qN))) return set_err(c, HLBM_ENOMEM, "gsum");
+    if (!c->gsum[o] && !(c->gsum[o] = (double*)dalloc(c, coef_bytes(c, o)))) return set_err(c, HLBM_ENOMEM, "gsum");
     if (!c->ddsum[o] && !(c->ddsum[o] = (double*)dalloc(c, (size_t)N * 8))) return set_err(c, HLBM_ENOMEM, "ddsum");
     if (!c->jblk[o] && !(c->jblk[o] = (double*)dalloc(c, (size_t)c->nblk * 8))) return set_err(c, HLBM_ENOMEM, "jblk");
   }
@@ -207,11 +222,12 @@ int reset_averages(hlbm_ctx* c, int mask) {
   int rc = ensure_averages(c, mask);
   if (rc) return rc;
   const long long N = c->g.N;
-  HLBM_TRY(c, cudaMemsetAsync(c->fsum, 0, (size_t)c->q * N * 8, c->stream), "memset");
+  HLBM_TRY(c, cudaMemsetAsync(c->msum, 0, (size_t)(1 + c->D) * N * 8, c->stream), "memset");
+  if (c->fsum) HLBM_TRY(c, cudaMemsetAsync(c->fsum, 0, (size_t)c->q * N * 8, c->stream), "memset");
   HLBM_TRY(c, cudaMemsetAsync(c->tsum, 0, (size_t)N * 8, c->stream), "memset");
   for (int o = 0; o < 2; ++o) {
     if (!(mask & (1 << o))) continue;
-    HLBM_TRY(c, cudaMemsetAsync(c->gsum[o], 0, (size_t)c->q * N * 8, c->stream), "memset");
+    HLBM_TRY(c, cudaMemsetAsync(c->gsum[o], 0, coef_bytes(c, o), c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->ddsum[o], 0, (size_t)N * 8, c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->jblk[o], 0, (size_t)c->nblk * 8, c->stream), "memset");
   }
@@ -240,6 +256,12 @@ PrimalArgs primal_args(hlbm_ctx* c) {
   a.u_in = c->opt.u_in;
   for (int k = 0; k < 3; ++k) a.us[k] = c->opt.u_solid[k];
   a.nu0 = c->nu0;
+  a.tau0_f = (float)a.tau0;
+  a.kles_f = (float)a.kles;
+  a.u_in_f = (float)a.u_in;
+  for (int k = 0; k < 3; ++k) a.us_f[k] = (float)a.us[k];
+  a.nu0_f = (float)a.nu0;
+  a.msum = c->msum;
   a.fsum = c->fsum;
   a.tsum = c->tsum;
   for (int o = 0; o < 2; ++o) {
@@ -328,6 +350,43 @@ int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau, doub
   c->kles = 4.5 * std::sqrt(2.0) * Cs * Cs;
   c->nu0 = (tau - 0.5) / 3.0;
   c->nblk = (long long)((dims[0] + NT - 1) / NT) * dims[1] * dims[2];
+  c->full_f = c->opt.average_full_f != 0 || Cs > 0.0;
+  // least-squares inverse P = (V^T V)^-1 V^T of the coefficient basis V (q x nc)
+  for (int o = 0; o < 2; ++o) {
+    const int nc = ncoef(o, c->D), q = c->q;
+    double V[19][10], M[10][20];
+    for (int i = 0; i < q; ++i) {
+      const int x = lattice == 9 ? Lat<9>::cx(i) : Lat<19>::cx(i);
+      const int y = lattice == 9 ? Lat<9>::cy(i) : Lat<19>::cy(i);
+      const int z = lattice == 9 ? 0 : Lat<19>::cz(i);
+      for (int k = 0; k < nc; ++k) V[i][k] = coef_basis(o, c->D, k, x, y, z);
+    }
+    for (int a = 0; a < nc; ++a)
+      for (int b = 0; b < 2 * nc; ++b) {
+        double v = 0.0;
+        if (b < nc) for (int i = 0; i < q; ++i) v += V[i][a] * V[i][b];
+        else v = (b - nc == a) ? 1.0 : 0.0;
+        M[a][b] = v;
+      }
+    for (int col = 0; col < nc; ++col) {  // Gauss-Jordan with partial pivoting
+      int piv = col;
+      for (int r = col + 1; r < nc; ++r) if (std::fabs(M[r][col]) > std::fabs(M[piv][col])) piv = r;
+      for (int b = 0; b < 2 * nc; ++b) std::swap(M[col][b], M[piv][b]);
+      const double inv = 1.0 / M[col][col];
+      for (int b = 0; b < 2 * nc; ++b) M[col][b] *= inv;
+      for (int r = 0; r < nc; ++r) {
+        if (r == col) continue;
+        const double fct = M[r][col];
+        for (int b = 0; b < 2 * nc; ++b) M[r][b] -= fct * M[col][b];
+      }
+    }
+    for (int k = 0; k < nc; ++k)
+      for (int i = 0; i < q; ++i) {
+        double v = 0.0;
+        for (int a = 0; a < nc; ++a) v += M[k][nc + a] * V[i][a];
+        c->pmat[o][k * q + i] = v;
+      }
+  }
   int ffa[6] = {c->opt.ffa_x, c->opt.ffa_x + 1, c->opt.ffa_y0, c->opt.ffa_y1, c->opt.ffa_z0, c->opt.ffa_z1};
   if (!check_box(c, ffa) || !check_box(c, c->opt.diss_box) || !check_box(c, c->opt.design_box)) {
     delete c;
@@ -425,6 +484,57 @@ int hlbm_init_equilibrium(hlbm_ctx* c, const void* rho, const void* u, int dtype
   return HLBM_OK;
 }
 
+static constexpr long kGraphSteps = 64;
+
+// Run `count` consecutive primal steps of one variant starting at the current
+// phase.  Whole blocks of kGraphSteps steps replay a captured CUDA graph (the
+// arguments of every step are identical, only the AA phase alternates), the
+// rest are launched directly.
+static int primal_steps(hlbm_ctx* c, const PrimalArgs& a, bool les, int accv, long count) {
+  long done = 0;
+  if (c->graphs_ok && count >= kGraphSteps) {
+    auto& pg = c->pgraph[accv][c->phase];
+    if (pg.exec && std::memcmp(&pg.args, &a, sizeof a) != 0) {
+      cudaGraphExecDestroy(pg.exec);
+      pg.exec = nullptr;
+    }
+    if (!pg.exec) {
+      cudaGraph_t graph = nullptr;
+      bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      int ph = c->phase;
+      for (long k = 0; ok && k < kGraphSteps; ++k) {
+        ok = launch_primal(a, c->q, c->storage, ph == 1, les, accv, c->stream) == cudaSuccess;
+        ph ^= 1;
+      }
+      if (cudaStreamEndCapture(c->stream, &graph) != cudaSuccess) ok = false;
+      if (ok && cudaGraphInstantiate(&pg.exec, graph, 0) != cudaSuccess) {
+        ok = false;
+        pg.exec = nullptr;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      if (!ok) {
+        cudaGetLastError();
+        c->graphs_ok = false;  // fall back to direct launches from now on
+      } else {
+        pg.args = a;
+      }
+    }
+    if (pg.exec) {
+      for (; done + kGraphSteps <= count; done += kGraphSteps) {
+        HLBM_TRY(c, cudaGraphLaunch(pg.exec, c->stream), "graph launch");
+        c->stats.kernels_total += kGraphSteps;
+      }
+      // kGraphSteps is even: the phase is unchanged after each replay
+    }
+  }
+  for (; done < count; ++done) {
+    cudaError_t e = CNT(c, launch_primal)(a, c->q, c->storage, c->phase == 1, les, accv, c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "primal launch");
+    c->phase ^= 1;
+  }
+  return HLBM_OK;
+}
+
 int hlbm_run_primal(hlbm_ctx* c, long steps, long W) {
   if (!c) return HLBM_EINVAL;
   if (steps < 0 || W < 0 || W > steps) return set_err(c, HLBM_EINVAL, "need 0 <= avg_window <= steps");
@@ -440,13 +550,24 @@ int hlbm_run_primal(hlbm_ctx* c, long steps, long W) {
   const long stride = c->opt.accum_stride;
   HLBM_TRY(c, cudaEventRecord(c->ev0, c->stream), "event");
   long launches = 0, samples = 0;
-  for (long n = 0; n < steps; ++n) {
-    const bool acc = W > 0 && n >= first && ((n - first) % stride) == 0;
-    cudaError_t e = CNT(c, launch_primal)(a, c->q, c->storage, c->phase == 1, les, acc, c->stream);
-    if (e != cudaSuccess) return cuda_check(c, e, "primal launch");
-    c->phase ^= 1;
-    ++launches;
-    if (acc) ++samples;
+  const int acc_variant = c->full_f ? 2 : 1;
+  // plain steps before the window
+  rc = primal_steps(c, a, les, 0, first);
+  if (rc) return rc;
+  launches += first;
+  if (W > 0 && stride == 1) {
+    rc = primal_steps(c, a, les, acc_variant, W);
+    if (rc) return rc;
+    launches += W;
+    samples = W;
+  } else {
+    for (long n = first; n < steps; ++n) {
+      const bool acc = ((n - first) % stride) == 0;
+      rc = primal_steps(c, a, les, acc ? acc_variant : 0, 1);
+      if (rc) return rc;
+      ++launches;
+      if (acc) ++samples;
+    }
   }
   HLBM_TRY(c, cudaEventRecord(c->ev1, c->stream), "event");
   unsigned err = 0;
@@ -494,8 +615,10 @@ static int prepare_linearisation(hlbm_ctx* c, int mode) {
     c->rec_bytes = c->rec ? bytes : 0;
     if (!c->rec) return set_err(c, HLBM_ENOMEM, "record");
   }
+  if (want && !c->fsum) return set_err(c, HLBM_ESTATE, "exact LES linearisation needs the averaged f");
   PrepArgs p{};
   p.fsum = c->fsum;
+  p.msum = c->msum;
   p.tsum = (mode == HLBM_ADJ_FTA && c->Cs > 0.0) ? c->tsum : nullptr;
   p.inv_n = 1.0 / (double)c->nsamples;
   p.rec = c->rec;
@@ -519,7 +642,9 @@ static AdjointArgs adjoint_args(hlbm_ctx* c, int mode, const int sb[6]) {
   a.rec_pitch = c->g.N;
   a.tau_b = c->rec_taub;
   a.kles = c->kles;
-  for (int k = 0; k < 3; ++k) a.us[k] = c->opt.u_solid[k];
+  for (int k = 0; k < 3; ++k) { a.us[k] = c->opt.u_solid[k]; a.us_f[k] = (float)a.us[k]; }
+  a.tau_b_f = (float)a.tau_b;
+  a.kles_f = (float)a.kles;
   a.src = c->src;
   std::memcpy(a.sb, sb, sizeof a.sb);
   a.src_pitch = (long long)(sb[1] - sb[0]) * (sb[3] - sb[2]) * (sb[5] - sb[4]);
@@ -566,6 +691,7 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
   HLBM_TRY(c, cudaEventRecord(c->ev0, c->stream), "event");
   SourceArgs sa{};
   sa.gsum = c->gsum[o];
+  sa.obj_slot = o;
   sa.inv_n = 1.0 / (double)c->nsamples;
   sa.src = c->src;
   std::memcpy(sa.box, sb, sizeof sa.box);
@@ -639,7 +765,9 @@ static int run_gradient(hlbm_ctx* c, const int box[6], double* out, double* mu_o
   ga.rec_pitch = c->g.N;
   ga.tau_b = c->rec_taub;
   ga.kles = c->kles;
-  for (int k = 0; k < 3; ++k) ga.us[k] = c->opt.u_solid[k];
+  for (int k = 0; k < 3; ++k) { ga.us[k] = c->opt.u_solid[k]; ga.us_f[k] = (float)ga.us[k]; }
+  ga.tau_b_f = (float)ga.tau_b;
+  ga.kles_f = (float)ga.kles;
   ga.ddsum = c->ddsum[o];
   ga.inv_n = 1.0 / (double)c->nsamples;
   std::memcpy(ga.box, box, sizeof ga.box);
@@ -681,21 +809,37 @@ int hlbm_get_field(hlbm_ctx* c, int which, void* out, int dtype, int on_device) 
                                  which == HLBM_FIELD_U ? c->stage : nullptr, c->stream), "readout");
       break;
     }
-    case HLBM_FIELD_FBAR:
     case HLBM_FIELD_GBAR_FFA:
-    case HLBM_FIELD_GBAR_DISS:
+    case HLBM_FIELD_GBAR_DISS: {
+      if (c->nsamples < 1) return set_err(c, HLBM_ESTATE, "no averages");
+      const int o = which == HLBM_FIELD_GBAR_FFA ? 0 : 1;
+      if (!c->gsum[o] || !(c->acc_mask & (1 << o))) return set_err(c, HLBM_ESTATE, "field not averaged");
+      n = qN;
+      rc = ensure_stage(c, (size_t)n * 12);
+      if (rc) return rc;
+      HLBM_TRY(c, CNT(c, launch_expand_coef)(c->gsum[o], o, c->q, N, 1.0 / (double)c->nsamples,
+                                             c->stage, c->stream), "expand");
+      break;
+    }
+    case HLBM_FIELD_FBAR:
     case HLBM_FIELD_DJDD_FFA:
     case HLBM_FIELD_DJDD_DISS:
     case HLBM_FIELD_TAU_T: {
       if (c->nsamples < 1) return set_err(c, HLBM_ESTATE, "no averages");
       const double* src = nullptr;
-      if (which == HLBM_FIELD_FBAR) { src = c->fsum; n = qN; }
-      if (which == HLBM_FIELD_GBAR_FFA) { src = c->gsum[0]; n = qN; }
-      if (which == HLBM_FIELD_GBAR_DISS) { src = c->gsum[1]; n = qN; }
+      if (which == HLBM_FIELD_FBAR) {
+        if (!c->fsum) return set_err(c, HLBM_ESTATE, "f_bar is not averaged (needs average_full_f or Cs > 0)");
+        n = qN;
+        rc = ensure_stage(c, (size_t)n * 12);
+        if (rc) return rc;
+        HLBM_TRY(c, CNT(c, launch_fbar_out)(c->fsum, c->q, N, 1.0 / (double)c->nsamples, c->stage,
+                                            c->stream), "fbar");
+        break;
+      }
       if (which == HLBM_FIELD_DJDD_FFA) { src = c->ddsum[0]; n = N; }
       if (which == HLBM_FIELD_DJDD_DISS) { src = c->ddsum[1]; n = N; }
       if (which == HLBM_FIELD_TAU_T) { src = c->tsum; n = N; }
-      if (!src) return set_err(c, HLBM_ESTATE, "field not averaged");
+      if (!src) return set_err(c, HLBM_ESTATE, "field not averaged (f_bar needs average_full_f or Cs > 0)");
       rc = ensure_stage(c, (size_t)n * 12);
       if (rc) return rc;
       HLBM_TRY(c, cudaMemcpyAsync(c->stage, src, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream), "copy");
@@ -752,14 +896,19 @@ int hlbm_set_field(hlbm_ctx* c, int which, const void* data, int dtype, int on_d
   }
   rc = ensure_averages(c, need_mask | c->acc_mask);
   if (rc) return rc;
+  if (which == HLBM_FIELD_FBAR && !c->fsum) {
+    if (!(c->fsum = (double*)dalloc(c, (size_t)qN * 8))) return set_err(c, HLBM_ENOMEM, "fsum");
+    HLBM_TRY(c, cudaMemsetAsync(c->fsum, 0, (size_t)qN * 8, c->stream), "memset");
+  }
   // a set field defines a window of one sample: rescale existing sums
   if (c->nsamples > 1) {
     const double s = 1.0 / (double)c->nsamples;
-    CNT(c, launch_scale)(c->fsum, qN, s, c->stream);
+    CNT(c, launch_scale)(c->msum, (long long)(1 + c->D) * N, s, c->stream);
+    if (c->fsum) CNT(c, launch_scale)(c->fsum, qN, s, c->stream);
     CNT(c, launch_scale)(c->tsum, N, s, c->stream);
     for (int o = 0; o < 2; ++o) {
       if (!(c->acc_mask & (1 << o))) continue;
-      CNT(c, launch_scale)(c->gsum[o], qN, s, c->stream);
+      CNT(c, launch_scale)(c->gsum[o], (long long)ncoef(o, c->D) * N, s, c->stream);
       CNT(c, launch_scale)(c->ddsum[o], N, s, c->stream);
       CNT(c, launch_scale)(c->jblk[o], c->nblk, s, c->stream);
     }
@@ -771,22 +920,28 @@ int hlbm_set_field(hlbm_ctx* c, int which, const void* data, int dtype, int on_d
   }
   if (need_mask && !(c->acc_mask & need_mask)) {
     const int o = need_mask - 1;
-    HLBM_TRY(c, cudaMemsetAsync(c->gsum[o], 0, (size_t)qN * 8, c->stream), "memset");
+    HLBM_TRY(c, cudaMemsetAsync(c->gsum[o], 0, coef_bytes(c, o), c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->ddsum[o], 0, (size_t)N * 8, c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->jblk[o], 0, (size_t)c->nblk * 8, c->stream), "memset");
     c->acc_mask |= need_mask;
   }
-  switch (which) {
-    case HLBM_FIELD_FBAR: dst = c->fsum; break;
-    case HLBM_FIELD_GBAR_FFA: dst = c->gsum[0]; break;
-    case HLBM_FIELD_GBAR_DISS: dst = c->gsum[1]; break;
-    case HLBM_FIELD_DJDD_FFA: dst = c->ddsum[0]; break;
-    case HLBM_FIELD_DJDD_DISS: dst = c->ddsum[1]; break;
-    case HLBM_FIELD_TAU_T: dst = c->tsum; break;
-  }
   rc = stage_in(c, data, dtype, on_device, n);
   if (rc) return rc;
-  HLBM_TRY(c, cudaMemcpyAsync(dst, c->stage, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  switch (which) {
+    case HLBM_FIELD_FBAR:
+      HLBM_TRY(c, CNT(c, launch_set_fbar)(c->stage, c->q, N, c->fsum, c->msum, c->stream), "fbar");
+      break;
+    case HLBM_FIELD_GBAR_FFA:
+    case HLBM_FIELD_GBAR_DISS: {
+      const int o = which == HLBM_FIELD_GBAR_FFA ? 0 : 1;
+      HLBM_TRY(c, CNT(c, launch_project_coef)(c->stage, c->pmat[o], o, c->q, N, c->gsum[o], c->stream), "project");
+      break;
+    }
+    default:
+      dst = which == HLBM_FIELD_DJDD_FFA ? c->ddsum[0]
+            : which == HLBM_FIELD_DJDD_DISS ? c->ddsum[1] : c->tsum;
+      HLBM_TRY(c, cudaMemcpyAsync(dst, c->stage, (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  }
   HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
   c->nsamples = 1;
   c->generation++;
@@ -803,7 +958,7 @@ int hlbm_get_stats(const hlbm_ctx* c, hlbm_stats* out) {
 // checkpoint file: header, then the raw population array and the FP64 sums
 struct CkptHeader {
   char magic[8];
-  int q, storage, nx, ny, nz, phase, acc_mask, pad;
+  int q, storage, nx, ny, nz, phase, acc_mask, has_fsum;
   long long steps_done, nsamples;
 };
 
@@ -812,7 +967,8 @@ int hlbm_save(hlbm_ctx* c, const char* path) {
   FILE* fp = std::fopen(path, "wb");
   if (!fp) return set_err(c, HLBM_EINVAL, "cannot open %s", path);
   CkptHeader h{};
-  std::memcpy(h.magic, "HLBMCK1", 8);
+  std::memcpy(h.magic, "HLBMCK2", 8);
+  h.has_fsum = c->fsum != nullptr;
   h.q = c->q; h.storage = c->storage; h.nx = c->g.nx; h.ny = c->g.ny; h.nz = c->g.nz;
   h.phase = c->phase; h.acc_mask = c->nsamples > 0 ? c->acc_mask : 0;
   h.steps_done = c->steps_done; h.nsamples = c->nsamples;
@@ -832,11 +988,12 @@ int hlbm_save(hlbm_ctx* c, const char* path) {
   int rc = dump(c->f, (size_t)c->q * c->g.pitch * pop_elem_bytes(c->storage));
   if (!rc) rc = dump(c->d, (size_t)c->g.N * real_bytes(c));
   if (!rc && h.nsamples > 0) {
-    rc = dump(c->fsum, (size_t)c->q * c->g.N * 8);
+    rc = dump(c->msum, (size_t)(1 + c->D) * c->g.N * 8);
+    if (!rc && h.has_fsum) rc = dump(c->fsum, (size_t)c->q * c->g.N * 8);
     if (!rc) rc = dump(c->tsum, (size_t)c->g.N * 8);
     for (int o = 0; o < 2 && !rc; ++o) {
       if (!(h.acc_mask & (1 << o))) continue;
-      rc = dump(c->gsum[o], (size_t)c->q * c->g.N * 8);
+      rc = dump(c->gsum[o], coef_bytes(c, o));
       if (!rc) rc = dump(c->ddsum[o], (size_t)c->g.N * 8);
       if (!rc) rc = dump(c->jblk[o], (size_t)c->nblk * 8);
     }
@@ -851,7 +1008,7 @@ int hlbm_load(hlbm_ctx* c, const char* path) {
   FILE* fp = std::fopen(path, "rb");
   if (!fp) return set_err(c, HLBM_EINVAL, "cannot open %s", path);
   CkptHeader h{};
-  if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "HLBMCK1", 8) != 0 ||
+  if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "HLBMCK2", 8) != 0 ||
       h.q != c->q || h.storage != c->storage || h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz) {
     std::fclose(fp);
     return set_err(c, HLBM_EINVAL, "checkpoint does not match this context");
@@ -872,11 +1029,15 @@ int hlbm_load(hlbm_ctx* c, const char* path) {
   if (!rc) rc = load(c->d, (size_t)c->g.N * real_bytes(c));
   if (!rc && h.nsamples > 0) {
     rc = ensure_averages(c, h.acc_mask);
-    if (!rc) rc = load(c->fsum, (size_t)c->q * c->g.N * 8);
+    if (!rc) rc = load(c->msum, (size_t)(1 + c->D) * c->g.N * 8);
+    if (!rc && h.has_fsum) {
+      if (!c->fsum && !(c->fsum = (double*)dalloc(c, (size_t)c->q * c->g.N * 8))) rc = HLBM_ENOMEM;
+      if (!rc) rc = load(c->fsum, (size_t)c->q * c->g.N * 8);
+    }
     if (!rc) rc = load(c->tsum, (size_t)c->g.N * 8);
     for (int o = 0; o < 2 && !rc; ++o) {
       if (!(h.acc_mask & (1 << o))) continue;
-      rc = load(c->gsum[o], (size_t)c->q * c->g.N * 8);
+      rc = load(c->gsum[o], coef_bytes(c, o));
       if (!rc) rc = load(c->ddsum[o], (size_t)c->g.N * 8);
       if (!rc) rc = load(c->jblk[o], (size_t)c->nblk * 8);
     }
@@ -902,6 +1063,7 @@ void hlbm_destroy(hlbm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   dfree(c, c->f);
   dfree(c, c->d);
+  dfree(c, c->msum);
   dfree(c, c->fsum);
   dfree(c, c->tsum);
   for (int o = 0; o < 2; ++o) {
@@ -919,6 +1081,9 @@ void hlbm_destroy(hlbm_ctx* c) {
   if (c->err_host) cudaFreeHost(c->err_host);
   if (c->scal_dev) cudaFree(c->scal_dev);
   if (c->scal_host) cudaFreeHost(c->scal_host);
+  for (auto& row : c->pgraph)
+    for (auto& pg : row)
+      if (pg.exec) cudaGraphExecDestroy(pg.exec);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

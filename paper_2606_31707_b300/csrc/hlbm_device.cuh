@@ -69,41 +69,41 @@ template <> struct Lat<19> {
 };
 
 // ----------------------------------------------------------------------------
-// population storage formats (spec precision form (1)): the arithmetic
-// type R is double for FP64 storage and float otherwise.  The 16-bit formats
-// hold the deviation f_i - w_i from the rest-state equilibrium.
+// population storage formats (spec precision form (1)).  Every format
+// stores the deviation g_i = f_i - w_i from the rest-state equilibrium, and all
+// arithmetic works on deviations: they are O(Ma) small, so FP32 keeps ~2 more
+// significant digits than it would on f_i ~ w_i, and the 16-bit formats need
+// no shift.  The arithmetic type R is double for FP64 storage, else float.
 // ----------------------------------------------------------------------------
 enum StorageKind { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 
 template <int S> struct Store;
 template <> struct Store<ST_F64> {
   using mem = double; using real = double;
-  static __device__ __forceinline__ real ld(const mem* p, double) { return *p; }
-  static __device__ __forceinline__ void st(mem* p, real v, double) { *p = v; }
+  static __device__ __forceinline__ real ld(const mem* p) { return *p; }
+  static __device__ __forceinline__ void st(mem* p, real v) { *p = v; }
 };
 template <> struct Store<ST_F32> {
   using mem = float; using real = float;
-  static __device__ __forceinline__ real ld(const mem* p, double) { return *p; }
-  static __device__ __forceinline__ void st(mem* p, real v, double) { *p = v; }
+  static __device__ __forceinline__ real ld(const mem* p) { return *p; }
+  static __device__ __forceinline__ void st(mem* p, real v) { *p = v; }
 };
 template <> struct Store<ST_F16> {
   using mem = __half; using real = float;
-  static __device__ __forceinline__ real ld(const mem* p, double w) {
-    return __half2float(*p) + (float)w;
-  }
-  static __device__ __forceinline__ void st(mem* p, real v, double w) {
-    *p = __float2half_rn(v - (float)w);
-  }
+  static __device__ __forceinline__ real ld(const mem* p) { return __half2float(*p); }
+  static __device__ __forceinline__ void st(mem* p, real v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<ST_BF16> {
   using mem = __nv_bfloat16; using real = float;
-  static __device__ __forceinline__ real ld(const mem* p, double w) {
-    return __bfloat162float(*p) + (float)w;
-  }
-  static __device__ __forceinline__ void st(mem* p, real v, double w) {
-    *p = __float2bfloat16_rn(v - (float)w);
-  }
+  static __device__ __forceinline__ real ld(const mem* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void st(mem* p, real v) { *p = __float2bfloat16_rn(v); }
 };
+
+// scalar kernel parameters are passed in both precisions; FP32 kernels read the
+// float copy so that no FP64 instruction is issued per cell
+template <class R> __device__ __forceinline__ R par(double d, float f);
+template <> __device__ __forceinline__ double par<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float par<float>(double, float f) { return f; }
 
 template <class R> __device__ __forceinline__ R sqrt_r(R v);
 template <> __device__ __forceinline__ double sqrt_r(double v) { return sqrt(v); }
@@ -153,13 +153,12 @@ __device__ __forceinline__ void aa_load(const typename Store<S>::mem* A, const G
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (!ODD) {
-      f[i] = St::ld(A + (long long)i * g.pitch + cell, L::w(i));
+      f[i] = St::ld(A + (long long)i * g.pitch + cell);
     } else {
       long long c = (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0)
                         ? cell
                         : nbr(g, x, y, z, -SIGN * L::cx(i), -SIGN * L::cy(i), -SIGN * L::cz(i));
-      f[i] = c >= 0 ? St::ld(A + (long long)L::opp(i) * g.pitch + c, L::w(L::opp(i)))
-                    : typename St::real(0);
+      f[i] = c >= 0 ? St::ld(A + (long long)L::opp(i) * g.pitch + c) : typename St::real(0);
     }
   }
 }
@@ -173,12 +172,12 @@ __device__ __forceinline__ void aa_store(typename Store<S>::mem* A, const Grid& 
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (!ODD) {
-      St::st(A + (long long)L::opp(i) * g.pitch + cell, f[i], L::w(L::opp(i)));
+      St::st(A + (long long)L::opp(i) * g.pitch + cell, f[i]);
     } else {
       long long c = (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0)
                         ? cell
                         : nbr(g, x, y, z, SIGN * L::cx(i), SIGN * L::cy(i), SIGN * L::cz(i));
-      if (c >= 0) St::st(A + (long long)i * g.pitch + c, f[i], L::w(i));
+      if (c >= 0) St::st(A + (long long)i * g.pitch + c, f[i]);
     }
   }
 }
@@ -188,6 +187,28 @@ __device__ __forceinline__ void aa_store(typename Store<S>::mem* A, const Grid& 
 // ----------------------------------------------------------------------------
 template <class R> struct Vec3 { R x, y, z; };
 
+// moments of a deviation field g_i = f_i - w_i: rho - 1 = sum g, rho u = sum xi g
+// (the weights carry unit mass and zero momentum)
+template <int Q, class R>
+__device__ __forceinline__ void moments_dev(const R (&g)[Q], R& drho, R& rho, Vec3<R>& m,
+                                            Vec3<R>& u) {
+  using L = Lat<Q>;
+  R r = 0, mx = 0, my = 0, mz = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    r += g[i];
+    if (L::cx(i)) mx += L::cx(i) > 0 ? g[i] : -g[i];
+    if (L::cy(i)) my += L::cy(i) > 0 ? g[i] : -g[i];
+    if (L::cz(i)) mz += L::cz(i) > 0 ? g[i] : -g[i];
+  }
+  drho = r;
+  rho = R(1) + r;
+  m = Vec3<R>{mx, my, mz};
+  const R inv = R(1) / rho;
+  u = Vec3<R>{mx * inv, my * inv, mz * inv};
+}
+
+// moments of a full population field f (used by the no-context entry points)
 template <int Q, class R>
 __device__ __forceinline__ void moments(const R (&f)[Q], R& rho, Vec3<R>& u) {
   using L = Lat<Q>;
@@ -221,6 +242,13 @@ template <int Q, class R>
 __device__ __forceinline__ R feq_i(int i, R rho, const Vec3<R>& u, R uu) {
   R cu = xi_dot<Q>(i, u);
   return R(Lat<Q>::w(i)) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+}
+
+// f_i^eq(rho, u) - w_i = w_i [(rho - 1) + rho (3 xi.u + 9/2 (xi.u)^2 - 3/2 u.u)]
+template <int Q, class R>
+__device__ __forceinline__ R geq_i(int i, R drho, R rho, const Vec3<R>& u, R uu) {
+  R cu = xi_dot<Q>(i, u);
+  return R(Lat<Q>::w(i)) * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
 }
 
 // symmetric 3x3 tensor (xx, yy, zz, xy, xz, yz)

@@ -22,10 +22,13 @@ struct PrimalArgs {
   double u_in;        // inflow velocity
   double us[3];       // solid velocity u_s
   double nu0;         // molecular viscosity (tau0 - 1/2)/3
+  float tau0_f, kles_f, u_in_f, us_f[3], nu0_f;  // the same in float for FP32 kernels
   // averaging (only read when the ACC variant runs)
-  double* fsum;       // q x N running sum of f
+  double* msum;       // (1 + D) x N running sums of rho - 1 and rho u (moments of f)
+  double* fsum;       // q x N running sum of f - w (only with the full-f variant)
   double* tsum;       // N running sum of tau_eff - tau0 (LES only)
-  double* gsum[2];    // q x N running sums of dJ/df (FFA, DISS); may be null
+  double* gsum[2];    // ncoef(obj) x N running sums of the coefficients of dJ/df
+                      // in the basis of coef_basis() (FFA, DISS); may be null
   double* ddsum[2];   // N running sums of dJ/dd
   double* jblk[2];    // per-block running sums of J
   int obj_mask;
@@ -34,9 +37,41 @@ struct PrimalArgs {
   unsigned* err;      // bit 0: non-finite or non-positive density
 };
 
-// launch one primal step kernel; storage 0..3, odd/les/acc select variants
-cudaError_t launch_primal(const PrimalArgs& a, int q, int storage, bool odd, bool les, bool acc,
+// Every objective's dJ/df_j is a polynomial of degree <= 2 in the lattice
+// velocity xi_j: dJ/df_j = sum_k c_k b_k(xi_j) with the basis
+//   FFA:  b = (1, x)                                  -> 2 coefficients
+//   DISS: b = (1, x, y[, z], x^2, y^2[, z^2], 2xy[, 2xz, 2yz])  -> 6 (2D) / 10 (3D)
+// Averaging the coefficients is averaging dJ/df (the map is linear).
+__host__ __device__ constexpr int ncoef(int obj_slot, int D) {
+  return obj_slot == 0 ? 2 : 1 + D + D * (D + 1) / 2;
+}
+__host__ __device__ inline double coef_basis(int obj_slot, int D, int k, int x, int y, int z) {
+  if (obj_slot == 0) return k == 0 ? 1.0 : (double)x;
+  if (k == 0) return 1.0;
+  if (k <= D) return (double)(k == 1 ? x : (k == 2 ? y : z));
+  k -= D + 1;
+  if (k < D) return (double)(k == 0 ? x * x : (k == 1 ? y * y : z * z));
+  k -= D;
+  if (D == 2) return 2.0 * x * y;
+  return 2.0 * (k == 0 ? x * y : (k == 1 ? x * z : y * z));
+}
+
+// launch one primal step kernel; storage 0..3, odd/les select variants,
+// acc: 0 no averaging, 1 averages of moments and coefficients, 2 also of f
+cudaError_t launch_primal(const PrimalArgs& a, int q, int storage, bool odd, bool les, int acc,
                           cudaStream_t s);
+// out[k] (k < q, per cell) = scale * sum_c coef[c] b_c(xi_k): expand coefficient sums
+cudaError_t launch_expand_coef(const double* coef, int obj_slot, int q, long long N, double scale,
+                               double* out, cudaStream_t s);
+// coef = P g with P (ncoef x q, row-major) the least-squares inverse of the basis
+cudaError_t launch_project_coef(const double* g, const double* Pmat, int obj_slot, int q,
+                                long long N, double* coef, cudaStream_t s);
+// fsum = f - w and msum = (rho - 1, rho u) of the q x N field f (a set f_bar)
+cudaError_t launch_set_fbar(const double* f, int q, long long N, double* fsum, double* msum,
+                            cudaStream_t s);
+// out = fsum * scale + w (readout of f_bar)
+cudaError_t launch_fbar_out(const double* fsum, int q, long long N, double scale, double* out,
+                            cudaStream_t s);
 
 // readout of the canonical state: f (q x N), rho (N), u (3 x N); any may be null
 cudaError_t launch_readout(const void* f, const void* d, const Grid& g, int q, int storage,
@@ -63,10 +98,11 @@ cudaError_t launch_fill_real(void* v, bool dbl, long long n, double value, cudaS
 // adjoint
 // --------------------------------------------------------------------------
 struct PrepArgs {
-  const double* fsum;  // q x N
+  const double* fsum;  // q x N sums of f - w (EXACT with LES)
+  const double* msum;  // (1 + D) x N sums of rho - 1, rho u (BGK / FTA)
   const double* tsum;  // N (FTA with LES) or null
   double inv_n;        // 1 / number of samples
-  void* rec;           // real planes: BGK/FTA (rho, ux, uy[, uz], omega); EXACT: q planes of f_bar
+  void* rec;           // real planes: BGK/FTA (rho, ux, uy[, uz], omega); EXACT: q planes of f_bar - w
   long long rec_pitch;
   Grid g;
   double tau_b;        // tau0 or tau_adj
@@ -75,7 +111,8 @@ struct PrepArgs {
 cudaError_t launch_prep(const PrepArgs& a, int q, bool dbl, cudaStream_t s);
 
 struct SourceArgs {
-  const double* gsum;  // q x N
+  const double* gsum;  // ncoef x N coefficient sums
+  int obj_slot;        // 0 FFA, 1 DISS
   double inv_n;
   void* src;           // real, q planes of box volume
   int box[6];
@@ -92,6 +129,7 @@ struct AdjointArgs {
   long long rec_pitch;
   double tau_b, kles;
   double us[3];
+  float tau_b_f, kles_f, us_f[3];
   const void* src;     // g_bar restricted to the source box (real)
   int sb[6];
   long long src_pitch;
@@ -111,6 +149,7 @@ struct GradArgs {
   long long rec_pitch;
   double tau_b, kles;
   double us[3];
+  float tau_b_f, kles_f, us_f[3];
   const double* ddsum; // N, may be null
   double inv_n;
   int box[6];          // design box

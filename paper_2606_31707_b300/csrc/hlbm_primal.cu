@@ -15,91 +15,117 @@
 
 namespace hlbm {
 
+// deviation of the equilibrium g^eq_i = f^eq_i(rho, u) - w_i for all i
 template <int Q, class R>
-__device__ __forceinline__ void equilibrium(R (&f)[Q], R rho, const Vec3<R>& u) {
+__device__ __forceinline__ void equilibrium_dev(R (&g)[Q], R drho, const Vec3<R>& u) {
   const R uu = dot3(u, u);
+  const R rho = R(1) + drho;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) f[i] = feq_i<Q>(i, rho, u, uu);
+  for (int i = 0; i < Q; ++i) g[i] = geq_i<Q>(i, drho, rho, u, uu);
 }
 
-// Collide the canonical state f of one cell, store it AA-style, and (ACC)
-// add the cell's samples to the running averages.  Returns the velocity.
-template <int Q, int S, bool ODD, bool LES, bool ACC>
+// Collide the canonical state of one cell (as deviations g = f - w), store it
+// AA-style, and (ACC > 0) add the cell's samples to the running averages.
+// Returns the velocity.
+//
+// Averages kept (Sec. 3.3 and App. A: what the mean-flow adjoint reads):
+//   rho - 1 and rho u of f (the BGK / frozen-turbulence linearisation needs
+//   only the density and velocity of f_bar), all of f - w when ACC == 2 (the
+//   exact LES linearisation needs f_bar itself), tau_eff - tau0 (LES), and per
+//   objective the coefficients of dJ/df in the basis of coef_basis(), dJ/dd
+//   and J.
+template <int Q, int S, bool ODD, bool LES, int ACC>
 __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
     const PrimalArgs& a, typename Store<S>::mem* A, int x, int y, int z, long long cell,
-    typename Store<S>::real (&f)[Q], typename Store<S>::real d, double (&jp)[2]) {
+    typename Store<S>::real (&g)[Q], typename Store<S>::real d, double (&jp)[2]) {
   using R = typename Store<S>::real;
   using L = Lat<Q>;
-  const Grid& g = a.g;
-  R rho;
-  Vec3<R> u;
-  moments<Q>(f, rho, u);
-  if (!(rho > R(0)) || !(fabs((double)u.x) + fabs((double)u.y) + fabs((double)u.z) < 1e30))
-    atomicOr(a.err, 1u);
+  constexpr int D = L::D;
+  const Grid& gr = a.g;
+  R drho, rho;
+  Vec3<R> m, u;
+  moments_dev<Q>(g, drho, rho, m, u);
+  if (!(rho > R(0)) || !(fabs(u.x) + fabs(u.y) + fabs(u.z) < R(1e30))) atomicOr(a.err, 1u);
+  const Vec3<R> us{par<R>(a.us[0], a.us_f[0]), par<R>(a.us[1], a.us_f[1]),
+                   par<R>(a.us[2], a.us_f[2])};
   const R one_d = R(1) - d;
-  const Vec3<R> ut{d * u.x + one_d * R(a.us[0]), d * u.y + one_d * R(a.us[1]),
-                   d * u.z + one_d * R(a.us[2])};
+  const Vec3<R> ut{d * u.x + one_d * us.x, d * u.y + one_d * us.y, d * u.z + one_d * us.z};
   const R uu = dot3(ut, ut);
   R fneq[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) fneq[i] = f[i] - feq_i<Q>(i, rho, ut, uu);
+  for (int i = 0; i < Q; ++i) fneq[i] = g[i] - geq_i<Q>(i, drho, rho, ut, uu);
 
-  const R tau0 = R(a.tau0);
+  const R tau0 = par<R>(a.tau0, a.tau0_f);
   R tau = tau0;
   Sym<R> P{0, 0, 0, 0, 0, 0};
   R nP = 0;
-  const bool diss_here = ACC && (a.obj_mask & 2) && x >= a.db[0] && x < a.db[1] &&
+  const bool diss_here = ACC > 0 && (a.obj_mask & 2) && x >= a.db[0] && x < a.db[1] &&
                          y >= a.db[2] && y < a.db[3] && z >= a.db[4] && z < a.db[5];
   if (LES || diss_here) {
     P = second_moment<Q>(fneq);
     nP = sqrt_r<R>(sym_norm2(P));
   }
-  if (LES) tau = tau_smagorinsky<R>(tau0, R(a.kles), nP);
+  const R kles = par<R>(a.kles, a.kles_f);
+  if (LES) tau = tau_smagorinsky<R>(tau0, kles, nP);
   const R om = R(1) / tau;
 
-  if (ACC) {
-    const long long N = g.N;
+  if constexpr (ACC > 0) {
+    const long long N = gr.N;
+    a.msum[cell] += (double)drho;
+    a.msum[N + cell] += (double)m.x;
+    a.msum[2 * N + cell] += (double)m.y;
+    if (D == 3) a.msum[3 * N + cell] += (double)m.z;
+    if constexpr (ACC == 2) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) a.fsum[(long long)i * N + cell] += (double)f[i];
+      for (int i = 0; i < Q; ++i) a.fsum[(long long)i * N + cell] += (double)g[i];
+    }
     if (LES) a.tsum[cell] += (double)(tau - tau0);
-    // far-field drag J_FFA on Gamma_J (Sec. 4.2): rho u_x (u0 - u_x) + c_s^2 (1 - rho)
+    // far-field drag J_FFA on Gamma_J (Sec. 4.2): rho u_x (u0 - u_x) + c_s^2 (1 - rho);
+    // dJ/df_j = (u_x^2 - c_s^2) + (u0 - 2 u_x) xi_jx
     if ((a.obj_mask & 1) && x == a.ffa[0] && y >= a.ffa[1] && y < a.ffa[2] && z >= a.ffa[3] &&
         z < a.ffa[4]) {
-      const R u0 = R(a.u_in);
-      const R c0 = u.x * u.x - R(1.0 / 3.0);
-      const R c1 = u0 - R(2) * u.x;
+      const R u0 = par<R>(a.u_in, a.u_in_f);
       double* gs = a.gsum[0];
-#pragma unroll
-      for (int i = 0; i < Q; ++i)
-        gs[(long long)i * N + cell] += (double)(c0 + (L::cx(i) > 0 ? c1 : (L::cx(i) < 0 ? -c1 : R(0))));
-      jp[0] += (double)(rho * u.x * (u0 - u.x) + R(1.0 / 3.0) * (R(1) - rho));
+      gs[cell] += (double)(u.x * u.x - R(1.0 / 3.0));
+      gs[N + cell] += (double)(u0 - R(2) * u.x);
+      jp[0] += (double)(m.x * (u0 - u.x) - R(1.0 / 3.0) * drho);
     }
     // dissipation J_DISS on Omega_J (Sec. 4.3): 2 nu S:S + (1-d)/tau0 u.u,
-    // S = -3 Pi / (2 tau):  J = (9 nu / 2) |Pi|^2 / tau^2 + (1-d)/tau0 |u|^2
+    // S = -3 Pi / (2 tau):  J = (9 nu / 2) |Pi|^2 / tau^2 + (1-d)/tau0 |u|^2.
+    // dJ/df_j = fac Pi:dPi/df_j + c2 (xi_j.u - |u|^2) with
+    // Pi:dPi/df_j = xi_j Pi xi_j - tr Pi / 3 - u~ Pi u~ - 2 d (xi_j - u) . Pi u~,
+    // i.e. coefficients (1, xi, xi xi) = (A0, A, fac Pi).
     if (diss_here) {
-      const R nu = R(a.nu0);
-      const R PP = nP * nP;
+      const R nu = par<R>(a.nu0, a.nu0_f);
       const R uu_raw = dot3(u, u);
-      const R J = R(4.5) * nu * PP / (tau * tau) + one_d / tau0 * uu_raw;
-      // d/dq of |Pi|^2 / tau^2 with tau(|Pi|): 2 Pi:dPi [1/tau^2 - |Pi| k/(tau^3 (2 tau - tau0))]
+      const R J = R(4.5) * nu * nP * nP / (tau * tau) + one_d / tau0 * uu_raw;
+      // d(|Pi|^2 / tau^2) with tau(|Pi|): 2 Pi:dPi [1/tau^2 - |Pi| k/(tau^3 (2 tau - tau0))]
       R fac = R(1) / (tau * tau);
-      if (LES) fac -= nP * R(a.kles) / (tau * tau * tau * (R(2) * tau - tau0));
+      if (LES) fac -= nP * kles / (tau * tau * tau * (R(2) * tau - tau0));
       fac *= R(9) * nu;
       const Vec3<R> PU = sym_mul(P, ut);
       const R uPu = dot3(ut, PU);
       const R trP = P.xx + P.yy + P.zz;
       const R uPU = dot3(u, PU);
-      const R inv_rho = R(1) / rho;
-      const R c2 = one_d / tau0 * R(2) * inv_rho;
+      const R c2 = one_d / tau0 * R(2) / rho;
       double* gs = a.gsum[1];
-#pragma unroll
-      for (int j = 0; j < Q; ++j) {
-        // Pi : dPi/df_j = xi P xi - tr P / 3 - u~ P u~ - 2 d (xi_j - u) . P u~
-        const R pdp = xi_P_xi<Q>(j, P) - trP * R(1.0 / 3.0) - uPu - R(2) * d * (xi_dot<Q>(j, PU) - uPU);
-        const R dJ = fac * pdp + c2 * (xi_dot<Q>(j, u) - uu_raw);
-        gs[(long long)j * N + cell] += (double)dJ;
+      gs[cell] += (double)(fac * (-trP * R(1.0 / 3.0) - uPu + R(2) * d * uPU) - c2 * uu_raw);
+      gs[N + cell] += (double)(-R(2) * d * fac * PU.x + c2 * u.x);
+      gs[2 * N + cell] += (double)(-R(2) * d * fac * PU.y + c2 * u.y);
+      if (D == 2) {
+        gs[3 * N + cell] += (double)(fac * P.xx);
+        gs[4 * N + cell] += (double)(fac * P.yy);
+        gs[5 * N + cell] += (double)(fac * P.xy);
+      } else {
+        gs[3 * N + cell] += (double)(-R(2) * d * fac * PU.z + c2 * u.z);
+        gs[4 * N + cell] += (double)(fac * P.xx);
+        gs[5 * N + cell] += (double)(fac * P.yy);
+        gs[6 * N + cell] += (double)(fac * P.zz);
+        gs[7 * N + cell] += (double)(fac * P.xy);
+        gs[8 * N + cell] += (double)(fac * P.xz);
+        gs[9 * N + cell] += (double)(fac * P.yz);
       }
-      const Vec3<R> v{u.x - R(a.us[0]), u.y - R(a.us[1]), u.z - R(a.us[2])};
+      const Vec3<R> v{u.x - us.x, u.y - us.y, u.z - us.z};
       const R dd = fac * (-R(2) * rho * dot3(v, PU)) - uu_raw / tau0;
       a.ddsum[1][cell] += (double)dd;
       jp[1] += (double)J;
@@ -107,65 +133,63 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
   }
 
 #pragma unroll
-  for (int i = 0; i < Q; ++i) f[i] -= om * fneq[i];
-  aa_store<Q, S, ODD, +1>(A, g, x, y, z, cell, f);
+  for (int i = 0; i < Q; ++i) g[i] -= om * fneq[i];
+  aa_store<Q, S, ODD, +1>(A, gr, x, y, z, cell, g);
   return u;
 }
 
-template <int Q, int S, bool ODD, bool LES, bool ACC>
+template <int Q, int S, bool ODD, bool LES, int ACC>
 __global__ void __launch_bounds__(NT) k_primal(PrimalArgs a) {
   using St = Store<S>;
   using R = typename St::real;
-  const Grid& g = a.g;
+  const Grid& gr = a.g;
   const int x = blockIdx.x * NT + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
   auto* A = static_cast<typename St::mem*>(a.f);
   const R* dp = static_cast<const R*>(a.d);
   double jp[2] = {0.0, 0.0};
-  if (x < g.nx - 1) {
-    const long long cell = cell_of(g, x, y, z);
-    R f[Q];
+  if (x < gr.nx - 1) {
+    const long long cell = cell_of(gr, x, y, z);
+    R g[Q];
     if (x == 0) {
-      equilibrium<Q, R>(f, R(1), Vec3<R>{R(a.u_in), R(0), R(0)});
+      equilibrium_dev<Q, R>(g, R(0), Vec3<R>{par<R>(a.u_in, a.u_in_f), R(0), R(0)});
     } else {
-      aa_load<Q, S, ODD, +1>(A, g, x, y, z, cell, f);
+      aa_load<Q, S, ODD, +1>(A, gr, x, y, z, cell, g);
     }
-    const Vec3<R> u = cell_update<Q, S, ODD, LES, ACC>(a, A, x, y, z, cell, f, dp[cell], jp);
-    if (x == g.nx - 2) {
+    const Vec3<R> u = cell_update<Q, S, ODD, LES, ACC>(a, A, x, y, z, cell, g, dp[cell], jp);
+    if (x == gr.nx - 2) {
       // outflow node: f^eq(1, u(nx-2)), then relaxed and streamed like any cell
-      R fo[Q];
-      equilibrium<Q, R>(fo, R(1), u);
-      cell_update<Q, S, ODD, LES, ACC>(a, A, x + 1, y, z, cell + 1, fo, dp[cell + 1], jp);
+      R go[Q];
+      equilibrium_dev<Q, R>(go, R(0), u);
+      cell_update<Q, S, ODD, LES, ACC>(a, A, x + 1, y, z, cell + 1, go, dp[cell + 1], jp);
     }
   }
-  if (ACC) {
+  if constexpr (ACC > 0) {
     __shared__ double sh[NT / 32];
 #pragma unroll
     for (int o = 0; o < 2; ++o) {
       if (!(a.obj_mask & (1 << o))) continue;
-      const double s = block_sum<NT>(jp[o], sh);
-      if (threadIdx.x == 0) a.jblk[o][block_linear()] += s;
+      const double sm = block_sum<NT>(jp[o], sh);
+      if (threadIdx.x == 0) a.jblk[o][block_linear()] += sm;
     }
   }
 }
 
 template <int Q, int S>
-static cudaError_t launch_primal_qs(const PrimalArgs& a, bool odd, bool les, bool acc,
+static cudaError_t launch_primal_qs(const PrimalArgs& a, bool odd, bool les, int acc,
                                     cudaStream_t s) {
   dim3 grid((a.g.nx + NT - 1) / NT, a.g.ny, a.g.nz);
 #define HLBM_L(O, L_, A_) k_primal<Q, S, O, L_, A_><<<grid, NT, 0, s>>>(a)
-  if (!odd) {
-    if (!les) { if (!acc) HLBM_L(false, false, false); else HLBM_L(false, false, true); }
-    else      { if (!acc) HLBM_L(false, true, false);  else HLBM_L(false, true, true); }
-  } else {
-    if (!les) { if (!acc) HLBM_L(true, false, false);  else HLBM_L(true, false, true); }
-    else      { if (!acc) HLBM_L(true, true, false);   else HLBM_L(true, true, true); }
-  }
+#define HLBM_LA(O, L_) \
+  do { if (acc == 0) HLBM_L(O, L_, 0); else if (acc == 1) HLBM_L(O, L_, 1); else HLBM_L(O, L_, 2); } while (0)
+  if (!odd) { if (!les) HLBM_LA(false, false); else HLBM_LA(false, true); }
+  else      { if (!les) HLBM_LA(true, false);  else HLBM_LA(true, true); }
+#undef HLBM_LA
 #undef HLBM_L
   return cudaGetLastError();
 }
 
-cudaError_t launch_primal(const PrimalArgs& a, int q, int storage, bool odd, bool les, bool acc,
+cudaError_t launch_primal(const PrimalArgs& a, int q, int storage, bool odd, bool les, int acc,
                           cudaStream_t s) {
   if (q == 9) {
     switch (storage) {
@@ -189,78 +213,78 @@ cudaError_t launch_primal(const PrimalArgs& a, int q, int storage, bool odd, boo
 // state readout / initialisation
 // ----------------------------------------------------------------------------
 template <int Q, int S, bool ODD>
-__global__ void __launch_bounds__(NT) k_readout(const void* fv, Grid g, double u_in, double* fout,
+__global__ void __launch_bounds__(NT) k_readout(const void* fv, Grid gr, double u_in, double* fout,
                                                 double* rho_out, double* u_out) {
   using St = Store<S>;
   using R = typename St::real;
   const int x = blockIdx.x * NT + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
-  if (x >= g.nx) return;
+  if (x >= gr.nx) return;
   const auto* A = static_cast<const typename St::mem*>(fv);
-  const long long cell = cell_of(g, x, y, z);
-  R f[Q];
+  const long long cell = cell_of(gr, x, y, z);
+  R g[Q];
   if (x == 0) {
-    equilibrium<Q, R>(f, R(1), Vec3<R>{R(u_in), R(0), R(0)});
-  } else if (x == g.nx - 1) {
-    R fi[Q];
-    aa_load<Q, S, ODD, +1>(A, g, x - 1, y, z, cell - 1, fi);
-    R r;
-    Vec3<R> u;
-    moments<Q>(fi, r, u);
-    equilibrium<Q, R>(f, R(1), u);
+    equilibrium_dev<Q, R>(g, R(0), Vec3<R>{R(u_in), R(0), R(0)});
+  } else if (x == gr.nx - 1) {
+    R gi[Q];
+    aa_load<Q, S, ODD, +1>(A, gr, x - 1, y, z, cell - 1, gi);
+    R dr, r;
+    Vec3<R> m, u;
+    moments_dev<Q>(gi, dr, r, m, u);
+    equilibrium_dev<Q, R>(g, R(0), u);
   } else {
-    aa_load<Q, S, ODD, +1>(A, g, x, y, z, cell, f);
+    aa_load<Q, S, ODD, +1>(A, gr, x, y, z, cell, g);
   }
   if (fout) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fout[(long long)i * g.N + cell] = (double)f[i];
+    for (int i = 0; i < Q; ++i) fout[(long long)i * gr.N + cell] = (double)g[i] + Lat<Q>::w(i);
   }
   if (rho_out || u_out) {
-    R r;
-    Vec3<R> u;
-    moments<Q>(f, r, u);
-    if (rho_out) rho_out[cell] = (double)r;
+    R dr, r;
+    Vec3<R> m, u;
+    moments_dev<Q>(g, dr, r, m, u);
+    if (rho_out) rho_out[cell] = 1.0 + (double)dr;
     if (u_out) {
       u_out[cell] = (double)u.x;
-      u_out[g.N + cell] = (double)u.y;
-      if (Lat<Q>::D == 3) u_out[2 * g.N + cell] = (double)u.z;
+      u_out[gr.N + cell] = (double)u.y;
+      if (Lat<Q>::D == 3) u_out[2 * gr.N + cell] = (double)u.z;
     }
   }
 }
 
 template <int Q, int S>
-__global__ void __launch_bounds__(NT) k_set_state(void* fv, Grid g, const double* in) {
+__global__ void __launch_bounds__(NT) k_set_state(void* fv, Grid gr, const double* in) {
   using St = Store<S>;
   const int x = blockIdx.x * NT + threadIdx.x;
-  if (x >= g.nx) return;
-  const long long cell = cell_of(g, x, blockIdx.y, blockIdx.z);
+  if (x >= gr.nx) return;
+  const long long cell = cell_of(gr, x, blockIdx.y, blockIdx.z);
   auto* A = static_cast<typename St::mem*>(fv);
 #pragma unroll
   for (int i = 0; i < Q; ++i)
-    St::st(A + (long long)i * g.pitch + cell, (typename St::real)in[(long long)i * g.N + cell],
-           Lat<Q>::w(i));
+    St::st(A + (long long)i * gr.pitch + cell,
+           (typename St::real)(in[(long long)i * gr.N + cell] - Lat<Q>::w(i)));
 }
 
 template <int Q, int S>
-__global__ void __launch_bounds__(NT) k_init_eq(void* fv, Grid g, const double* rho,
+__global__ void __launch_bounds__(NT) k_init_eq(void* fv, Grid gr, const double* rho,
                                                 const double* u, double u_in) {
   using St = Store<S>;
   using R = typename St::real;
   const int x = blockIdx.x * NT + threadIdx.x;
-  if (x >= g.nx) return;
-  const long long cell = cell_of(g, x, blockIdx.y, blockIdx.z);
+  if (x >= gr.nx) return;
+  const long long cell = cell_of(gr, x, blockIdx.y, blockIdx.z);
   auto* A = static_cast<typename St::mem*>(fv);
-  R r = rho ? (R)rho[cell] : R(1);
+  R dr = rho ? (R)(rho[cell] - 1.0) : R(0);
   Vec3<R> v{R(u_in), R(0), R(0)};
   if (u) {
     v.x = (R)u[cell];
-    v.y = (R)u[g.N + cell];
-    v.z = Lat<Q>::D == 3 ? (R)u[2 * g.N + cell] : R(0);
+    v.y = (R)u[gr.N + cell];
+    v.z = Lat<Q>::D == 3 ? (R)u[2 * gr.N + cell] : R(0);
   }
-  R f[Q];
-  equilibrium<Q, R>(f, r, v);
+  R g[Q];
+  equilibrium_dev<Q, R>(g, dr, v);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) St::st(A + (long long)i * g.pitch + cell, f[i], Lat<Q>::w(i));
+  for (int i = 0; i < Q; ++i) St::st(A + (long long)i * gr.pitch + cell, g[i]);
 }
 
 #define HLBM_DISPATCH_QS(q, storage, CALL)                                  \
@@ -382,12 +406,117 @@ cudaError_t launch_scale(double* v, long long n, double s_, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// out[k][cell] = scale * sum_c coef[c][cell] b_c(xi_k)
+template <int Q>
+__global__ void k_expand_coef(const double* coef, int obj_slot, long long N, double scale,
+                              double* out) {
+  constexpr int D = Lat<Q>::D;
+  const int nc = ncoef(obj_slot, D);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    double cf[10];
+    for (int k = 0; k < nc; ++k) cf[k] = coef[(long long)k * N + c];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      double v = 0.0;
+      for (int k = 0; k < nc; ++k)
+        v += cf[k] * coef_basis(obj_slot, D, k, Lat<Q>::cx(i), Lat<Q>::cy(i), Lat<Q>::cz(i));
+      out[(long long)i * N + c] = scale * v;
+    }
+  }
+}
+
+struct ProjMat { double p[10 * 19]; };
+
+template <int Q>
+__global__ void k_project_coef(const double* gin, ProjMat P, int obj_slot, long long N,
+                               double* coef) {
+  constexpr int D = Lat<Q>::D;
+  const int nc = ncoef(obj_slot, D);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    double gv[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) gv[i] = gin[(long long)i * N + c];
+    for (int k = 0; k < nc; ++k) {
+      double v = 0.0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) v += P.p[k * Q + i] * gv[i];
+      coef[(long long)k * N + c] = v;
+    }
+  }
+}
+
+template <int Q>
+__global__ void k_set_fbar(const double* f, long long N, double* fsum, double* msum) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    double gv[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      gv[i] = f[(long long)i * N + c] - Lat<Q>::w(i);
+      fsum[(long long)i * N + c] = gv[i];
+    }
+    double dr, r;
+    Vec3<double> m, u;
+    moments_dev<Q, double>(gv, dr, r, m, u);
+    msum[c] = dr;
+    msum[N + c] = m.x;
+    msum[2 * N + c] = m.y;
+    if (Lat<Q>::D == 3) msum[3 * N + c] = m.z;
+  }
+}
+
+template <int Q>
+__global__ void k_fbar_out(const double* fsum, long long N, double scale, double* out) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) out[(long long)i * N + c] = fsum[(long long)i * N + c] * scale + Lat<Q>::w(i);
+  }
+}
+
 template <class R>
 __global__ void k_fill(R* v, long long n, R value) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x)
     v[k] = value;
 }
+cudaError_t launch_expand_coef(const double* coef, int obj_slot, int q, long long N, double scale,
+                               double* out, cudaStream_t s) {
+  if (q == 9) k_expand_coef<9><<<util_blocks(N), 256, 0, s>>>(coef, obj_slot, N, scale, out);
+  else if (q == 19) k_expand_coef<19><<<util_blocks(N), 256, 0, s>>>(coef, obj_slot, N, scale, out);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_coef(const double* g, const double* Pmat, int obj_slot, int q,
+                                long long N, double* coef, cudaStream_t s) {
+  ProjMat P{};
+  const int nc = ncoef(obj_slot, q == 9 ? 2 : 3);
+  for (int k = 0; k < nc * q; ++k) P.p[k] = Pmat[k];
+  if (q == 9) k_project_coef<9><<<util_blocks(N), 256, 0, s>>>(g, P, obj_slot, N, coef);
+  else if (q == 19) k_project_coef<19><<<util_blocks(N), 256, 0, s>>>(g, P, obj_slot, N, coef);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_fbar(const double* f, int q, long long N, double* fsum, double* msum,
+                            cudaStream_t s) {
+  if (q == 9) k_set_fbar<9><<<util_blocks(N), 256, 0, s>>>(f, N, fsum, msum);
+  else if (q == 19) k_set_fbar<19><<<util_blocks(N), 256, 0, s>>>(f, N, fsum, msum);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fbar_out(const double* fsum, int q, long long N, double scale, double* out,
+                            cudaStream_t s) {
+  if (q == 9) k_fbar_out<9><<<util_blocks(N), 256, 0, s>>>(fsum, N, scale, out);
+  else if (q == 19) k_fbar_out<19><<<util_blocks(N), 256, 0, s>>>(fsum, N, scale, out);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill_real(void* v, bool dbl, long long n, double value, cudaStream_t s) {
   if (dbl) k_fill<double><<<util_blocks(n), 256, 0, s>>>((double*)v, n, value);
   else k_fill<float><<<util_blocks(n), 256, 0, s>>>((float*)v, n, (float)value);

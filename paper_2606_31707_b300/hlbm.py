@@ -51,6 +51,7 @@ class hlbm_options(C.Structure):
         ("design_box", C.c_int * 6),
         ("accum_stride", C.c_int),
         ("check_every", C.c_int),
+        ("average_full_f", C.c_int),
         ("stream", C.c_void_p),
         ("dev_alloc", _ALLOC),
         ("dev_free", _FREE),

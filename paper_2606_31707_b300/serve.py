@@ -1,0 +1,174 @@
+"""Continuous-batching server for mean-flow sensitivity requests.
+
+A request is one whole Algorithm-1 solve (primal with averages, adjoint,
+gradient) on its own grid and porosity field.  The server keeps a fixed
+number of slots; a request is admitted as soon as a slot is free and its
+device footprint fits the HBM budget, so requests that arrive while others
+run join immediately and their kernels overlap on the GPU (each slot owns a
+context and a CUDA stream, driven by its own host thread; the C ABI releases
+the GIL).  All state of a request stays on the device until its gradient is
+copied out.  Every reduction in the library is per request and in a fixed
+order, so a result does not depend on what else is running.
+
+This module is orchestration only: every arithmetic step runs in the CUDA
+library.
+"""
+from __future__ import annotations
+
+import queue
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import hlbm as H
+from .solver import Solver
+
+
+@dataclass
+class Request:
+    q: int
+    dims: Sequence[int]
+    tau: float
+    porosity: np.ndarray                 # (nz, ny, nx)
+    u_in: float = 0.05
+    Cs: float = 0.0
+    warm_steps: int = 2000
+    avg_steps: int = 2000
+    objective: int = H.OBJ_DRAG_FFA
+    mode: int = H.ADJ_EXACT
+    tol: float = 1e-6
+    max_iter: int = 4000
+    storage: int = H.FP32
+    regions: object = None
+    tag: object = None
+    t_submit: float = 0.0
+
+
+@dataclass
+class Result:
+    tag: object
+    J: float
+    gradient: np.ndarray
+    adjoint_iters: int
+    adjoint_residual: float
+    status: int
+    latency_s: float
+    queued_s: float
+    lups: int
+
+
+def footprint_bytes(q: int, dims: Sequence[int], storage: int = H.FP32, objectives: int = 1) -> int:
+    """Device bytes one request holds (populations, averages, adjoint state)."""
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    pop = {H.FP64: 8, H.FP32: 4, H.FP16DEV: 2, H.BF16DEV: 2}[storage]
+    real = 8 if storage == H.FP64 else 4
+    D = 2 if q == 9 else 3
+    b = q * N * pop + N * real                       # populations, porosity
+    b += q * N * 8 + N * 8                           # sum f, sum tau
+    b += objectives * (q * N * 8 + N * 8)            # sum dJ/df, dJ/dd
+    b += 2 * q * N * real + q * N * real + (D + 2) * N * real  # lambda, snapshot, source, record
+    b += q * N * 8 * 2                               # staging for readouts
+    return int(b)
+
+
+class SensitivityServer:
+    """Admit requests into at most ``slots`` concurrent solves within
+    ``hbm_budget`` bytes; results are returned through futures."""
+
+    def __init__(self, slots: int = 8, hbm_budget: int = 200 << 30):
+        self.slots = slots
+        self.budget = hbm_budget
+        self._q: "queue.Queue[tuple]" = queue.Queue()
+        self._used = 0
+        self._active = 0
+        self._cv = threading.Condition()
+        self._stop = False
+        self._threads: List[threading.Thread] = []
+        self._sched = threading.Thread(target=self._schedule, daemon=True)
+        self._pending: List[tuple] = []
+        self.completed: List[Result] = []
+        self._sched.start()
+
+    # ------------------------------------------------------------------
+    def submit(self, req: Request) -> Future:
+        fut: Future = Future()
+        req.t_submit = time.perf_counter()
+        need = footprint_bytes(req.q, req.dims, req.storage)
+        if need > self.budget:
+            fut.set_exception(H.HlbmError(H.ENOMEM, "request larger than the HBM budget"))
+            return fut
+        with self._cv:
+            self._pending.append((req, fut, need))
+            self._cv.notify_all()
+        return fut
+
+    def close(self):
+        with self._cv:
+            self._stop = True
+            self._cv.notify_all()
+        self._sched.join()
+        for t in self._threads:
+            t.join()
+
+    # ------------------------------------------------------------------
+    def _schedule(self):
+        while True:
+            with self._cv:
+                while not self._stop and not self._admissible():
+                    self._cv.wait(timeout=0.05)
+                if self._stop and not self._pending:
+                    return
+                if not self._admissible():
+                    continue
+                # first-come first-served among requests that fit
+                k = next(i for i, (_, _, need) in enumerate(self._pending)
+                         if self._used + need <= self.budget)
+                req, fut, need = self._pending.pop(k)
+                self._used += need
+                self._active += 1
+            t = threading.Thread(target=self._run, args=(req, fut, need), daemon=True)
+            t.start()
+            self._threads.append(t)
+
+    def _admissible(self) -> bool:
+        if self._active >= self.slots or not self._pending:
+            return False
+        return any(self._used + need <= self.budget for _, _, need in self._pending)
+
+    def _run(self, req: Request, fut: Future, need: int):
+        t0 = time.perf_counter()
+        try:
+            res = solve_one(req)
+            res.queued_s = t0 - req.t_submit
+            res.latency_s = time.perf_counter() - req.t_submit
+            self.completed.append(res)
+            fut.set_result(res)
+        except Exception as e:  # noqa: BLE001 - forwarded to the caller
+            fut.set_exception(e)
+        finally:
+            with self._cv:
+                self._used -= need
+                self._active -= 1
+                self._cv.notify_all()
+
+
+def solve_one(req: Request) -> Result:
+    """Algorithm 1 for one request on its own context and stream."""
+    s = Solver(req.q, req.dims, req.tau, req.Cs, storage=req.storage, u_in=req.u_in,
+               regions=req.regions, objectives=req.objective)
+    try:
+        s.set_porosity(req.porosity)
+        steps = req.warm_steps + req.avg_steps
+        s.run_primal(steps, req.avg_steps)
+        J = s.objective(req.objective)
+        st, it, res = s.solve_adjoint(req.objective, req.mode, req.tol, req.max_iter)
+        G = s.gradient()
+        N = int(np.prod(req.dims))
+        return Result(req.tag, J, G, it, res, st, 0.0, 0.0, N * (steps + it))
+    finally:
+        s.close()

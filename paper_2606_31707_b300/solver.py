@@ -21,7 +21,7 @@ class Solver:
                  storage: int = H.FP32, u_in: float = 0.05, regions=None,
                  objectives: int = H.OBJ_DRAG_FFA | H.OBJ_DISSIPATION, tau_adj: float = 0.0,
                  accum_stride: int = 1, check_every: int = 100, stream=None,
-                 u_solid=(0.0, 0.0, 0.0)):
+                 u_solid=(0.0, 0.0, 0.0), average_full_f: bool = False):
         self.q = lattice
         self.dims = tuple(int(v) for v in dims)
         self.dim = 2 if lattice == 9 else 3
@@ -34,6 +34,7 @@ class Solver:
         opt.objectives = objectives
         opt.accum_stride = accum_stride
         opt.check_every = check_every
+        opt.average_full_f = int(average_full_f)
         if regions is not None:
             opt.ffa_x = regions.ffa_x
             opt.ffa_y0, opt.ffa_y1 = regions.ffa_y

@@ -1,0 +1,138 @@
+"""Parity at the benchmark workloads' full sizes, in the launch configuration
+the benchmark uses, on outputs the oracle can compute directly.
+
+* Kármán case (D2Q9 1100x410, FP32): primal steps, an averaging step, and
+  adjoint iterations from the same state, compared element by element over
+  the whole grid (the oracle does one step of this grid in well under a
+  second).
+* Steady Re-20 case (D2Q9 200x80, FP64): the whole of Algorithm 1 at its full
+  size, gradient compared with the oracle's direct adjoint solve.
+* LES case (D3Q19 640x320x100, FP32 and FP16 deviations): one primal step
+  checked on sampled sub-boxes, which the oracle recomputes from the same
+  state with a one-cell halo.
+"""
+import numpy as np
+import pytest
+
+from oracle import adjoint as oadj
+from oracle import hlbm as ohlbm
+from oracle import meanflow as omf
+from oracle import objectives as oobj
+from tests.hlbm_cases import direction_perm, params_of, rel_l2, to_lib
+from workloads import make_workload
+
+pytestmark = pytest.mark.gpu
+
+H = pytest.importorskip("paper_2606_31707_b300.hlbm")
+from paper_2606_31707_b300 import Solver  # noqa: E402
+
+
+def _state_near(P, wl, seed=5, amp=0.002):
+    rng = np.random.default_rng(seed)
+    u = np.zeros((3,) + P.shape)
+    u[0] = wl.u0 * (1 + 0.1 * rng.standard_normal(P.shape))
+    u[1] = 0.1 * wl.u0 * rng.standard_normal(P.shape)
+    if P.q == 19:
+        u[2] = 0.1 * wl.u0 * rng.standard_normal(P.shape)
+    f = ohlbm.equilibrium(np.ones(P.shape), u, P) * (1 + amp * rng.standard_normal((P.q,) + P.shape))
+    return ohlbm.apply_boundary(f, P)
+
+
+def test_karman_fullsize_primal_average_and_adjoint_iterations():
+    wl = make_workload("karman2d_re100")
+    P = params_of(wl)
+    f0 = _state_near(P, wl)
+    s = Solver(9, wl.dims, P.tau0, 0.0, storage=H.FP32, u_in=wl.u0, regions=wl.regions)
+    perm = direction_perm(s.xi, P)
+    s.set_porosity(wl.porosity)
+    s.set_field(H.FIELD_F, to_lib(f0, perm))
+    s.run_primal(3, 0)
+    f = f0
+    for _ in range(3):
+        f = ohlbm.step(f, wl.porosity, P)
+    assert rel_l2(s.field(H.FIELD_F), to_lib(f, perm)) <= 1e-6
+    # one averaging step from the state reached
+    s.set_field(H.FIELD_F, to_lib(f, perm))
+    s.run_primal(1, 1)
+    out = omf.run_primal(f, wl.porosity, P, 1, 1, wl.regions, 3)
+    for o, gf in ((oobj.FFA, H.FIELD_GBAR_FFA), (oobj.DISS, H.FIELD_GBAR_DISS)):
+        assert rel_l2(s.field(gf), to_lib(out[("gbar", o)], perm)) <= 1e-5
+        assert abs(s.objective(o) - out[("Jbar", o)]) <= 1e-5 * abs(out[("Jbar", o)])
+    # 20 adjoint iterations from zero on both sides, same averaged state
+    lin = oadj.Linearisation(out["fbar"], wl.porosity, P, oadj.EXACT)
+    for o in (oobj.FFA, oobj.DISS):
+        st, it, res = s.solve_adjoint(o, H.ADJ_EXACT, 0.0, 20)
+        assert it == 20
+        lam, _, _ = oadj.solve_adjoint(lin, out[("gbar", o)], tol=0.0, max_iter=20)
+        mu_ref = to_lib(lin.mu(lam), perm)
+        assert rel_l2(s.field(H.FIELD_LAMBDA), mu_ref) <= 1e-5
+        G = oadj.gradient(lin, lam, out[("dJdd_bar", o)])
+        assert rel_l2(s.gradient(), G) <= 1e-5
+    s.close()
+
+
+def test_cylinder_re20_fullsize_fp64_algorithm1():
+    wl = make_workload("cyl2d_re20")
+    P = params_of(wl)
+    s = Solver(9, wl.dims, P.tau0, 0.0, storage=H.FP64, u_in=wl.u0, regions=wl.regions)
+    s.set_porosity(wl.porosity)
+    s.run_primal(wl.steps - 1, 0)
+    perm = direction_perm(s.xi, P)
+    fbar = s.field(H.FIELD_F)[np.argsort(perm)]
+    s.run_primal(1, 1)
+    out = omf.run_primal(fbar, wl.porosity, P, 1, 1, wl.regions, 3)
+    lin = oadj.Linearisation(fbar, wl.porosity, P, oadj.EXACT)
+    for o in (oobj.FFA, oobj.DISS):
+        st, it, res = s.solve_adjoint(o, H.ADJ_EXACT, 1e-10, 2_000_000)
+        assert st == H.OK
+        lam = oadj.solve_adjoint_direct(lin, out[("gbar", o)])
+        G = oadj.gradient(lin, lam, out[("dJdd_bar", o)])
+        assert rel_l2(s.gradient(), G) <= 1e-8
+    # the GPU's own primal agrees with the oracle's primal over the full 6000 steps
+    f = ohlbm.initial_state(P)
+    for _ in range(wl.steps):
+        f = ohlbm.step(f, wl.porosity, P)
+    assert rel_l2(s.field(H.FIELD_F), to_lib(f, perm)) <= 1e-12
+    s.close()
+
+
+def _subbox_step(f, d, P, box):
+    """One oracle step on the sub-box (x0, x1, y0, y1, z0, z1) of an interior
+    region, computed from a one-cell halo of the given state."""
+    x0, x1, y0, y1, z0, z1 = box
+    sub = f[:, z0 - 1:z1 + 1, y0 - 1:y1 + 1, x0 - 1:x1 + 1]
+    dsub = d[z0 - 1:z1 + 1, y0 - 1:y1 + 1, x0 - 1:x1 + 1]
+    Ps = ohlbm.Params(P.q, (x1 - x0 + 2, y1 - y0 + 2, z1 - z0 + 2), tau0=P.tau0, Cs=P.Cs, u_in=P.u_in)
+    fs, _ = ohlbm.collide(sub, dsub, Ps)
+    st = ohlbm.stream(fs, Ps)
+    return st[:, 1:-1, 1:-1, 1:-1]
+
+
+@pytest.mark.parametrize("storage,tol", [(H.FP32, 1e-6), (H.FP16DEV, 2e-3)])
+def test_les_fullsize_primal_step_on_sampled_boxes(storage, tol):
+    wl = make_workload("les3d_re3900")
+    P = params_of(wl)
+    nx, ny, nz = wl.dims
+    rng = np.random.default_rng(9)
+    s = Solver(19, wl.dims, P.tau0, wl.Cs, storage=storage, u_in=wl.u0, regions=wl.regions)
+    perm = direction_perm(s.xi, P)
+    s.set_porosity(wl.porosity)
+    # a random smooth perturbed state built on the device side: equilibrium of a
+    # seeded velocity field, written through the ABI
+    u = np.zeros((3,) + P.shape)
+    u[0] = wl.u0
+    u[1] = 0.2 * wl.u0 * np.sin(2 * np.pi * np.arange(ny) / ny)[None, :, None]
+    u[2] = 0.1 * wl.u0 * rng.standard_normal(P.shape)
+    s.init_equilibrium(None, u)
+    s.run_primal(2, 0)                      # a non-equilibrium state
+    f = s.field(H.FIELD_F)[np.argsort(perm)]
+    s.set_field(H.FIELD_F, to_lib(f, perm))
+    s.run_primal(1, 0)
+    g = s.field(H.FIELD_F)[np.argsort(perm)]
+    boxes = [(150, 166, 150, 170, 40, 48), (300, 316, 10, 26, 3, 9), (600, 620, 290, 310, 90, 98)]
+    for box in boxes:
+        ref = _subbox_step(f, wl.porosity, P, box)
+        x0, x1, y0, y1, z0, z1 = box
+        assert rel_l2(g[:, z0:z1, y0:y1, x0:x1] - P.w[:, None, None, None],
+                      ref - P.w[:, None, None, None]) <= tol
+    s.close()

@@ -100,7 +100,8 @@ def test_primal_16bit_deviation_storage_bound(storage, tol):
 def test_averages_match_oracle(q, dims, Cs):
     P, d, R = _case(q, dims, Cs)
     f0 = _perturbed_state(P)
-    s = Solver(P.q, P.dims, P.tau0, P.Cs, storage=H.FP64, u_in=P.u_in, regions=R, accum_stride=2)
+    s = Solver(P.q, P.dims, P.tau0, P.Cs, storage=H.FP64, u_in=P.u_in, regions=R, accum_stride=2,
+               average_full_f=True)
     perm = direction_perm(s.xi, P)
     s.set_porosity(d)
     s.set_field(H.FIELD_F, to_lib(f0, perm))
@@ -126,11 +127,11 @@ def _steady_gpu_vs_oracle(q, dims, Cs, storage, objective, mode, tau_adj=None, s
     s = _solver(P, R, storage, tau_adj=tau_adj or 0.0)
     perm = direction_perm(s.xi, P)
     s.set_porosity(d)
-    s.run_primal(steps, 1)
-    # the oracle linearises at the same averaged state (kernel-level parity)
-    fbar_lib = s.field(H.FIELD_FBAR)
-    inv = np.argsort(perm)
-    fbar = fbar_lib[inv]
+    s.run_primal(steps - 1, 0)
+    # the oracle linearises at the same state (kernel-level parity): with a
+    # window of one step f_bar is the canonical state the last step starts from
+    fbar = s.field(H.FIELD_F)[np.argsort(perm)]
+    s.run_primal(1, 1)
     out = omf.run_primal(fbar, d, P, 1, 1, R, 3)
     lin = oadj.Linearisation(fbar, d, P, mode, tau_adj, out["tau_t_bar"])
     lam = oadj.solve_adjoint_direct(lin, out[("gbar", objective)])
@@ -184,6 +185,43 @@ def test_full_pipeline_steady_fp64_vs_oracle_gradient_sign_and_directional_fd():
     b = R.design_box
     assert rel_l2(Gg, ref["G"][b[4]:b[5], b[2]:b[3], b[0]:b[1]]) <= 1e-8
     assert abs(s.objective(oobj.DISS) - ref["out"][("Jbar", oobj.DISS)]) <= 1e-10 * abs(ref["out"][("Jbar", oobj.DISS)])
+    s.close()
+
+
+def test_compact_and_full_averages_agree_and_fbar_needs_full():
+    # BGK / FTA linearisations read only rho and rho u of f_bar; the full
+    # average of f is optional there and gives the same record
+    P, d, R = _case(9, (300, 24, 1), 0.0, tau=0.8, u_in=0.04)
+    Gs = []
+    for full in (False, True):
+        s = Solver(P.q, P.dims, P.tau0, P.Cs, storage=H.FP64, u_in=P.u_in, regions=R,
+                   average_full_f=full)
+        s.set_porosity(d)
+        s.run_primal(500, 100)
+        if not full:
+            with pytest.raises(H.HlbmError) as e:
+                s.field(H.FIELD_FBAR)
+            assert e.value.status == H.ESTATE
+        s.solve_adjoint(oobj.DISS, H.ADJ_EXACT, 1e-10, 100000)
+        Gs.append(s.gradient())
+        s.close()
+    assert np.array_equal(Gs[0], Gs[1])
+
+
+def test_set_gbar_is_projected_onto_the_derivative_form():
+    # a set dJ/df of the form every objective derivative has is kept exactly
+    P, d, R = _case(9, (300, 24, 1), 0.0)
+    f0 = _perturbed_state(P)
+    out = omf.run_primal(f0, d, P, 1, 1, R, 3)
+    s = _solver(P, R, H.FP64)
+    perm = direction_perm(s.xi, P)
+    s.set_porosity(d)
+    s.set_field(H.FIELD_FBAR, to_lib(out["fbar"], perm))
+    s.set_field(H.FIELD_GBAR_DISS, to_lib(out[("gbar", oobj.DISS)], perm))
+    s.set_field(H.FIELD_GBAR_FFA, to_lib(out[("gbar", oobj.FFA)], perm))
+    assert rel_l2(s.field(H.FIELD_GBAR_DISS), to_lib(out[("gbar", oobj.DISS)], perm)) <= 1e-13
+    assert rel_l2(s.field(H.FIELD_GBAR_FFA), to_lib(out[("gbar", oobj.FFA)], perm)) <= 1e-13
+    assert rel_l2(s.field(H.FIELD_FBAR), to_lib(out["fbar"], perm)) == 0.0
     s.close()
 
 
