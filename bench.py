@@ -43,6 +43,30 @@ from workloads import make_workload  # noqa: E402
 L2_BYTES = 126 * 2 ** 20
 CS2 = 1.0 / 3.0
 
+# DRAM bytes (read + write) per launch measured by ncu for the dominant kernels,
+# keyed by a hash of the kernel sources at capture time; a kernel changed since
+# its capture reports traffic null.  Summaries: profiles/*.md.
+MEASURED_DRAM = {
+    # profiles/k_primal_karman2d_re100.md (ncu --set full, 2 launches each parity)
+    ("291b05ef34e1616c", "karman2d_re100", "fp32", "primal_step_accumulate"): 31_829_000,
+    ("291b05ef34e1616c", "karman2d_re100", "fp32", "primal_step_plain"): 18_052_000,
+    # profiles/k_adjoint_karman2d_re100.md
+    ("291b05ef34e1616c", "karman2d_re100", "fp32", "adjoint_step_ffa"): 30_267_000,
+    ("291b05ef34e1616c", "karman2d_re100", "fp32", "adjoint_step_diss"): 30_267_000,
+}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2606_31707_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        # the translation units that define the hot-path kernels and their headers
+        if name in ("hlbm_primal.cu", "hlbm_adjoint.cu", "hlbm_device.cuh", "hlbm_internal.h"):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
 
 def tau_of(wl):
     # nu = u0 L / Re, tau = nu / c_s^2 + 1/2 (viscosity-relaxation relation)
@@ -60,9 +84,14 @@ def parse():
                     help="override the workload's primal step count (testing only)")
     ap.add_argument("--avg-window", type=int, default=None)
     ap.add_argument("--adjoint-tol", type=float, default=1e-6)
+    ap.add_argument("--adjoint-mode", default="exact", choices=["exact", "fta"])
+    ap.add_argument("--tau-adj", type=float, default=0.0,
+                    help="adjoint relaxation time (0: tau0), the regularisation of Sec. 5.4")
     ap.add_argument("--adjoint-max-iter", type=int, default=20000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage", default=None, choices=["fp64", "fp32", "fp16dev", "bf16dev"],
+                    help="population storage (default: the workload's)")
     return ap.parse_args()
 
 
@@ -188,11 +217,15 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     wl = make_workload(args.workload, seed=rank)
+    if args.storage:
+        import dataclasses
+        wl = dataclasses.replace(wl, storage=args.storage)
     steps, W = job_shape(wl, args)
     n_warm = steps - W
     stream = torch.cuda.Stream(device=dev)
     s = Solver(wl.q, wl.dims, tau_of(wl), wl.Cs, storage=storage_code(H, wl), u_in=wl.u0,
-               regions=wl.regions, stream=stream)
+               regions=wl.regions, stream=stream, tau_adj=args.tau_adj)
+    mode = H.ADJ_EXACT if args.adjoint_mode == "exact" else H.ADJ_FTA
     N = wl.cells
     D = 2 if wl.q == 9 else 3
     d_dev = torch.from_numpy(np.ascontiguousarray(wl.porosity.ravel())).to(dev)
@@ -234,7 +267,7 @@ def run_ours(args, rank, world):
         Js = []
         for k, o in enumerate(objectives):
             Js.append(s.objective(o))
-            _, it, res = s.solve_adjoint(o, H.ADJ_EXACT, args.adjoint_tol, args.adjoint_max_iter)
+            _, it, res = s.solve_adjoint(o, mode, args.adjoint_tol, args.adjoint_max_iter)
             st = s.stats()
             if record:
                 phase["adj_ms"][k] += st.adjoint_ms
@@ -302,7 +335,8 @@ def run_ours(args, rank, world):
 def roofline_of(res, args, H_storage_bytes, real_bytes):
     wl = res["wl"]
     N = wl.cells
-    bm = bytes_model(wl, H_storage_bytes, real_bytes)
+    bm = bytes_model(wl, H_storage_bytes, real_bytes,
+                     exact_rec=(wl.Cs > 0 and args.adjoint_mode == "exact"))
     ph = res["phase"]
     cand = []
     if ph["plain_launch"]:
@@ -315,6 +349,8 @@ def roofline_of(res, args, H_storage_bytes, real_bytes):
     name, ms, launches, bpl = max(cand, key=lambda c: c[1])
     per_launch_s = ms * 1e-3 / launches
     achieved = bpl * N / per_launch_s / 1e9
+    src_hash = kernel_source_hash()
+    traffic = MEASURED_DRAM.get((src_hash, wl.name, wl.storage, name))
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -324,7 +360,9 @@ def roofline_of(res, args, H_storage_bytes, real_bytes):
     share = {c[0]: c[1] for c in cand}
     tot = sum(share.values())
     return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "algorithmic_bytes_per_launch": round(bpl * N), "kernel_source_hash": src_hash,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "bytes_per_lup": round(bpl, 2), "launch_us": round(per_launch_s * 1e6, 3),
             "time_share": {k: round(v / tot, 4) for k, v in share.items()},
@@ -444,7 +482,8 @@ def main():
                    "lattice": f"D{2 if wl.q == 9 else 3}Q{wl.q}", "storage": wl.storage,
                    "Re": wl.Re, "u0": wl.u0, "primal_steps": res["steps"],
                    "avg_window": res["W"], "objectives": ["drag_ffa", "dissipation"],
-                   "adjoint": {"mode": "exact", "tol": args.adjoint_tol,
+                   "adjoint": {"mode": args.adjoint_mode, "tau_adj": args.tau_adj or None,
+                               "tol": args.adjoint_tol,
                                "max_iter": args.adjoint_max_iter,
                                "iters_per_step": it_per_step},
                    "l2": "flushed between timed steps (252 MB write)",

@@ -207,8 +207,9 @@ __global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
   double rp = 0.0;
   if (x < g.nx - 1) {
     const long long cell = cell_of(g, x, y, z);
+    const Rows rows = make_rows<Lat<Q>::D>(g, y, z);
     R v[Q];
-    aa_load<Q, S, ODD, -1>(A, g, x, y, z, cell, v);
+    aa_load<Q, S, ODD, -1>(A, g, rows, x, cell, v);
     LinCell<Q, R, EXACT> c;
     load_lin<Q, R, EXACT>(a, cell, dp[cell], c);
     transpose_collide<Q, R, EXACT>(c, v, a);
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
     residual_io<Q, R, RES>(a, cell, v, rp);
     if (x == g.nx - 2) {
       R vo[Q];
-      aa_load<Q, S, ODD, -1>(A, g, x + 1, y, z, cell + 1, vo);
+      aa_load<Q, S, ODD, -1>(A, g, rows, x + 1, cell + 1, vo);
       LinCell<Q, R, EXACT> co;
       load_lin<Q, R, EXACT>(a, cell + 1, dp[cell + 1], co);
       transpose_collide<Q, R, EXACT>(co, vo, a);
@@ -225,13 +226,13 @@ __global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
       outlet_transpose<Q, R>(v, vo, c.rho, c.u);
 #pragma unroll
       for (int i = 0; i < Q; ++i) vo[i] = R(0);
-      aa_store<Q, S, ODD, -1>(A, g, x + 1, y, z, cell + 1, vo);
+      aa_store<Q, S, ODD, -1>(A, g, rows, x + 1, cell + 1, vo);
     }
     if (x == 0) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) v[i] = R(0);
     }
-    aa_store<Q, S, ODD, -1>(A, g, x, y, z, cell, v);
+    aa_store<Q, S, ODD, -1>(A, g, rows, x, cell, v);
   }
   if (RES == 2) {
     __shared__ double sh[NT / 32];
@@ -359,7 +360,8 @@ __global__ void __launch_bounds__(NT) k_gradient(GradArgs ga) {
   const Grid& g = ga.g;
   const long long cell = cell_of(g, x, y, z);
   R mu[Q];
-  aa_load<Q, S, false, -1>(static_cast<const R*>(ga.lam), g, x, y, z, cell, mu);
+  const Rows rows = make_rows<Lat<Q>::D>(g, y, z);
+  aa_load<Q, S, false, -1>(static_cast<const R*>(ga.lam), g, rows, x, cell, mu);
   AdjointArgs a{};
   a.rec = ga.rec;
   a.rec_pitch = ga.rec_pitch;

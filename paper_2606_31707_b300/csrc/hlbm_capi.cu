@@ -40,6 +40,11 @@ struct hlbm_ctx {
   double* gsum[2] = {nullptr, nullptr};
   double* ddsum[2] = {nullptr, nullptr};
   double* jblk[2] = {nullptr, nullptr};
+  float* mstage = nullptr;  // FP32 staging of the sums (FP32 / 16-bit storage only)
+  float* fstage = nullptr;
+  float* tstage = nullptr;
+  float* gstage[2] = {nullptr, nullptr};
+  float* ddstage[2] = {nullptr, nullptr};
   long long nblk = 0;
   long nsamples = 0;
   int acc_mask = 0;
@@ -73,7 +78,15 @@ struct hlbm_ctx {
   struct PrimalGraph {
     cudaGraphExec_t exec = nullptr;
     PrimalArgs args{};
-  } pgraph[3][2];
+  } pgraph[2][2];  // [plain, averaging pattern][phase]
+  // captured adjoint chunk: check_every iterations, the residual reduction
+  // and its copy to pinned host memory
+  struct AdjointGraph {
+    cudaGraphExec_t exec = nullptr;
+    AdjointArgs args{};
+    long chunk = 0;
+    bool exact = false;
+  } agraph;
   bool graphs_ok = true;
   hlbm_stats stats{};
   std::string msg;
@@ -209,8 +222,16 @@ int ensure_averages(hlbm_ctx* c, int mask) {
     return set_err(c, HLBM_ENOMEM, "msum");
   if (c->full_f && !c->fsum && !(c->fsum = (double*)dalloc(c, qN))) return set_err(c, HLBM_ENOMEM, "fsum");
   if (!c->tsum && !(c->tsum = (double*)dalloc(c, (size_t)N * 8))) return set_err(c, HLBM_ENOMEM, "tsum");
+  const bool stage = !real_is_double(c);
+  if (stage) {
+    if (!c->mstage && !(c->mstage = (float*)dalloc(c, (size_t)(1 + c->D) * N * 4))) return set_err(c, HLBM_ENOMEM, "mstage");
+    if (c->full_f && !c->fstage && !(c->fstage = (float*)dalloc(c, (size_t)c->q * N * 4))) return set_err(c, HLBM_ENOMEM, "fstage");
+    if (!c->tstage && !(c->tstage = (float*)dalloc(c, (size_t)N * 4))) return set_err(c, HLBM_ENOMEM, "tstage");
+  }
   for (int o = 0; o < 2; ++o) {
     if (!(mask & (1 << o))) continue;
+    if (stage && !c->gstage[o] && !(c->gstage[o] = (float*)dalloc(c, coef_bytes(c, o) / 2))) return set_err(c, HLBM_ENOMEM, "gstage");
+    if (stage && !c->ddstage[o] && !(c->ddstage[o] = (float*)dalloc(c, (size_t)N * 4))) return set_err(c, HLBM_ENOMEM, "ddstage");
     if (!c->gsum[o] && !(c->gsum[o] = (double*)dalloc(c, coef_bytes(c, o)))) return set_err(c, HLBM_ENOMEM, "gsum");
     if (!c->ddsum[o] && !(c->ddsum[o] = (double*)dalloc(c, (size_t)N * 8))) return set_err(c, HLBM_ENOMEM, "ddsum");
     if (!c->jblk[o] && !(c->jblk[o] = (double*)dalloc(c, (size_t)c->nblk * 8))) return set_err(c, HLBM_ENOMEM, "jblk");
@@ -225,8 +246,13 @@ int reset_averages(hlbm_ctx* c, int mask) {
   HLBM_TRY(c, cudaMemsetAsync(c->msum, 0, (size_t)(1 + c->D) * N * 8, c->stream), "memset");
   if (c->fsum) HLBM_TRY(c, cudaMemsetAsync(c->fsum, 0, (size_t)c->q * N * 8, c->stream), "memset");
   HLBM_TRY(c, cudaMemsetAsync(c->tsum, 0, (size_t)N * 8, c->stream), "memset");
+  if (c->mstage) HLBM_TRY(c, cudaMemsetAsync(c->mstage, 0, (size_t)(1 + c->D) * N * 4, c->stream), "memset");
+  if (c->fstage) HLBM_TRY(c, cudaMemsetAsync(c->fstage, 0, (size_t)c->q * N * 4, c->stream), "memset");
+  if (c->tstage) HLBM_TRY(c, cudaMemsetAsync(c->tstage, 0, (size_t)N * 4, c->stream), "memset");
   for (int o = 0; o < 2; ++o) {
     if (!(mask & (1 << o))) continue;
+    if (c->gstage[o]) HLBM_TRY(c, cudaMemsetAsync(c->gstage[o], 0, coef_bytes(c, o) / 2, c->stream), "memset");
+    if (c->ddstage[o]) HLBM_TRY(c, cudaMemsetAsync(c->ddstage[o], 0, (size_t)N * 4, c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->gsum[o], 0, coef_bytes(c, o), c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->ddsum[o], 0, (size_t)N * 8, c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->jblk[o], 0, (size_t)c->nblk * 8, c->stream), "memset");
@@ -268,7 +294,12 @@ PrimalArgs primal_args(hlbm_ctx* c) {
     a.gsum[o] = c->gsum[o];
     a.ddsum[o] = c->ddsum[o];
     a.jblk[o] = c->jblk[o];
+    a.gstage[o] = c->gstage[o];
+    a.ddstage[o] = c->ddstage[o];
   }
+  a.mstage = c->mstage;
+  a.fstage = c->fstage;
+  a.tstage = c->tstage;
   a.obj_mask = c->acc_mask;
   a.ffa[0] = c->opt.ffa_x;
   a.ffa[1] = c->opt.ffa_y0;
@@ -484,16 +515,28 @@ int hlbm_init_equilibrium(hlbm_ctx* c, const void* rho, const void* u, int dtype
   return HLBM_OK;
 }
 
-static constexpr long kGraphSteps = 64;
+static constexpr long kGraphSteps = 64;  // a multiple of 2 (AA phase) and of kStage
 
-// Run `count` consecutive primal steps of one variant starting at the current
-// phase.  Whole blocks of kGraphSteps steps replay a captured CUDA graph (the
-// arguments of every step are identical, only the AA phase alternates), the
-// rest are launched directly.
-static int primal_steps(hlbm_ctx* c, const PrimalArgs& a, bool les, int accv, long count) {
+// Variant of the k-th step of a run: plain (acc_base = 0) or, inside an
+// averaging window of `nsamp` samples taken every step, the averaging variant
+// that folds the FP32 staging into the FP64 sums every kStage samples and at
+// the last sample.
+static int step_variant(int acc_base, long k, long nsamp) {
+  if (!acc_base) return 0;
+  const bool flush = (k % kStage) == kStage - 1 || k == nsamp - 1;
+  return acc_base | (flush ? ACC_FLUSH : 0);
+}
+
+// Run `count` consecutive steps (k = 0 .. count-1 of a plain stretch, or of an
+// averaging window with one sample per step).  Whole blocks of kGraphSteps
+// steps replay a captured CUDA graph -- every step of a block has the same
+// arguments, only the AA phase alternates and the flush falls on fixed
+// positions -- and the remaining steps are launched directly.
+static int primal_steps(hlbm_ctx* c, const PrimalArgs& a, bool les, int acc_base, long count) {
   long done = 0;
-  if (c->graphs_ok && count >= kGraphSteps) {
-    auto& pg = c->pgraph[accv][c->phase];
+  const long blocks = count / kGraphSteps;
+  if (c->graphs_ok && blocks > 0) {
+    auto& pg = c->pgraph[acc_base ? 1 : 0][c->phase];
     if (pg.exec && std::memcmp(&pg.args, &a, sizeof a) != 0) {
       cudaGraphExecDestroy(pg.exec);
       pg.exec = nullptr;
@@ -503,7 +546,8 @@ static int primal_steps(hlbm_ctx* c, const PrimalArgs& a, bool les, int accv, lo
       bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
       int ph = c->phase;
       for (long k = 0; ok && k < kGraphSteps; ++k) {
-        ok = launch_primal(a, c->q, c->storage, ph == 1, les, accv, c->stream) == cudaSuccess;
+        const int v = step_variant(acc_base, k, kGraphSteps + 1);  // interior block: flush on % kStage
+        ok = launch_primal(a, c->q, c->storage, ph == 1, les, v, c->stream) == cudaSuccess;
         ph ^= 1;
       }
       if (cudaStreamEndCapture(c->stream, &graph) != cudaSuccess) ok = false;
@@ -520,6 +564,9 @@ static int primal_steps(hlbm_ctx* c, const PrimalArgs& a, bool les, int accv, lo
       }
     }
     if (pg.exec) {
+      // kGraphSteps is a multiple of kStage, so a replayed block ends on a
+      // flush; the window's own last sample must be a flush too, which holds
+      // when it is the last step of a block
       for (; done + kGraphSteps <= count; done += kGraphSteps) {
         HLBM_TRY(c, cudaGraphLaunch(pg.exec, c->stream), "graph launch");
         c->stats.kernels_total += kGraphSteps;
@@ -528,7 +575,8 @@ static int primal_steps(hlbm_ctx* c, const PrimalArgs& a, bool les, int accv, lo
     }
   }
   for (; done < count; ++done) {
-    cudaError_t e = CNT(c, launch_primal)(a, c->q, c->storage, c->phase == 1, les, accv, c->stream);
+    const int v = step_variant(acc_base, done, count);
+    cudaError_t e = CNT(c, launch_primal)(a, c->q, c->storage, c->phase == 1, les, v, c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "primal launch");
     c->phase ^= 1;
   }
@@ -550,21 +598,24 @@ int hlbm_run_primal(hlbm_ctx* c, long steps, long W) {
   const long stride = c->opt.accum_stride;
   HLBM_TRY(c, cudaEventRecord(c->ev0, c->stream), "event");
   long launches = 0, samples = 0;
-  const int acc_variant = c->full_f ? 2 : 1;
+  const int acc_base = ACC_ON | (c->full_f ? ACC_FULL : 0);
   // plain steps before the window
   rc = primal_steps(c, a, les, 0, first);
   if (rc) return rc;
   launches += first;
   if (W > 0 && stride == 1) {
-    rc = primal_steps(c, a, les, acc_variant, W);
+    rc = primal_steps(c, a, les, acc_base, W);
     if (rc) return rc;
     launches += W;
     samples = W;
-  } else {
+  } else if (W > 0) {
+    const long nsamp = (W + stride - 1) / stride;
     for (long n = first; n < steps; ++n) {
       const bool acc = ((n - first) % stride) == 0;
-      rc = primal_steps(c, a, les, acc ? acc_variant : 0, 1);
-      if (rc) return rc;
+      const int v = acc ? step_variant(acc_base, samples, nsamp) : 0;
+      cudaError_t e = CNT(c, launch_primal)(a, c->q, c->storage, c->phase == 1, les, v, c->stream);
+      if (e != cudaSuccess) return cuda_check(c, e, "primal launch");
+      c->phase ^= 1;
       ++launches;
       if (acc) ++samples;
     }
@@ -711,20 +762,53 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
   long k = 0, launches = 0;
   double r = INFINITY, rmin = INFINITY;
   int status = HLBM_NOT_CONVERGED;
+  auto enqueue_chunk = [&](long chunk) -> cudaError_t {
+    for (long j = 0; j < chunk; ++j) {
+      const bool odd = (j & 1) != 0;
+      const int res = j == chunk - 2 ? 1 : (j == chunk - 1 ? 2 : 0);
+      cudaError_t e = launch_adjoint(a, c->q, dbl, odd, exact, res, c->stream);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = launch_finalize_sum(c->red, nb_adj, c->scal_dev, c->stream);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream);
+  };
+  auto& ag = c->agraph;
+  if (ag.exec && (ag.chunk != m || ag.exact != exact || std::memcmp(&ag.args, &a, sizeof a) != 0)) {
+    cudaGraphExecDestroy(ag.exec);
+    ag.exec = nullptr;
+  }
   while (k < max_iter) {
     long chunk = max_iter - k < m ? max_iter - k : m;
     if (chunk & 1) chunk += 1;
     if (chunk < 2) chunk = 2;
-    for (long j = 0; j < chunk; ++j) {
-      const bool odd = (j & 1) != 0;
-      const int res = j == chunk - 2 ? 1 : (j == chunk - 1 ? 2 : 0);
-      cudaError_t e = CNT(c, launch_adjoint)(a, c->q, dbl, odd, exact, res, c->stream);
-      if (e != cudaSuccess) return cuda_check(c, e, "adjoint launch");
-      ++launches;
+    if (chunk == m && c->graphs_ok && !ag.exec) {
+      cudaGraph_t graph = nullptr;
+      bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) ok = enqueue_chunk(chunk) == cudaSuccess;
+      if (cudaStreamEndCapture(c->stream, &graph) != cudaSuccess) ok = false;
+      if (ok && cudaGraphInstantiate(&ag.exec, graph, 0) != cudaSuccess) {
+        ok = false;
+        ag.exec = nullptr;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      if (!ok) {
+        cudaGetLastError();
+        c->graphs_ok = false;
+      } else {
+        ag.args = a;
+        ag.chunk = m;
+        ag.exact = exact;
+      }
     }
+    if (chunk == m && ag.exec) {
+      HLBM_TRY(c, cudaGraphLaunch(ag.exec, c->stream), "graph launch");
+    } else {
+      HLBM_TRY(c, enqueue_chunk(chunk), "adjoint launch");
+    }
+    c->stats.kernels_total += chunk + 1;
+    launches += chunk;
     k += chunk;
-    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, nb_adj, c->scal_dev, c->stream), "reduce");
-    HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
     HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
     r = std::sqrt(c->scal_host[0]) / gnorm;
     if (!std::isfinite(r)) { status = HLBM_ENONFINITE; break; }
@@ -1065,6 +1149,13 @@ void hlbm_destroy(hlbm_ctx* c) {
   dfree(c, c->d);
   dfree(c, c->msum);
   dfree(c, c->fsum);
+  dfree(c, c->mstage);
+  dfree(c, c->fstage);
+  dfree(c, c->tstage);
+  for (int o = 0; o < 2; ++o) {
+    dfree(c, c->gstage[o]);
+    dfree(c, c->ddstage[o]);
+  }
   dfree(c, c->tsum);
   for (int o = 0; o < 2; ++o) {
     dfree(c, c->gsum[o]);
@@ -1084,6 +1175,7 @@ void hlbm_destroy(hlbm_ctx* c) {
   for (auto& row : c->pgraph)
     for (auto& pg : row)
       if (pg.exec) cudaGraphExecDestroy(pg.exec);
+  if (c->agraph.exec) cudaGraphExecDestroy(c->agraph.exec);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

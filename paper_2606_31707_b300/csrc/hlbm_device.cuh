@@ -132,21 +132,38 @@ __device__ __forceinline__ long long cell_of(const Grid& g, int x, int y, int z)
   return (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
 }
 
-// neighbour (x + dx, y + dy, z + dz); returns -1 when x leaves the domain
-__device__ __forceinline__ long long nbr(const Grid& g, int x, int y, int z, int dx, int dy,
-                                         int dz) {
-  int xn = x + dx;
-  if (xn < 0 || xn >= g.nx) return -1;
-  int yn = y + dy;
-  yn = yn < 0 ? yn + g.ny : (yn >= g.ny ? yn - g.ny : yn);
-  int zn = z + dz;
-  zn = zn < 0 ? zn + g.nz : (zn >= g.nz ? zn - g.nz : zn);
-  return cell_of(g, xn, yn, zn);
+// Row bases (y + ny z) * nx of the 3 x 3 neighbouring rows of (y, z), with the
+// periodic wrap resolved once per cell; the cell index of (x + dx, y + dy,
+// z + dz) is row[dy + 1][dz + 1] + x + dx.
+struct Rows {
+  long long r[3][3];
+};
+
+template <int D>
+__device__ __forceinline__ Rows make_rows(const Grid& g, int y, int z) {
+  Rows R;
+  const int ym = y == 0 ? g.ny - 1 : y - 1;
+  const int yp = y == g.ny - 1 ? 0 : y + 1;
+  const int yy[3] = {ym, y, yp};
+  if (D == 2) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) R.r[a][1] = (long long)yy[a] * g.nx;
+  } else {
+    const int zm = z == 0 ? g.nz - 1 : z - 1;
+    const int zp = z == g.nz - 1 ? 0 : z + 1;
+    const int zz[3] = {zm, z, zp};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        R.r[a][b] = ((long long)yy[a] + (long long)g.ny * zz[b]) * g.nx;
+  }
+  return R;
 }
 
 template <int Q, int S, bool ODD, int SIGN>
-__device__ __forceinline__ void aa_load(const typename Store<S>::mem* A, const Grid& g, int x,
-                                        int y, int z, long long cell,
+__device__ __forceinline__ void aa_load(const typename Store<S>::mem* A, const Grid& g,
+                                        const Rows& rows, int x, long long cell,
                                         typename Store<S>::real (&f)[Q]) {
   using L = Lat<Q>;
   using St = Store<S>;
@@ -155,17 +172,19 @@ __device__ __forceinline__ void aa_load(const typename Store<S>::mem* A, const G
     if (!ODD) {
       f[i] = St::ld(A + (long long)i * g.pitch + cell);
     } else {
-      long long c = (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0)
-                        ? cell
-                        : nbr(g, x, y, z, -SIGN * L::cx(i), -SIGN * L::cy(i), -SIGN * L::cz(i));
-      f[i] = c >= 0 ? St::ld(A + (long long)L::opp(i) * g.pitch + c) : typename St::real(0);
+      // read A[opp(i)][x - s xi_i]
+      const int dx = -SIGN * L::cx(i), dy = -SIGN * L::cy(i), dz = -SIGN * L::cz(i);
+      const int xn = x + dx;
+      const bool in = (dx == 0) || (xn >= 0 && xn < g.nx);
+      const long long c = rows.r[dy + 1][dz + 1] + xn;
+      f[i] = in ? St::ld(A + (long long)L::opp(i) * g.pitch + c) : typename St::real(0);
     }
   }
 }
 
 template <int Q, int S, bool ODD, int SIGN>
-__device__ __forceinline__ void aa_store(typename Store<S>::mem* A, const Grid& g, int x, int y,
-                                         int z, long long cell,
+__device__ __forceinline__ void aa_store(typename Store<S>::mem* A, const Grid& g, const Rows& rows,
+                                         int x, long long cell,
                                          const typename Store<S>::real (&f)[Q]) {
   using L = Lat<Q>;
   using St = Store<S>;
@@ -174,10 +193,12 @@ __device__ __forceinline__ void aa_store(typename Store<S>::mem* A, const Grid& 
     if (!ODD) {
       St::st(A + (long long)L::opp(i) * g.pitch + cell, f[i]);
     } else {
-      long long c = (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0)
-                        ? cell
-                        : nbr(g, x, y, z, SIGN * L::cx(i), SIGN * L::cy(i), SIGN * L::cz(i));
-      if (c >= 0) St::st(A + (long long)i * g.pitch + c, f[i]);
+      // write A[i][x + s xi_i]
+      const int dx = SIGN * L::cx(i), dy = SIGN * L::cy(i), dz = SIGN * L::cz(i);
+      const int xn = x + dx;
+      const bool in = (dx == 0) || (xn >= 0 && xn < g.nx);
+      const long long c = rows.r[dy + 1][dz + 1] + xn;
+      if (in) St::st(A + (long long)i * g.pitch + c, f[i]);
     }
   }
 }
@@ -323,6 +344,23 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   }
   __syncthreads();
   return r;  // valid in thread 0
+}
+
+// block sum in the arithmetic type (valid in thread 0)
+template <class R, int NT>
+__device__ __forceinline__ R block_sum_r(R v, R* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  R r = 0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) r += sh[k];
+  }
+  __syncthreads();
+  return r;
 }
 
 __device__ __forceinline__ long long block_linear() {

@@ -31,6 +31,15 @@ struct PrimalArgs {
                       // in the basis of coef_basis() (FFA, DISS); may be null
   double* ddsum[2];   // N running sums of dJ/dd
   double* jblk[2];    // per-block running sums of J
+  // FP32 kernels add each sample to a float staging copy of every sum and fold
+  // the staged value into the FP64 sum every kStage samples (flush variant),
+  // so that the per-step path issues no FP64 instruction; FP64 kernels add to
+  // the sums directly and leave these null
+  float* mstage;
+  float* fstage;
+  float* tstage;
+  float* gstage[2];
+  float* ddstage[2];
   int obj_mask;
   int ffa[5];         // x, y0, y1, z0, z1 of Gamma_J
   int db[6];          // Omega_J box
@@ -56,8 +65,13 @@ __host__ __device__ inline double coef_basis(int obj_slot, int D, int k, int x, 
   return 2.0 * (k == 0 ? x * y : (k == 1 ? x * z : y * z));
 }
 
+// averaging variant bits of the primal kernel
+enum { ACC_ON = 1, ACC_FULL = 2, ACC_FLUSH = 4 };
+constexpr int kStage = 16;  // samples staged in FP32 before folding into FP64
+
 // launch one primal step kernel; storage 0..3, odd/les select variants,
-// acc: 0 no averaging, 1 averages of moments and coefficients, 2 also of f
+// acc: 0 no averaging, else ACC_ON | optional ACC_FULL (also average f) |
+// optional ACC_FLUSH (fold the FP32 staging into the FP64 sums)
 cudaError_t launch_primal(const PrimalArgs& a, int q, int storage, bool odd, bool les, int acc,
                           cudaStream_t s);
 // out[k] (k < q, per cell) = scale * sum_c coef[c] b_c(xi_k): expand coefficient sums

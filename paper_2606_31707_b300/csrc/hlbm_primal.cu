@@ -24,6 +24,21 @@ __device__ __forceinline__ void equilibrium_dev(R (&g)[Q], R drho, const Vec3<R>
   for (int i = 0; i < Q; ++i) g[i] = geq_i<Q>(i, drho, rho, u, uu);
 }
 
+// Add one sample v to a running FP64 sum.  FP64 kernels add directly; FP32
+// kernels add to the float staging value and, in the flush variant, move the
+// staged total into the FP64 sum and clear the staging value.
+template <class R, int ACC>
+__device__ __forceinline__ void acc_add(double* sum, float* stage, long long k, R v) {
+  if constexpr (sizeof(R) == 8) {
+    sum[k] += (double)v;
+  } else if constexpr ((ACC & ACC_FLUSH) == 0) {
+    stage[k] += v;
+  } else {
+    sum[k] += (double)(stage[k] + v);
+    stage[k] = 0.0f;
+  }
+}
+
 // Collide the canonical state of one cell (as deviations g = f - w), store it
 // AA-style, and (ACC > 0) add the cell's samples to the running averages.
 // Returns the velocity.
@@ -36,8 +51,10 @@ __device__ __forceinline__ void equilibrium_dev(R (&g)[Q], R drho, const Vec3<R>
 //   and J.
 template <int Q, int S, bool ODD, bool LES, int ACC>
 __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
-    const PrimalArgs& a, typename Store<S>::mem* A, int x, int y, int z, long long cell,
-    typename Store<S>::real (&g)[Q], typename Store<S>::real d, double (&jp)[2]) {
+    const PrimalArgs& a, typename Store<S>::mem* A, const Rows& rows, int x, int y, int z,
+    long long cell,
+    typename Store<S>::real (&g)[Q], typename Store<S>::real d,
+    typename Store<S>::real (&jp)[2]) {
   using R = typename Store<S>::real;
   using L = Lat<Q>;
   constexpr int D = L::D;
@@ -71,24 +88,23 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
 
   if constexpr (ACC > 0) {
     const long long N = gr.N;
-    a.msum[cell] += (double)drho;
-    a.msum[N + cell] += (double)m.x;
-    a.msum[2 * N + cell] += (double)m.y;
-    if (D == 3) a.msum[3 * N + cell] += (double)m.z;
-    if constexpr (ACC == 2) {
+    acc_add<R, ACC>(a.msum, a.mstage, cell, drho);
+    acc_add<R, ACC>(a.msum, a.mstage, N + cell, m.x);
+    acc_add<R, ACC>(a.msum, a.mstage, 2 * N + cell, m.y);
+    if (D == 3) acc_add<R, ACC>(a.msum, a.mstage, 3 * N + cell, m.z);
+    if constexpr ((ACC & ACC_FULL) != 0) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) a.fsum[(long long)i * N + cell] += (double)g[i];
+      for (int i = 0; i < Q; ++i) acc_add<R, ACC>(a.fsum, a.fstage, (long long)i * N + cell, g[i]);
     }
-    if (LES) a.tsum[cell] += (double)(tau - tau0);
+    if (LES) acc_add<R, ACC>(a.tsum, a.tstage, cell, tau - tau0);
     // far-field drag J_FFA on Gamma_J (Sec. 4.2): rho u_x (u0 - u_x) + c_s^2 (1 - rho);
     // dJ/df_j = (u_x^2 - c_s^2) + (u0 - 2 u_x) xi_jx
     if ((a.obj_mask & 1) && x == a.ffa[0] && y >= a.ffa[1] && y < a.ffa[2] && z >= a.ffa[3] &&
         z < a.ffa[4]) {
       const R u0 = par<R>(a.u_in, a.u_in_f);
-      double* gs = a.gsum[0];
-      gs[cell] += (double)(u.x * u.x - R(1.0 / 3.0));
-      gs[N + cell] += (double)(u0 - R(2) * u.x);
-      jp[0] += (double)(m.x * (u0 - u.x) - R(1.0 / 3.0) * drho);
+      acc_add<R, ACC>(a.gsum[0], a.gstage[0], cell, u.x * u.x - R(1.0 / 3.0));
+      acc_add<R, ACC>(a.gsum[0], a.gstage[0], N + cell, u0 - R(2) * u.x);
+      jp[0] += m.x * (u0 - u.x) - R(1.0 / 3.0) * drho;
     }
     // dissipation J_DISS on Omega_J (Sec. 4.3): 2 nu S:S + (1-d)/tau0 u.u,
     // S = -3 Pi / (2 tau):  J = (9 nu / 2) |Pi|^2 / tau^2 + (1-d)/tau0 |u|^2.
@@ -109,32 +125,33 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
       const R uPU = dot3(u, PU);
       const R c2 = one_d / tau0 * R(2) / rho;
       double* gs = a.gsum[1];
-      gs[cell] += (double)(fac * (-trP * R(1.0 / 3.0) - uPu + R(2) * d * uPU) - c2 * uu_raw);
-      gs[N + cell] += (double)(-R(2) * d * fac * PU.x + c2 * u.x);
-      gs[2 * N + cell] += (double)(-R(2) * d * fac * PU.y + c2 * u.y);
+      float* st = a.gstage[1];
+      acc_add<R, ACC>(gs, st, cell, fac * (-trP * R(1.0 / 3.0) - uPu + R(2) * d * uPU) - c2 * uu_raw);
+      acc_add<R, ACC>(gs, st, N + cell, -R(2) * d * fac * PU.x + c2 * u.x);
+      acc_add<R, ACC>(gs, st, 2 * N + cell, -R(2) * d * fac * PU.y + c2 * u.y);
       if (D == 2) {
-        gs[3 * N + cell] += (double)(fac * P.xx);
-        gs[4 * N + cell] += (double)(fac * P.yy);
-        gs[5 * N + cell] += (double)(fac * P.xy);
+        acc_add<R, ACC>(gs, st, 3 * N + cell, fac * P.xx);
+        acc_add<R, ACC>(gs, st, 4 * N + cell, fac * P.yy);
+        acc_add<R, ACC>(gs, st, 5 * N + cell, fac * P.xy);
       } else {
-        gs[3 * N + cell] += (double)(-R(2) * d * fac * PU.z + c2 * u.z);
-        gs[4 * N + cell] += (double)(fac * P.xx);
-        gs[5 * N + cell] += (double)(fac * P.yy);
-        gs[6 * N + cell] += (double)(fac * P.zz);
-        gs[7 * N + cell] += (double)(fac * P.xy);
-        gs[8 * N + cell] += (double)(fac * P.xz);
-        gs[9 * N + cell] += (double)(fac * P.yz);
+        acc_add<R, ACC>(gs, st, 3 * N + cell, -R(2) * d * fac * PU.z + c2 * u.z);
+        acc_add<R, ACC>(gs, st, 4 * N + cell, fac * P.xx);
+        acc_add<R, ACC>(gs, st, 5 * N + cell, fac * P.yy);
+        acc_add<R, ACC>(gs, st, 6 * N + cell, fac * P.zz);
+        acc_add<R, ACC>(gs, st, 7 * N + cell, fac * P.xy);
+        acc_add<R, ACC>(gs, st, 8 * N + cell, fac * P.xz);
+        acc_add<R, ACC>(gs, st, 9 * N + cell, fac * P.yz);
       }
       const Vec3<R> v{u.x - us.x, u.y - us.y, u.z - us.z};
       const R dd = fac * (-R(2) * rho * dot3(v, PU)) - uu_raw / tau0;
-      a.ddsum[1][cell] += (double)dd;
-      jp[1] += (double)J;
+      acc_add<R, ACC>(a.ddsum[1], a.ddstage[1], cell, dd);
+      jp[1] += J;
     }
   }
 
 #pragma unroll
   for (int i = 0; i < Q; ++i) g[i] -= om * fneq[i];
-  aa_store<Q, S, ODD, +1>(A, gr, x, y, z, cell, g);
+  aa_store<Q, S, ODD, +1>(A, gr, rows, x, cell, g);
   return u;
 }
 
@@ -147,30 +164,33 @@ __global__ void __launch_bounds__(NT) k_primal(PrimalArgs a) {
   const int y = blockIdx.y, z = blockIdx.z;
   auto* A = static_cast<typename St::mem*>(a.f);
   const R* dp = static_cast<const R*>(a.d);
-  double jp[2] = {0.0, 0.0};
+  R jp[2] = {R(0), R(0)};
   if (x < gr.nx - 1) {
     const long long cell = cell_of(gr, x, y, z);
+    const Rows rows = make_rows<Lat<Q>::D>(gr, y, z);
     R g[Q];
     if (x == 0) {
       equilibrium_dev<Q, R>(g, R(0), Vec3<R>{par<R>(a.u_in, a.u_in_f), R(0), R(0)});
     } else {
-      aa_load<Q, S, ODD, +1>(A, gr, x, y, z, cell, g);
+      aa_load<Q, S, ODD, +1>(A, gr, rows, x, cell, g);
     }
-    const Vec3<R> u = cell_update<Q, S, ODD, LES, ACC>(a, A, x, y, z, cell, g, dp[cell], jp);
+    const Vec3<R> u = cell_update<Q, S, ODD, LES, ACC>(a, A, rows, x, y, z, cell, g, dp[cell], jp);
     if (x == gr.nx - 2) {
       // outflow node: f^eq(1, u(nx-2)), then relaxed and streamed like any cell
       R go[Q];
       equilibrium_dev<Q, R>(go, R(0), u);
-      cell_update<Q, S, ODD, LES, ACC>(a, A, x + 1, y, z, cell + 1, go, dp[cell + 1], jp);
+      cell_update<Q, S, ODD, LES, ACC>(a, A, rows, x + 1, y, z, cell + 1, go, dp[cell + 1], jp);
     }
   }
   if constexpr (ACC > 0) {
-    __shared__ double sh[NT / 32];
+    // J of this step summed over the block in the arithmetic type, then added
+    // to the block's FP64 running sum (one FP64 add per block and step)
+    __shared__ R sh[NT / 32];
 #pragma unroll
     for (int o = 0; o < 2; ++o) {
       if (!(a.obj_mask & (1 << o))) continue;
-      const double sm = block_sum<NT>(jp[o], sh);
-      if (threadIdx.x == 0) a.jblk[o][block_linear()] += sm;
+      const R sm = block_sum_r<R, NT>(jp[o], sh);
+      if (threadIdx.x == 0) a.jblk[o][block_linear()] += (double)sm;
     }
   }
 }
@@ -180,8 +200,17 @@ static cudaError_t launch_primal_qs(const PrimalArgs& a, bool odd, bool les, int
                                     cudaStream_t s) {
   dim3 grid((a.g.nx + NT - 1) / NT, a.g.ny, a.g.nz);
 #define HLBM_L(O, L_, A_) k_primal<Q, S, O, L_, A_><<<grid, NT, 0, s>>>(a)
-#define HLBM_LA(O, L_) \
-  do { if (acc == 0) HLBM_L(O, L_, 0); else if (acc == 1) HLBM_L(O, L_, 1); else HLBM_L(O, L_, 2); } while (0)
+#define HLBM_LA(O, L_)                                   \
+  do {                                                   \
+    switch (acc) {                                       \
+      case 0: HLBM_L(O, L_, 0); break;                   \
+      case ACC_ON: HLBM_L(O, L_, ACC_ON); break;         \
+      case ACC_ON | ACC_FULL: HLBM_L(O, L_, ACC_ON | ACC_FULL); break; \
+      case ACC_ON | ACC_FLUSH: HLBM_L(O, L_, ACC_ON | ACC_FLUSH); break; \
+      case ACC_ON | ACC_FULL | ACC_FLUSH: HLBM_L(O, L_, ACC_ON | ACC_FULL | ACC_FLUSH); break; \
+      default: return cudaErrorInvalidValue;             \
+    }                                                    \
+  } while (0)
   if (!odd) { if (!les) HLBM_LA(false, false); else HLBM_LA(false, true); }
   else      { if (!les) HLBM_LA(true, false);  else HLBM_LA(true, true); }
 #undef HLBM_LA
@@ -222,18 +251,19 @@ __global__ void __launch_bounds__(NT) k_readout(const void* fv, Grid gr, double 
   if (x >= gr.nx) return;
   const auto* A = static_cast<const typename St::mem*>(fv);
   const long long cell = cell_of(gr, x, y, z);
+  const Rows rows = make_rows<Lat<Q>::D>(gr, y, z);
   R g[Q];
   if (x == 0) {
     equilibrium_dev<Q, R>(g, R(0), Vec3<R>{R(u_in), R(0), R(0)});
   } else if (x == gr.nx - 1) {
     R gi[Q];
-    aa_load<Q, S, ODD, +1>(A, gr, x - 1, y, z, cell - 1, gi);
+    aa_load<Q, S, ODD, +1>(A, gr, rows, x - 1, cell - 1, gi);
     R dr, r;
     Vec3<R> m, u;
     moments_dev<Q>(gi, dr, r, m, u);
     equilibrium_dev<Q, R>(g, R(0), u);
   } else {
-    aa_load<Q, S, ODD, +1>(A, gr, x, y, z, cell, g);
+    aa_load<Q, S, ODD, +1>(A, gr, rows, x, cell, g);
   }
   if (fout) {
 #pragma unroll

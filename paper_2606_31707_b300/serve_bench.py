@@ -82,11 +82,14 @@ def run(args):
     wall_plain = time.perf_counter() - t0
     span_plain = clock - reqs[0][0]
 
-    # served path: submit at arrival times
+    # served path: submit at arrival times, in the chosen storage form
+    import dataclasses
+    st_code = {"fp32": H.FP32, "fp16dev": H.FP16DEV, "bf16dev": H.BF16DEV}[args.served_storage]
     srv = SensitivityServer(slots=args.slots, hbm_budget=args.budget_gb << 30)
     t0 = time.perf_counter()
     futs = []
     for t_arr, r in reqs:
+        r = dataclasses.replace(r, storage=st_code)
         now = time.perf_counter() - t0
         if t_arr > now:
             time.sleep(t_arr - now)
@@ -110,7 +113,7 @@ def run(args):
         "plain": {"gradients_per_s": len(plain) / span_plain, "p50_s": pct(lat_plain, 50),
                   "p99_s": pct(lat_plain, 99), "busy_s": wall_plain},
         "served": {"gradients_per_s": len(served) / span_served, "p50_s": pct(lat_served, 50),
-                   "p99_s": pct(lat_served, 99)},
+                   "p99_s": pct(lat_served, 99), "storage": args.served_storage},
         "speedup_gradients_per_s": (len(served) / span_served) / (len(plain) / span_plain),
         "max_rel_gradient_diff_served_vs_plain": maxdiff,
         "mlups_plain": lups / wall_plain / 1e6,
@@ -129,6 +132,7 @@ def main():
     ap.add_argument("--avg", type=int, default=2000)
     ap.add_argument("--max-iter", type=int, default=4000)
     ap.add_argument("--budget-gb", type=int, default=200)
+    ap.add_argument("--served-storage", default="fp32", choices=["fp32", "fp16dev", "bf16dev"])
     run(ap.parse_args())
 
 

@@ -136,3 +136,32 @@ def test_les_fullsize_primal_step_on_sampled_boxes(storage, tol):
         assert rel_l2(g[:, z0:z1, y0:y1, x0:x1] - P.w[:, None, None, None],
                       ref - P.w[:, None, None, None]) <= tol
     s.close()
+
+
+@pytest.mark.parametrize("mode", [oadj.EXACT, oadj.FTA])
+def test_les_config_adjoint_iterations_kernel_level(mode):
+    # the LES configuration (D3Q19, C_S = 0.1, tau0 from Re 3900, FP32) on a
+    # reduced grid: 30 adjoint iterations and the gradient from the same
+    # averaged state on both sides (exact LES and frozen turbulence, tau_adj 0.6)
+    wl = make_workload("les3d_re3900_quarter")
+    dims = (64, 24, 12)
+    P = ohlbm.Params(19, dims, tau0=ohlbm.tau_from_reynolds(wl.u0, wl.L, wl.Re), Cs=wl.Cs, u_in=wl.u0)
+    from workloads import Regions, cylinder_porosity
+    d = cylinder_porosity(dims, 16.0, 12.0, 4.0, 2.0, jitter=0.01, seed=4)
+    R = Regions(ffa_x=40, ffa_y=(0, 24), ffa_z=(0, 12), diss_box=(2, 60, 0, 24, 0, 12),
+                design_box=(0, 64, 0, 24, 0, 12))
+    f = _state_near(P, wl, seed=8, amp=0.01)
+    s = Solver(19, dims, P.tau0, P.Cs, storage=H.FP32, u_in=wl.u0, regions=R, tau_adj=0.6)
+    perm = direction_perm(s.xi, P)
+    s.set_porosity(d)
+    s.set_field(H.FIELD_F, to_lib(f, perm))
+    s.run_primal(4, 3)
+    out = omf.run_primal(f, d, P, 4, 3, R, 3)
+    lin = oadj.Linearisation(out["fbar"], d, P, mode, 0.6, out["tau_t_bar"])
+    for o in (oobj.FFA, oobj.DISS):
+        st, it, res = s.solve_adjoint(o, mode, 0.0, 30)
+        lam, _, _ = oadj.solve_adjoint(lin, out[("gbar", o)], tol=0.0, max_iter=30)
+        assert rel_l2(s.field(H.FIELD_LAMBDA), to_lib(lin.mu(lam), perm)) <= 1e-4
+        G = oadj.gradient(lin, lam, out[("dJdd_bar", o)])
+        assert rel_l2(s.gradient(), G) <= 1e-4
+    s.close()
