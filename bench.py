@@ -112,11 +112,14 @@ def job_shape(wl, args):
 def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False):
     """Algorithmic bytes per lattice update of each kernel (reads + writes).
 
-    Averaging step: the populations and porosity of a plain step, a
-    read-modify-write (16 B) of each FP64 running sum it updates: density and
-    momentum (1 + D), all q populations when Cs > 0, tau_eff - tau0 when Cs > 0,
-    and inside the objective regions the dJ/df coefficients (2 for the drag
-    plane, 1 + D + D(D+1)/2 for the dissipation box) and dJ/dd."""
+    Averaging step: the populations and porosity of a plain step plus, for
+    each running sum it updates, a read-modify-write of the sum -- 16 B for
+    FP64 storage; for the other storages the sample goes to a float staging
+    value (8 B) that is folded into the FP64 sum every 16 samples
+    (16 B + 8 B, amortised 1.5 B).  Sums: density and momentum (1 + D), all q
+    populations and tau_eff - tau0 when Cs > 0, and inside the objective
+    regions the dJ/df coefficients (2 on the drag plane, 1 + D + D(D+1)/2 in
+    the dissipation box) and dJ/dd."""
     q = wl.q
     nx, ny, nz = wl.dims
     N = nx * ny * nz
@@ -127,8 +130,9 @@ def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False):
     b = r.diss_box
     diss_cells = (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
     les = wl.Cs > 0
-    acc = plain + 16 * (1 + D) + (16 * q + 16 if les else 0)
-    acc += (ffa_cells * 16 * 2 + diss_cells * (16 * (1 + D + D * (D + 1) // 2) + 16)) / N
+    sb = 16.0 if real_bytes == 8 else 8.0 + 24.0 / 16
+    acc = plain + sb * (1 + D) + (sb * (q + 1) if les else 0)
+    acc += (ffa_cells * sb * 2 + diss_cells * sb * (1 + D + D * (D + 1) // 2 + 1)) / N
     rec = q if exact_rec else D + 2
     adj_ffa = (2 * q + rec + 1) * real_bytes + ffa_cells * q * real_bytes / N
     adj_diss = (2 * q + rec + 1) * real_bytes + diss_cells * q * real_bytes / N

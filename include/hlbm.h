@@ -117,6 +117,8 @@ typedef struct {
                            linearises at f_bar itself.  Otherwise only the
                            density and momentum of f are averaged, which is
                            all the BGK / frozen-turbulence linearisation reads */
+  int block_x;          /* threads per block along x of the step kernels: 32, 64
+                           or 128; 0 = chosen from the grid size */
   void* stream;         /* cudaStream_t to issue work on; NULL = own stream */
   void* (*dev_alloc)(size_t bytes, void* user); /* NULL = cudaMalloc */
   void (*dev_free)(void* ptr, void* user);      /* NULL = cudaFree */
@@ -141,6 +143,15 @@ void hlbm_default_options(hlbm_options* opt, const int dims[3]);
  * (defaults).  On error *out is NULL. */
 int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau,
                 double Cs, const hlbm_options* opt);
+
+/* Change the physical parameters of an existing context without
+ * reallocating it: relaxation time tau, Smagorinsky constant Cs and, from
+ * opt (may be NULL), u_in, u_solid, tau_adj, objectives, the regions,
+ * accum_stride, check_every and average_full_f (storage, stream, allocator
+ * and block_x keep their creation values).  Clears the averages and the
+ * adjoint; the state and the porosity are kept.  Lets a server reuse a
+ * context (and its captured graphs) for a new request of the same grid. */
+int hlbm_configure(hlbm_ctx* ctx, double tau, double Cs, const hlbm_options* opt);
 
 /* Set the lattice porosity d(x) in [0, 1] (Sec. 2.1; the control of
  * Sec. 3.1), N values of dtype, host or device.  Values outside [0, 1]

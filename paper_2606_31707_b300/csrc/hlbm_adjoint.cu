@@ -200,7 +200,7 @@ template <int Q, class R, bool ODD, bool EXACT, int RES>
 __global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
   constexpr int S = RealStore<R>::S;
   const Grid& g = a.g;
-  const int x = blockIdx.x * NT + threadIdx.x;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
   R* A = static_cast<R*>(a.lam);
   const R* dp = static_cast<const R*>(a.d);
@@ -241,13 +241,14 @@ __global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
   }
 }
 
-int adjoint_blocks(const Grid& g) { return ((g.nx + NT - 1) / NT) * g.ny * g.nz; }
+int adjoint_blocks(const Grid& g) { return ((g.nx + g.bx - 1) / g.bx) * g.ny * g.nz; }
 
 template <int Q, class R>
 static cudaError_t launch_adj_qr(const AdjointArgs& a, bool odd, bool exact, int res,
                                  cudaStream_t s) {
-  dim3 grid((a.g.nx + NT - 1) / NT, a.g.ny, a.g.nz);
-#define HLBM_A(O, E, RS) k_adjoint<Q, R, O, E, RS><<<grid, NT, 0, s>>>(a)
+  const int bx = a.g.bx;
+  dim3 grid((a.g.nx + bx - 1) / bx, a.g.ny, a.g.nz);
+#define HLBM_A(O, E, RS) k_adjoint<Q, R, O, E, RS><<<grid, bx, 0, s>>>(a)
 #define HLBM_AR(O, E) \
   do { if (res == 0) HLBM_A(O, E, 0); else if (res == 1) HLBM_A(O, E, 1); else HLBM_A(O, E, 2); } while (0)
   if (!odd) { if (!exact) HLBM_AR(false, false); else HLBM_AR(false, true); }

@@ -380,7 +380,27 @@ int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau, doub
   c->Cs = Cs;
   c->kles = 4.5 * std::sqrt(2.0) * Cs * Cs;
   c->nu0 = (tau - 0.5) / 3.0;
-  c->nblk = (long long)((dims[0] + NT - 1) / NT) * dims[1] * dims[2];
+  // threads per block along x of the step kernels: the widest of 128 / 64 / 32
+  // that still gives enough blocks to fill the GPU (small grids get narrower
+  // blocks so that every SM has warps to switch between)
+  {
+    int bx = c->opt.block_x;
+    if (bx != 32 && bx != 64 && bx != 128) {
+      int sms = 148, dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 148;
+      }
+      bx = 32;
+      for (int cand : {128, 64}) {
+        const long long blocks = (long long)((dims[0] + cand - 1) / cand) * dims[1] * dims[2];
+        if (blocks >= 16LL * sms) { bx = cand; break; }
+      }
+    }
+    c->g.bx = bx;
+  }
+  c->nblk = (long long)((dims[0] + c->g.bx - 1) / c->g.bx) * dims[1] * dims[2];
   c->full_f = c->opt.average_full_f != 0 || Cs > 0.0;
   // least-squares inverse P = (V^T V)^-1 V^T of the coefficient basis V (q x nc)
   for (int o = 0; o < 2; ++o) {
@@ -454,6 +474,39 @@ int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau, doub
   if (rc != HLBM_OK) { hlbm_destroy(c); return rc; }
   c->stats.primal_bytes_per_lup_plain = bytes_plain(c);
   *out = c;
+  return HLBM_OK;
+}
+
+int hlbm_configure(hlbm_ctx* c, double tau, double Cs, const hlbm_options* opt) {
+  if (!c) return HLBM_EINVAL;
+  if (!(tau > 0.5) || !(Cs >= 0.0) || !std::isfinite(tau) || !std::isfinite(Cs))
+    return set_err(c, HLBM_EINVAL, "need tau > 0.5 and Cs >= 0");
+  if (opt) {
+    int ffa[6] = {opt->ffa_x, opt->ffa_x + 1, opt->ffa_y0, opt->ffa_y1, opt->ffa_z0, opt->ffa_z1};
+    if (!check_box(c, ffa) || !check_box(c, opt->diss_box) || !check_box(c, opt->design_box))
+      return set_err(c, HLBM_EINVAL, "region outside the grid");
+    c->opt.u_in = opt->u_in;
+    for (int k = 0; k < 3; ++k) c->opt.u_solid[k] = opt->u_solid[k];
+    c->opt.tau_adj = opt->tau_adj;
+    c->opt.objectives = opt->objectives;
+    c->opt.ffa_x = opt->ffa_x;
+    c->opt.ffa_y0 = opt->ffa_y0; c->opt.ffa_y1 = opt->ffa_y1;
+    c->opt.ffa_z0 = opt->ffa_z0; c->opt.ffa_z1 = opt->ffa_z1;
+    std::memcpy(c->opt.diss_box, opt->diss_box, sizeof c->opt.diss_box);
+    std::memcpy(c->opt.design_box, opt->design_box, sizeof c->opt.design_box);
+    c->opt.accum_stride = opt->accum_stride < 1 ? 1 : opt->accum_stride;
+    c->opt.check_every = opt->check_every < 2 ? 100 : opt->check_every + (opt->check_every & 1);
+    c->opt.average_full_f = opt->average_full_f;
+  }
+  c->tau0 = tau;
+  c->Cs = Cs;
+  c->kles = 4.5 * std::sqrt(2.0) * Cs * Cs;
+  c->nu0 = (tau - 0.5) / 3.0;
+  c->full_f = c->full_f || c->opt.average_full_f != 0 || Cs > 0.0;
+  c->nsamples = 0;
+  c->acc_mask = 0;
+  c->generation++;
+  c->have_adjoint = false;
   return HLBM_OK;
 }
 

@@ -126,6 +126,7 @@ struct Grid {
   int nx, ny, nz;
   long long N;      // cells
   long long pitch;  // plane stride (elements) of population arrays
+  int bx;           // threads per block along x of the step kernels (32, 64 or 128)
 };
 
 __device__ __forceinline__ long long cell_of(const Grid& g, int x, int y, int z) {
@@ -331,6 +332,7 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// block sum over blockDim.x <= NT threads (valid in thread 0)
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   v = warp_sum(v);
@@ -339,11 +341,11 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   __syncthreads();
   double r = 0;
   if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NT / 32; ++k) r += sh[k];
+    const int nw = (int)(blockDim.x >> 5);
+    for (int k = 0; k < nw; ++k) r += sh[k];
   }
   __syncthreads();
-  return r;  // valid in thread 0
+  return r;
 }
 
 // block sum in the arithmetic type (valid in thread 0)
@@ -356,8 +358,8 @@ __device__ __forceinline__ R block_sum_r(R v, R* sh) {
   __syncthreads();
   R r = 0;
   if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NT / 32; ++k) r += sh[k];
+    const int nw = (int)(blockDim.x >> 5);
+    for (int k = 0; k < nw; ++k) r += sh[k];
   }
   __syncthreads();
   return r;

@@ -52,6 +52,7 @@ class hlbm_options(C.Structure):
         ("accum_stride", C.c_int),
         ("check_every", C.c_int),
         ("average_full_f", C.c_int),
+        ("block_x", C.c_int),
         ("stream", C.c_void_p),
         ("dev_alloc", _ALLOC),
         ("dev_free", _FREE),
@@ -91,6 +92,7 @@ def _load():
         "hlbm_create": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.c_double,
                                   C.c_double, C.POINTER(hlbm_options)]),
         "hlbm_set_porosity": (C.c_int, [P, P, C.c_int, C.c_int]),
+        "hlbm_configure": (C.c_int, [P, C.c_double, C.c_double, C.POINTER(hlbm_options)]),
         "hlbm_init_equilibrium": (C.c_int, [P, P, P, C.c_int, C.c_int]),
         "hlbm_run_primal": (C.c_int, [P, C.c_long, C.c_long]),
         "hlbm_objective": (C.c_int, [P, C.c_int, C.POINTER(C.c_double)]),
@@ -116,7 +118,8 @@ def _load():
 
 
 _lib = _load()
-EXPORTED = ("hlbm_velocity_set", "hlbm_default_options", "hlbm_create", "hlbm_set_porosity",
+EXPORTED = ("hlbm_velocity_set", "hlbm_default_options", "hlbm_create", "hlbm_configure",
+            "hlbm_set_porosity",
             "hlbm_init_equilibrium", "hlbm_run_primal", "hlbm_objective", "hlbm_solve_adjoint",
             "hlbm_gradient", "hlbm_get_field", "hlbm_set_field", "hlbm_get_stats", "hlbm_save",
             "hlbm_load", "hlbm_last_error", "hlbm_destroy", "hlbm_objective_noalloc")
@@ -198,6 +201,10 @@ def hlbm_create(lattice: int, dims: Sequence[int], tau: float, Cs: float,
     if r < 0:
         raise HlbmError(r, "hlbm_create failed")
     return ctx
+
+
+def hlbm_configure(ctx, tau: float, Cs: float, opt: Optional[hlbm_options] = None):
+    return _check(ctx, _lib.hlbm_configure(ctx, tau, Cs, C.byref(opt) if opt is not None else None))
 
 
 def hlbm_set_porosity(ctx, d):

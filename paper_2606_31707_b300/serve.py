@@ -76,11 +76,64 @@ def footprint_bytes(q: int, dims: Sequence[int], storage: int = H.FP32, objectiv
     return int(b)
 
 
+class ContextPool:
+    """Idle contexts kept for reuse, keyed by (lattice, grid, storage).
+
+    Reusing a context avoids its allocations and frees (cudaFree waits for the
+    whole device, which would stall every other request in flight) and keeps
+    its captured CUDA graphs.  Idle contexts count against the HBM budget and
+    are destroyed, oldest first, when an admission needs their memory."""
+
+    def __init__(self):
+        self._idle = {}          # key -> list of (Solver, bytes)
+        self._order: List[tuple] = []
+        self.idle_bytes = 0
+        self.hits = 0
+        self.misses = 0
+
+    def take(self, key):
+        lst = self._idle.get(key)
+        if lst:
+            s, b = lst.pop()
+            self._order.remove((key, id(s)))
+            self.idle_bytes -= b
+            self.hits += 1
+            return s
+        self.misses += 1
+        return None
+
+    def give(self, key, solver, nbytes):
+        self._idle.setdefault(key, []).append((solver, nbytes))
+        self._order.append((key, id(solver)))
+        self.idle_bytes += nbytes
+
+    def evict_one(self) -> bool:
+        if not self._order:
+            return False
+        key, sid = self._order.pop(0)
+        lst = self._idle[key]
+        for k, (s, b) in enumerate(lst):
+            if id(s) == sid:
+                lst.pop(k)
+                self.idle_bytes -= b
+                s.close()
+                return True
+        return False
+
+    def clear(self):
+        while self.evict_one():
+            pass
+
+
+def _key(req: "Request"):
+    return (req.q, tuple(req.dims), req.storage)
+
+
 class SensitivityServer:
     """Admit requests into at most ``slots`` concurrent solves within
     ``hbm_budget`` bytes; results are returned through futures."""
 
-    def __init__(self, slots: int = 8, hbm_budget: int = 200 << 30):
+    def __init__(self, slots: int = 8, hbm_budget: int = 200 << 30, reuse_contexts: bool = True):
         self.slots = slots
         self.budget = hbm_budget
         self._q: "queue.Queue[tuple]" = queue.Queue()
@@ -92,6 +145,7 @@ class SensitivityServer:
         self._sched = threading.Thread(target=self._schedule, daemon=True)
         self._pending: List[tuple] = []
         self.completed: List[Result] = []
+        self.pool = ContextPool() if reuse_contexts else None
         self._sched.start()
 
     # ------------------------------------------------------------------
@@ -114,6 +168,8 @@ class SensitivityServer:
         self._sched.join()
         for t in self._threads:
             t.join()
+        if self.pool is not None:
+            self.pool.clear()
 
     # ------------------------------------------------------------------
     def _schedule(self):
@@ -125,25 +181,36 @@ class SensitivityServer:
                     return
                 if not self._admissible():
                     continue
-                # first-come first-served among requests that fit
+                # first-come first-served among requests that fit; a reusable idle
+                # context of the same shape needs no new memory
                 k = next(i for i, (_, _, need) in enumerate(self._pending)
-                         if self._used + need <= self.budget)
+                         if self._fits(need))
                 req, fut, need = self._pending.pop(k)
+                solver = self.pool.take(_key(req)) if self.pool is not None else None
+                if solver is None:
+                    while self.pool is not None and self._used + self.pool.idle_bytes + need > self.budget:
+                        if not self.pool.evict_one():
+                            break
                 self._used += need
                 self._active += 1
-            t = threading.Thread(target=self._run, args=(req, fut, need), daemon=True)
+            t = threading.Thread(target=self._run, args=(req, fut, need, solver), daemon=True)
             t.start()
             self._threads.append(t)
+
+    def _fits(self, need: int) -> bool:
+        # idle pooled contexts can always be evicted to make room
+        return self._used + need <= self.budget
 
     def _admissible(self) -> bool:
         if self._active >= self.slots or not self._pending:
             return False
-        return any(self._used + need <= self.budget for _, _, need in self._pending)
+        return any(self._fits(need) for _, _, need in self._pending)
 
-    def _run(self, req: Request, fut: Future, need: int):
+    def _run(self, req: Request, fut: Future, need: int, solver):
         t0 = time.perf_counter()
+        keep = None
         try:
-            res = solve_one(req)
+            res, keep = solve_one(req, solver, keep_context=self.pool is not None)
             res.queued_s = t0 - req.t_submit
             res.latency_s = time.perf_counter() - req.t_submit
             self.completed.append(res)
@@ -154,21 +221,38 @@ class SensitivityServer:
             with self._cv:
                 self._used -= need
                 self._active -= 1
+                if keep is not None:
+                    self.pool.give(_key(req), keep, need)
                 self._cv.notify_all()
 
 
-def solve_one(req: Request) -> Result:
-    """Algorithm 1 for one request on its own context and stream."""
-    s = Solver(req.q, req.dims, req.tau, req.Cs, storage=req.storage, u_in=req.u_in,
-               regions=req.regions, objectives=req.objective)
+def solve_one(req: Request, solver: Optional[Solver] = None, keep_context: bool = False):
+    """Algorithm 1 for one request on its own context and stream.
+
+    With ``solver`` an idle context of the same grid and storage is reused
+    (reconfigured for the request).  Returns the Result, and with
+    ``keep_context`` also the context (else it is destroyed)."""
+    if solver is None:
+        s = Solver(req.q, req.dims, req.tau, req.Cs, storage=req.storage, u_in=req.u_in,
+                   regions=req.regions, objectives=req.objective)
+    else:
+        s = solver
+        s.configure(req.tau, req.Cs, u_in=req.u_in, regions=req.regions, objectives=req.objective)
+    ok = False
     try:
         s.set_porosity(req.porosity)
+        H.hlbm_init_equilibrium(s.ctx)
         steps = req.warm_steps + req.avg_steps
         s.run_primal(steps, req.avg_steps)
         J = s.objective(req.objective)
         st, it, res = s.solve_adjoint(req.objective, req.mode, req.tol, req.max_iter)
         G = s.gradient()
         N = int(np.prod(req.dims))
-        return Result(req.tag, J, G, it, res, st, 0.0, 0.0, N * (steps + it))
+        ok = True
+        result = Result(req.tag, J, G, it, res, st, 0.0, 0.0, N * (steps + it))
     finally:
-        s.close()
+        if not (ok and keep_context):
+            s.close()
+    if keep_context:
+        return result, s
+    return result

@@ -71,6 +71,7 @@ def run(args):
     plain = []
     lat_plain = []
     clock = 0.0
+    per_size = {}
     for t_arr, r in reqs:
         start = max(clock, t_arr)
         t = time.perf_counter()
@@ -79,6 +80,7 @@ def run(args):
         clock = start + dt
         lat_plain.append(clock - t_arr)
         plain.append(res)
+        per_size.setdefault("x".join(map(str, r.dims)), []).append(round(dt, 4))
     wall_plain = time.perf_counter() - t0
     span_plain = clock - reqs[0][0]
 
@@ -96,6 +98,7 @@ def run(args):
         futs.append(srv.submit(r))
     served = [f.result() for f in futs]
     t_end = time.perf_counter() - t0
+    pool = {"hits": srv.pool.hits, "misses": srv.pool.misses} if srv.pool is not None else None
     srv.close()
     lat_served = [s.latency_s for s in served]
     span_served = t_end - reqs[0][0]
@@ -117,6 +120,9 @@ def run(args):
         "speedup_gradients_per_s": (len(served) / span_served) / (len(plain) / span_plain),
         "max_rel_gradient_diff_served_vs_plain": maxdiff,
         "mlups_plain": lups / wall_plain / 1e6,
+        "plain_solve_s_by_size": per_size,
+        "adjoint_iters": [r.adjoint_iters for r in plain],
+        "context_pool": pool,
         "sizes": [list(r.dims) for _, r in reqs],
     }
     print(json.dumps(line))

@@ -25,6 +25,17 @@ class Solver:
         self.q = lattice
         self.dims = tuple(int(v) for v in dims)
         self.dim = 2 if lattice == 9 else 3
+        opt = self._options(storage, u_in, regions, objectives, tau_adj, accum_stride,
+                            check_every, u_solid, average_full_f)
+        if stream is not None:
+            opt.stream = stream if isinstance(stream, int) else int(stream.cuda_stream)
+        self.opt = opt
+        self.ctx = H.hlbm_create(lattice, self.dims, tau, Cs, opt)
+        self.xi, self.w = H.hlbm_velocity_set(lattice)
+        self._design(opt)
+
+    def _options(self, storage, u_in, regions, objectives, tau_adj, accum_stride, check_every,
+                 u_solid, average_full_f):
         opt = H.hlbm_default_options(self.dims)
         opt.storage = storage
         opt.u_in = u_in
@@ -42,13 +53,21 @@ class Solver:
             for k in range(6):
                 opt.diss_box[k] = regions.diss_box[k]
                 opt.design_box[k] = regions.design_box[k]
-        if stream is not None:
-            opt.stream = stream if isinstance(stream, int) else int(stream.cuda_stream)
-        self.opt = opt
-        self.ctx = H.hlbm_create(lattice, self.dims, tau, Cs, opt)
-        self.xi, self.w = H.hlbm_velocity_set(lattice)
+        return opt
+
+    def _design(self, opt):
         box = list(opt.design_box)
         self.design_shape = (box[5] - box[4], box[3] - box[2], box[1] - box[0])
+
+    def configure(self, tau: float, Cs: float = 0.0, u_in: float = 0.05, regions=None,
+                  objectives: int = H.OBJ_DRAG_FFA | H.OBJ_DISSIPATION, tau_adj: float = 0.0,
+                  accum_stride: int = 1, check_every: int = 100, u_solid=(0.0, 0.0, 0.0),
+                  average_full_f: bool = False):
+        """New physical parameters for this context (same grid and storage)."""
+        opt = self._options(self.opt.storage, u_in, regions, objectives, tau_adj, accum_stride,
+                            check_every, u_solid, average_full_f)
+        H.hlbm_configure(self.ctx, tau, Cs, opt)
+        self._design(opt)
 
     # ------------------------------------------------------------------
     @property

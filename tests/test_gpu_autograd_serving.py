@@ -111,3 +111,23 @@ def test_server_rejects_requests_above_the_budget():
     with pytest.raises(H.HlbmError):
         fut.result(timeout=10)
     srv.close()
+
+
+def test_reused_contexts_give_the_same_results_as_fresh_ones():
+    # requests of one grid with different Re: the server reuses idle contexts
+    base = _requests()[0]
+    reqs = []
+    for k, Re in enumerate((30.0, 60.0, 90.0, 45.0, 75.0)):
+        D = base.dims[1] / 4.0
+        tau = 0.05 * D / Re / (1 / 3) + 0.5
+        reqs.append(Request(q=base.q, dims=base.dims, tau=tau, porosity=serving_porosity(base.dims, seed=10 + k),
+                            warm_steps=500, avg_steps=300, objective=H.OBJ_DRAG_FFA, max_iter=800,
+                            regions=base.regions, tag=k))
+    fresh = [solve_one(r) for r in reqs]
+    srv = SensitivityServer(slots=2)
+    got = [f.result(timeout=600) for f in [srv.submit(r) for r in reqs]]
+    assert srv.pool.hits >= 1
+    srv.close()
+    for a, m in zip(fresh, got):
+        assert a.J == m.J
+        assert np.array_equal(a.gradient, m.gradient)
