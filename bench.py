@@ -47,12 +47,8 @@ CS2 = 1.0 / 3.0
 # keyed by a hash of the kernel sources at capture time; a kernel changed since
 # its capture reports traffic null.  Summaries: profiles/*.md.
 MEASURED_DRAM = {
-    # profiles/k_primal_karman2d_re100.md (ncu --set full, 2 launches each parity)
-    ("291b05ef34e1616c", "karman2d_re100", "fp32", "primal_step_accumulate"): 31_829_000,
-    ("291b05ef34e1616c", "karman2d_re100", "fp32", "primal_step_plain"): 18_052_000,
-    # profiles/k_adjoint_karman2d_re100.md
-    ("291b05ef34e1616c", "karman2d_re100", "fp32", "adjoint_step_ffa"): 30_267_000,
-    ("291b05ef34e1616c", "karman2d_re100", "fp32", "adjoint_step_diss"): 30_267_000,
+    # profiles/k_primal_karman2d_re100.md (ncu --set full, one launch per AA parity)
+    ("58a4fea437ffb0bf", "karman2d_re100", "fp32", "primal_step_accumulate"): 31_817_000,
 }
 
 
@@ -85,6 +81,8 @@ def parse():
     ap.add_argument("--avg-window", type=int, default=None)
     ap.add_argument("--adjoint-tol", type=float, default=1e-6)
     ap.add_argument("--adjoint-mode", default="exact", choices=["exact", "fta"])
+    ap.add_argument("--adjoint-solver", default="fixed-point", choices=["fixed-point", "gmres"],
+                    help="the paper's iteration, or restarted GMRES on the same fixed point")
     ap.add_argument("--tau-adj", type=float, default=0.0,
                     help="adjoint relaxation time (0: tau0), the regularisation of Sec. 5.4")
     ap.add_argument("--adjoint-max-iter", type=int, default=20000)
@@ -228,7 +226,8 @@ def run_ours(args, rank, world):
     n_warm = steps - W
     stream = torch.cuda.Stream(device=dev)
     s = Solver(wl.q, wl.dims, tau_of(wl), wl.Cs, storage=storage_code(H, wl), u_in=wl.u0,
-               regions=wl.regions, stream=stream, tau_adj=args.tau_adj)
+               regions=wl.regions, stream=stream, tau_adj=args.tau_adj,
+               adjoint_solver=1 if args.adjoint_solver == "gmres" else 0)
     mode = H.ADJ_EXACT if args.adjoint_mode == "exact" else H.ADJ_FTA
     N = wl.cells
     D = 2 if wl.q == 9 else 3
@@ -487,6 +486,7 @@ def main():
                    "Re": wl.Re, "u0": wl.u0, "primal_steps": res["steps"],
                    "avg_window": res["W"], "objectives": ["drag_ffa", "dissipation"],
                    "adjoint": {"mode": args.adjoint_mode, "tau_adj": args.tau_adj or None,
+                               "solver": args.adjoint_solver,
                                "tol": args.adjoint_tol,
                                "max_iter": args.adjoint_max_iter,
                                "iters_per_step": it_per_step},

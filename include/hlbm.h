@@ -119,6 +119,13 @@ typedef struct {
                            all the BGK / frozen-turbulence linearisation reads */
   int block_x;          /* threads per block along x of the step kernels: 32, 64
                            or 128; 0 = chosen from the grid size */
+  int adjoint_solver;   /* 0: the paper's fixed-point iteration of the adjoint
+                           sweep; 1: restarted GMRES on the same fixed point
+                           (operator = two sweeps), same stopping criterion */
+  int gmres_restart;    /* Krylov basis size of solver 1 (default 30, <= 64) */
+  int gmres_inner;      /* pairs of sweeps per operator application of solver 1
+                           (>= 1): GMRES then solves (I - M^(2k)) mu = c_k, the
+                           same fixed point with the fast modes pre-damped */
   void* stream;         /* cudaStream_t to issue work on; NULL = own stream */
   void* (*dev_alloc)(size_t bytes, void* user); /* NULL = cudaMalloc */
   void (*dev_free)(void* ptr, void* user);      /* NULL = cudaFree */
@@ -172,6 +179,17 @@ int hlbm_init_equilibrium(hlbm_ctx* ctx, const void* rho, const void* u,
  * became non-finite. */
 int hlbm_run_primal(hlbm_ctx* ctx, long steps, long avg_window);
 
+/* Forward (tangent-linear) sensitivity along the primal trajectory, the
+ * quantity whose growth App. C of the paper studies: advances the state
+ * `steps` steps together with its derivative f' = (df/dd) . delta along the
+ * porosity direction delta (N values of dtype, host or device), from f' = 0,
+ * and writes to jdot_out[n] (host, `steps` doubles) the derivative
+ * dJ/dd . delta of the instantaneous objective at the canonical state each
+ * step starts from.  The state advances as in hlbm_run_primal; averages and
+ * the adjoint are cleared. */
+int hlbm_run_tangent(hlbm_ctx* ctx, long steps, const void* delta, int dtype, int on_device,
+                     int objective, double* jdot_out);
+
 /* Time-averaged objective J_bar over the last window (HLBM_ESTATE if the
  * objective was not in the accumulation mask or no window was run). */
 int hlbm_objective(hlbm_ctx* ctx, int objective, double* J_out);
@@ -180,6 +198,9 @@ int hlbm_objective(hlbm_ctx* ctx, int objective, double* J_out);
  * the averaged state (Eq. adjoint_unsteady; Eq. adjoint_steady for window
  * 1), from lambda = 0, until ||lambda^{k+1} - lambda^k||_2 / ||g_bar||_2
  * <= tol (checked every check_every iterations) or max_iter iterations.
+ * With opt.adjoint_solver = 1 the fixed point is reached by restarted GMRES
+ * (max_iter then bounds the adjoint sweeps it applies, two per Krylov
+ * step) and the criterion is evaluated once on its result.
  * mode is HLBM_ADJ_EXACT or HLBM_ADJ_FTA.  iters_out / residual_out may
  * be NULL.  Returns HLBM_NOT_CONVERGED at max_iter, HLBM_EDIVERGED or
  * HLBM_ENONFINITE on blow-up. */

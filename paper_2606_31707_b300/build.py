@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libhlbm.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["hlbm_primal.cu", "hlbm_adjoint.cu", "hlbm_capi.cu", "hlbm_noalloc.cu"]
+SOURCES = ["hlbm_primal.cu", "hlbm_adjoint.cu", "hlbm_krylov.cu", "hlbm_tangent.cu", "hlbm_capi.cu",
+           "hlbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-v"]

@@ -11,10 +11,14 @@
 #include <cstdio>
 #include <cstring>
 #include <utility>
+#include <vector>
+#include <algorithm>
 #include <string>
 
 #include "../../include/hlbm.h"
 #include "hlbm_internal.h"
+#include "hlbm_krylov.h"
+#include "hlbm_tangent.h"
 
 using namespace hlbm;
 
@@ -58,6 +62,15 @@ struct hlbm_ctx {
   size_t src_bytes = 0;
   double* red = nullptr;
   long long red_n = 0;
+  void* fd = nullptr;         // tangent state (AA array of the arithmetic type)
+  void* delta = nullptr;      // porosity direction of the tangent
+  double* jhist = nullptr;    // per-step J' of the last tangent run
+  long jhist_n = 0;
+  void* kry = nullptr;        // GMRES vectors: basis (restart + 1), w, x, c
+  size_t kry_bytes = 0;
+  double* kpart = nullptr;    // multi-dot partial sums
+  double* kdev = nullptr;     // device copies of the Arnoldi coefficients
+  double* khost = nullptr;    // pinned host copies
   int rec_mode = -1;
   double rec_taub = 0;
   long rec_generation = -1;
@@ -497,6 +510,9 @@ int hlbm_configure(hlbm_ctx* c, double tau, double Cs, const hlbm_options* opt) 
     c->opt.accum_stride = opt->accum_stride < 1 ? 1 : opt->accum_stride;
     c->opt.check_every = opt->check_every < 2 ? 100 : opt->check_every + (opt->check_every & 1);
     c->opt.average_full_f = opt->average_full_f;
+    c->opt.adjoint_solver = opt->adjoint_solver;
+    c->opt.gmres_restart = opt->gmres_restart;
+    c->opt.gmres_inner = opt->gmres_inner;
   }
   c->tau0 = tau;
   c->Cs = Cs;
@@ -692,6 +708,70 @@ int hlbm_run_primal(hlbm_ctx* c, long steps, long W) {
   return HLBM_OK;
 }
 
+int hlbm_run_tangent(hlbm_ctx* c, long steps, const void* delta, int dtype, int on_device,
+                     int objective, double* jdot_out) {
+  if (!c || !delta || !jdot_out || steps < 1) return HLBM_EINVAL;
+  const int o = obj_slot(objective);
+  if (o < 0) return set_err(c, HLBM_EINVAL, "unknown objective");
+  const long long N = c->g.N;
+  const size_t rb = real_bytes(c);
+  const size_t fd_bytes = (size_t)c->q * c->g.pitch * rb;
+  if (!c->fd && !(c->fd = dalloc(c, fd_bytes))) return set_err(c, HLBM_ENOMEM, "tangent state");
+  if (!c->delta && !(c->delta = dalloc(c, (size_t)N * rb))) return set_err(c, HLBM_ENOMEM, "direction");
+  if (c->jhist_n < steps) {
+    dfree(c, c->jhist);
+    c->jhist = (double*)dalloc(c, (size_t)steps * 8);
+    c->jhist_n = c->jhist ? steps : 0;
+    if (!c->jhist) return set_err(c, HLBM_ENOMEM, "history");
+  }
+  if (c->red_n < c->nblk) {
+    dfree(c, c->red);
+    c->red = (double*)dalloc(c, (size_t)c->nblk * 8);
+    c->red_n = c->red ? c->nblk : 0;
+    if (!c->red) return set_err(c, HLBM_ENOMEM, "reduction buffer");
+  }
+  int rc = stage_in(c, delta, dtype, on_device, N);
+  if (rc) return rc;
+  if (real_is_double(c)) {
+    HLBM_TRY(c, cudaMemcpyAsync(c->delta, c->stage, (size_t)N * 8, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  } else {
+    HLBM_TRY(c, CNT(c, launch_convert_f64_to_f32)(c->stage, (float*)c->delta, N, c->stream), "convert");
+  }
+  // the tangent starts from zero: the initial state does not depend on d
+  HLBM_TRY(c, cudaMemsetAsync(c->fd, 0, fd_bytes, c->stream), "memset");
+  TangentArgs a{};
+  a.f = c->f;
+  a.fd = c->fd;
+  a.d = c->d;
+  a.delta = c->delta;
+  a.g = c->g;
+  a.tau0 = c->tau0; a.kles = c->kles; a.u_in = c->opt.u_in; a.nu0 = c->nu0;
+  for (int k = 0; k < 3; ++k) { a.us[k] = c->opt.u_solid[k]; a.us_f[k] = (float)a.us[k]; }
+  a.tau0_f = (float)a.tau0; a.kles_f = (float)a.kles; a.u_in_f = (float)a.u_in; a.nu0_f = (float)a.nu0;
+  a.objective = objective;
+  a.ffa[0] = c->opt.ffa_x; a.ffa[1] = c->opt.ffa_y0; a.ffa[2] = c->opt.ffa_y1;
+  a.ffa[3] = c->opt.ffa_z0; a.ffa[4] = c->opt.ffa_z1;
+  std::memcpy(a.db, c->opt.diss_box, sizeof a.db);
+  a.jpart = c->red;
+  const bool les = c->Cs > 0.0;
+  for (long n = 0; n < steps; ++n) {
+    HLBM_TRY(c, CNT(c, launch_tangent)(a, c->q, c->storage, c->phase == 1, les, c->stream), "tangent");
+    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, c->nblk, c->jhist + n, c->stream), "reduce");
+    c->phase ^= 1;
+  }
+  HLBM_TRY(c, cudaMemcpyAsync(jdot_out, c->jhist, (size_t)steps * 8, cudaMemcpyDeviceToHost, c->stream), "copy");
+  unsigned err = 0;
+  rc = read_err(c, &err);
+  if (rc) return rc;
+  c->steps_done += steps;
+  c->stats.primal_steps += steps;
+  c->nsamples = 0;
+  c->acc_mask = 0;
+  c->generation++;
+  c->have_adjoint = false;
+  return HLBM_OK;
+}
+
 int hlbm_objective(hlbm_ctx* c, int obj, double* J) {
   if (!c || !J) return HLBM_EINVAL;
   const int o = obj_slot(obj);
@@ -758,6 +838,157 @@ static AdjointArgs adjoint_args(hlbm_ctx* c, int mode, const int sb[6]) {
   return a;
 }
 
+static constexpr int kMaxRestart = 64;
+
+// Restarted GMRES on the fixed point of the adjoint sweeps.  In natural layout
+// the stored adjoint state mu = S^T B_f^T lambda obeys, over one pair of
+// sweeps, mu <- M^2 mu + c.  Its fixed point solves (I - M^2) mu = c with
+// c = two sweeps from mu = 0; the operator is two sweeps without source.
+// Arnoldi with classical Gram-Schmidt applied twice, Givens rotations, FP64
+// small matrices on the host.  Returns the number of sweeps used; on exit the
+// adjoint array holds the solution x.
+static int adjoint_gmres(hlbm_ctx* c, const AdjointArgs& a, bool dbl, bool exact, double tol,
+                         long max_sweeps, long* sweeps_out) {
+  const long long L = (long long)c->q * c->g.pitch;
+  const size_t rb = real_bytes(c);
+  int m = c->opt.gmres_restart;
+  if (m < 2) m = 30;
+  if (m > kMaxRestart) m = kMaxRestart;
+  const size_t need = (size_t)(m + 4) * L * rb;
+  if (c->kry_bytes < need) {
+    dfree(c, c->kry);
+    c->kry = dalloc(c, need);
+    c->kry_bytes = c->kry ? need : 0;
+    if (!c->kry) return set_err(c, HLBM_ENOMEM, "GMRES vectors");
+  }
+  if (!c->kpart && !(c->kpart = (double*)dalloc(c, (size_t)(kMaxRestart + 1) * kKrylovBlocks * 8)))
+    return set_err(c, HLBM_ENOMEM, "GMRES partials");
+  if (!c->kdev && !(c->kdev = (double*)dalloc(c, (size_t)3 * (kMaxRestart + 1) * 8)))
+    return set_err(c, HLBM_ENOMEM, "GMRES coefficients");
+  if (!c->khost && cudaMallocHost(&c->khost, (size_t)3 * (kMaxRestart + 1) * 8) != cudaSuccess) {
+    cudaGetLastError();
+    c->khost = nullptr;
+    return set_err(c, HLBM_ENOMEM, "GMRES host buffer");
+  }
+  char* base = static_cast<char*>(c->kry);
+  auto vec = [&](long long k) { return (void*)(base + (size_t)k * L * rb); };
+  void* V = vec(0);
+  void* w = vec(m + 1);
+  void* x = vec(m + 2);
+  void* cv = vec(m + 3);
+  double* h1 = c->kdev;
+  double* h2 = c->kdev + (kMaxRestart + 1);
+  double* hn = c->kdev + 2 * (kMaxRestart + 1);
+  cudaStream_t st = c->stream;
+  AdjointArgs a0 = a;  // operator: no source
+  for (int k = 0; k < 6; ++k) a0.sb[k] = 0;
+  long sweeps = 0;
+  // one operator application = `inner` pairs of sweeps (polynomial
+  // preconditioning by the fixed-point iteration itself: the fast-decaying
+  // modes are damped before the Krylov space has to resolve them)
+  const int inner = c->opt.gmres_inner < 1 ? 1 : c->opt.gmres_inner;
+  auto pair = [&](const AdjointArgs& aa) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < inner && e == cudaSuccess; ++k) {
+      e = CNT(c, launch_adjoint)(aa, c->q, dbl, false, exact, 0, st);
+      if (e == cudaSuccess) e = CNT(c, launch_adjoint)(aa, c->q, dbl, true, exact, 0, st);
+      sweeps += 2;
+    }
+    return e;
+  };
+  auto fetch = [&](const double* dsrc, int n) -> int {
+    HLBM_TRY(c, cudaMemcpyAsync(c->khost, dsrc, (size_t)n * 8, cudaMemcpyDeviceToHost, st), "copy");
+    HLBM_TRY(c, cudaStreamSynchronize(st), "sync");
+    return HLBM_OK;
+  };
+  // c = P(0), x = 0
+  HLBM_TRY(c, cudaMemsetAsync(c->lam, 0, (size_t)L * rb, st), "memset");
+  HLBM_TRY(c, pair(a), "adjoint");
+  HLBM_TRY(c, CNT(c, launch_lincomb)(cv, c->lam, 1.0, nullptr, 0.0, L, dbl, st), "copy");
+  HLBM_TRY(c, cudaMemsetAsync(x, 0, (size_t)L * rb, st), "memset");
+  HLBM_TRY(c, CNT(c, launch_mdot)(cv, cv, 1, L, dbl, c->kpart, hn, st), "dot");
+  int rc = fetch(hn, 1);
+  if (rc) return rc;
+  const double cnorm = std::sqrt(c->khost[0]) > 0 ? std::sqrt(c->khost[0]) : 1.0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  bool first = true;
+  while (sweeps < max_sweeps) {
+    // r = c - (I - M^2) x  into V_0
+    if (first) {
+      HLBM_TRY(c, CNT(c, launch_lincomb)(V, cv, 1.0, nullptr, 0.0, L, dbl, st), "copy");
+      first = false;
+    } else {
+      HLBM_TRY(c, CNT(c, launch_lincomb)(c->lam, x, 1.0, nullptr, 0.0, L, dbl, st), "copy");
+      HLBM_TRY(c, pair(a0), "adjoint");
+      HLBM_TRY(c, CNT(c, launch_lincomb)(V, cv, 1.0, x, -1.0, L, dbl, st), "lincomb");
+      HLBM_TRY(c, CNT(c, launch_lincomb)(V, V, 1.0, c->lam, 1.0, L, dbl, st), "lincomb");
+    }
+    HLBM_TRY(c, CNT(c, launch_mdot)(V, V, 1, L, dbl, c->kpart, hn, st), "dot");
+    rc = fetch(hn, 1);
+    if (rc) return rc;
+    const double beta = std::sqrt(c->khost[0]);
+    if (!std::isfinite(beta)) return set_err(c, HLBM_ENONFINITE, "adjoint became non-finite");
+    if (beta / cnorm <= tol * 0.5) break;
+    HLBM_TRY(c, CNT(c, launch_lincomb)(V, V, 1.0 / beta, nullptr, 0.0, L, dbl, st), "scale");
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m && sweeps < max_sweeps; ++j) {
+      void* Vj = vec(j);
+      // w = (I - M^2) V_j
+      HLBM_TRY(c, CNT(c, launch_lincomb)(c->lam, Vj, 1.0, nullptr, 0.0, L, dbl, st), "copy");
+      HLBM_TRY(c, pair(a0), "adjoint");
+      HLBM_TRY(c, CNT(c, launch_lincomb)(w, Vj, 1.0, c->lam, -1.0, L, dbl, st), "lincomb");
+      // classical Gram-Schmidt, twice
+      HLBM_TRY(c, CNT(c, launch_mdot)(w, V, j + 1, L, dbl, c->kpart, h1, st), "dot");
+      HLBM_TRY(c, CNT(c, launch_maxpy)(w, V, h1, j + 1, -1.0, L, dbl, st), "axpy");
+      HLBM_TRY(c, CNT(c, launch_mdot)(w, V, j + 1, L, dbl, c->kpart, h2, st), "dot");
+      HLBM_TRY(c, CNT(c, launch_maxpy)(w, V, h2, j + 1, -1.0, L, dbl, st), "axpy");
+      HLBM_TRY(c, CNT(c, launch_mdot)(w, w, 1, L, dbl, c->kpart, hn, st), "dot");
+      HLBM_TRY(c, cudaMemcpyAsync(c->khost, h1, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, st), "copy");
+      HLBM_TRY(c, cudaMemcpyAsync(c->khost + (kMaxRestart + 1), h2, (size_t)(j + 1) * 8,
+                                  cudaMemcpyDeviceToHost, st), "copy");
+      HLBM_TRY(c, cudaMemcpyAsync(c->khost + 2 * (kMaxRestart + 1), hn, 8, cudaMemcpyDeviceToHost, st), "copy");
+      HLBM_TRY(c, cudaStreamSynchronize(st), "sync");
+      double* col = &H[(size_t)j * (m + 1)];
+      for (int i = 0; i <= j; ++i) col[i] = c->khost[i] + c->khost[(kMaxRestart + 1) + i];
+      const double hnorm = std::sqrt(c->khost[2 * (kMaxRestart + 1)]);
+      col[j + 1] = hnorm;
+      if (!std::isfinite(hnorm)) return set_err(c, HLBM_ENONFINITE, "adjoint became non-finite");
+      if (hnorm > 0) HLBM_TRY(c, CNT(c, launch_lincomb)(vec(j + 1), w, 1.0 / hnorm, nullptr, 0.0, L, dbl, st), "scale");
+      // previous rotations, then a new one that zeroes col[j + 1]
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+      }
+      const double rr = std::hypot(col[j], col[j + 1]);
+      cs[j] = rr > 0 ? col[j] / rr : 1.0;
+      sn[j] = rr > 0 ? col[j + 1] / rr : 0.0;
+      col[j] = rr;
+      col[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      k = j + 1;
+      if (std::fabs(g[j + 1]) / cnorm <= tol * 0.5 || hnorm <= 1e-300) break;
+    }
+    // y = H^-1 g (upper triangular k x k), x += V y
+    for (int i = k - 1; i >= 0; --i) {
+      double v = g[i];
+      for (int l = i + 1; l < k; ++l) v -= H[(size_t)l * (m + 1) + i] * y[l];
+      y[i] = v / H[(size_t)i * (m + 1) + i];
+    }
+    for (int i = 0; i < k; ++i) c->khost[i] = y[i];
+    HLBM_TRY(c, cudaMemcpyAsync(h1, c->khost, (size_t)k * 8, cudaMemcpyHostToDevice, st), "copy");
+    HLBM_TRY(c, CNT(c, launch_maxpy)(x, V, h1, k, 1.0, L, dbl, st), "axpy");
+    HLBM_TRY(c, cudaStreamSynchronize(st), "sync");
+  }
+  // the adjoint array holds the solution
+  HLBM_TRY(c, CNT(c, launch_lincomb)(c->lam, x, 1.0, nullptr, 0.0, L, dbl, st), "copy");
+  *sweeps_out = sweeps;
+  return HLBM_OK;
+}
+
 int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter, long* iters_out,
                        double* res_out) {
   if (!c) return HLBM_EINVAL;
@@ -815,6 +1046,15 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
   long k = 0, launches = 0;
   double r = INFINITY, rmin = INFINITY;
   int status = HLBM_NOT_CONVERGED;
+  if (c->opt.adjoint_solver == 1) {
+    // Krylov solve, then the fixed-point residual of the result from one more
+    // pair of sweeps (the same criterion as the plain iteration)
+    long sweeps = 0;
+    rc = adjoint_gmres(c, a, dbl, exact, tol, max_iter > 4 ? max_iter - 2 : 2, &sweeps);
+    if (rc) return rc;
+    k = sweeps;
+    launches = sweeps;
+  }
   auto enqueue_chunk = [&](long chunk) -> cudaError_t {
     for (long j = 0; j < chunk; ++j) {
       const bool odd = (j & 1) != 0;
@@ -831,8 +1071,9 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
     cudaGraphExecDestroy(ag.exec);
     ag.exec = nullptr;
   }
-  while (k < max_iter) {
+  while (k < max_iter || (c->opt.adjoint_solver == 1 && r == INFINITY)) {
     long chunk = max_iter - k < m ? max_iter - k : m;
+    if (c->opt.adjoint_solver == 1) chunk = 2;  // residual check of the Krylov result
     if (chunk & 1) chunk += 1;
     if (chunk < 2) chunk = 2;
     if (chunk == m && c->graphs_ok && !ag.exec) {
@@ -868,6 +1109,7 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
     if (r < rmin) rmin = r;
     if (r <= tol) { status = HLBM_OK; break; }
     if (r > 1e6 * rmin && rmin > 0) { status = HLBM_EDIVERGED; break; }
+    if (c->opt.adjoint_solver == 1) break;
   }
   HLBM_TRY(c, cudaEventRecord(c->ev1, c->stream), "event");
   HLBM_TRY(c, cudaEventSynchronize(c->ev1), "sync");
@@ -1221,6 +1463,13 @@ void hlbm_destroy(hlbm_ctx* c) {
   dfree(c, c->src);
   dfree(c, c->red);
   dfree(c, c->stage);
+  dfree(c, c->fd);
+  dfree(c, c->delta);
+  dfree(c, c->jhist);
+  dfree(c, c->kry);
+  dfree(c, c->kpart);
+  dfree(c, c->kdev);
+  if (c->khost) cudaFreeHost(c->khost);
   if (c->err_dev) cudaFree(c->err_dev);
   if (c->err_host) cudaFreeHost(c->err_host);
   if (c->scal_dev) cudaFree(c->scal_dev);

@@ -39,6 +39,33 @@ __device__ __forceinline__ void acc_add(double* sum, float* stage, long long k, 
   }
 }
 
+// The same update split in two: the old values are loaded right after the
+// populations (so that all loads of a cell are in flight together, before any
+// store), the new values are written at the end.
+template <class R, int ACC>
+struct AccSlot {
+  double s;   // FP64 sum (FP64 kernels, and the fold of FP32 kernels)
+  float t;    // FP32 staging value (FP32 kernels)
+  __device__ __forceinline__ void load(const double* sum, const float* stage, long long k) {
+    if constexpr (sizeof(R) == 8) {
+      s = sum[k];
+    } else {
+      t = stage[k];
+      if constexpr ((ACC & ACC_FLUSH) != 0) s = sum[k];
+    }
+  }
+  __device__ __forceinline__ void store(double* sum, float* stage, long long k, R v) const {
+    if constexpr (sizeof(R) == 8) {
+      sum[k] = s + (double)v;
+    } else if constexpr ((ACC & ACC_FLUSH) == 0) {
+      stage[k] = t + v;
+    } else {
+      sum[k] = s + (double)(t + v);
+      stage[k] = 0.0f;
+    }
+  }
+};
+
 // Collide the canonical state of one cell (as deviations g = f - w), store it
 // AA-style, and (ACC > 0) add the cell's samples to the running averages.
 // Returns the velocity.
@@ -88,22 +115,44 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
 
   if constexpr (ACC > 0) {
     const long long N = gr.N;
-    acc_add<R, ACC>(a.msum, a.mstage, cell, drho);
-    acc_add<R, ACC>(a.msum, a.mstage, N + cell, m.x);
-    acc_add<R, ACC>(a.msum, a.mstage, 2 * N + cell, m.y);
-    if (D == 3) acc_add<R, ACC>(a.msum, a.mstage, 3 * N + cell, m.z);
+    const bool ffa_here = (a.obj_mask & 1) && x == a.ffa[0] && y >= a.ffa[1] && y < a.ffa[2] &&
+                          z >= a.ffa[3] && z < a.ffa[4];
+    constexpr int NCD = 1 + D + D * (D + 1) / 2;  // dissipation coefficients
+    // old values of every sum this cell updates, loaded together
+    AccSlot<R, ACC> sm[1 + D], sg0[2], sg1[NCD], sdd, st;
+    AccSlot<R, ACC> sf[(ACC & ACC_FULL) != 0 ? Q : 1];
+#pragma unroll
+    for (int k = 0; k < 1 + D; ++k) sm[k].load(a.msum, a.mstage, (long long)k * N + cell);
     if constexpr ((ACC & ACC_FULL) != 0) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) acc_add<R, ACC>(a.fsum, a.fstage, (long long)i * N + cell, g[i]);
+      for (int i = 0; i < Q; ++i) sf[i].load(a.fsum, a.fstage, (long long)i * N + cell);
     }
-    if (LES) acc_add<R, ACC>(a.tsum, a.tstage, cell, tau - tau0);
+    if (LES) st.load(a.tsum, a.tstage, cell);
+    if (ffa_here) {
+      sg0[0].load(a.gsum[0], a.gstage[0], cell);
+      sg0[1].load(a.gsum[0], a.gstage[0], N + cell);
+    }
+    if (diss_here) {
+#pragma unroll
+      for (int k = 0; k < NCD; ++k) sg1[k].load(a.gsum[1], a.gstage[1], (long long)k * N + cell);
+      sdd.load(a.ddsum[1], a.ddstage[1], cell);
+    }
+
+    sm[0].store(a.msum, a.mstage, cell, drho);
+    sm[1].store(a.msum, a.mstage, N + cell, m.x);
+    sm[2].store(a.msum, a.mstage, 2 * N + cell, m.y);
+    if (D == 3) sm[D].store(a.msum, a.mstage, (long long)D * N + cell, m.z);
+    if constexpr ((ACC & ACC_FULL) != 0) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) sf[i].store(a.fsum, a.fstage, (long long)i * N + cell, g[i]);
+    }
+    if (LES) st.store(a.tsum, a.tstage, cell, tau - tau0);
     // far-field drag J_FFA on Gamma_J (Sec. 4.2): rho u_x (u0 - u_x) + c_s^2 (1 - rho);
     // dJ/df_j = (u_x^2 - c_s^2) + (u0 - 2 u_x) xi_jx
-    if ((a.obj_mask & 1) && x == a.ffa[0] && y >= a.ffa[1] && y < a.ffa[2] && z >= a.ffa[3] &&
-        z < a.ffa[4]) {
+    if (ffa_here) {
       const R u0 = par<R>(a.u_in, a.u_in_f);
-      acc_add<R, ACC>(a.gsum[0], a.gstage[0], cell, u.x * u.x - R(1.0 / 3.0));
-      acc_add<R, ACC>(a.gsum[0], a.gstage[0], N + cell, u0 - R(2) * u.x);
+      sg0[0].store(a.gsum[0], a.gstage[0], cell, u.x * u.x - R(1.0 / 3.0));
+      sg0[1].store(a.gsum[0], a.gstage[0], N + cell, u0 - R(2) * u.x);
       jp[0] += m.x * (u0 - u.x) - R(1.0 / 3.0) * drho;
     }
     // dissipation J_DISS on Omega_J (Sec. 4.3): 2 nu S:S + (1-d)/tau0 u.u,
@@ -124,27 +173,27 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
       const R trP = P.xx + P.yy + P.zz;
       const R uPU = dot3(u, PU);
       const R c2 = one_d / tau0 * R(2) / rho;
-      double* gs = a.gsum[1];
-      float* st = a.gstage[1];
-      acc_add<R, ACC>(gs, st, cell, fac * (-trP * R(1.0 / 3.0) - uPu + R(2) * d * uPU) - c2 * uu_raw);
-      acc_add<R, ACC>(gs, st, N + cell, -R(2) * d * fac * PU.x + c2 * u.x);
-      acc_add<R, ACC>(gs, st, 2 * N + cell, -R(2) * d * fac * PU.y + c2 * u.y);
-      if (D == 2) {
-        acc_add<R, ACC>(gs, st, 3 * N + cell, fac * P.xx);
-        acc_add<R, ACC>(gs, st, 4 * N + cell, fac * P.yy);
-        acc_add<R, ACC>(gs, st, 5 * N + cell, fac * P.xy);
+      R cf[NCD];
+      cf[0] = fac * (-trP * R(1.0 / 3.0) - uPu + R(2) * d * uPU) - c2 * uu_raw;
+      cf[1] = -R(2) * d * fac * PU.x + c2 * u.x;
+      cf[2] = -R(2) * d * fac * PU.y + c2 * u.y;
+      if constexpr (D == 2) {
+        cf[3] = fac * P.xx;
+        cf[4] = fac * P.yy;
+        cf[5] = fac * P.xy;
       } else {
-        acc_add<R, ACC>(gs, st, 3 * N + cell, -R(2) * d * fac * PU.z + c2 * u.z);
-        acc_add<R, ACC>(gs, st, 4 * N + cell, fac * P.xx);
-        acc_add<R, ACC>(gs, st, 5 * N + cell, fac * P.yy);
-        acc_add<R, ACC>(gs, st, 6 * N + cell, fac * P.zz);
-        acc_add<R, ACC>(gs, st, 7 * N + cell, fac * P.xy);
-        acc_add<R, ACC>(gs, st, 8 * N + cell, fac * P.xz);
-        acc_add<R, ACC>(gs, st, 9 * N + cell, fac * P.yz);
+        cf[3] = -R(2) * d * fac * PU.z + c2 * u.z;
+        cf[4] = fac * P.xx;
+        cf[5] = fac * P.yy;
+        cf[6] = fac * P.zz;
+        cf[7] = fac * P.xy;
+        cf[8] = fac * P.xz;
+        cf[9] = fac * P.yz;
       }
+#pragma unroll
+      for (int k = 0; k < NCD; ++k) sg1[k].store(a.gsum[1], a.gstage[1], (long long)k * N + cell, cf[k]);
       const Vec3<R> v{u.x - us.x, u.y - us.y, u.z - us.z};
-      const R dd = fac * (-R(2) * rho * dot3(v, PU)) - uu_raw / tau0;
-      acc_add<R, ACC>(a.ddsum[1], a.ddstage[1], cell, dd);
+      sdd.store(a.ddsum[1], a.ddstage[1], cell, fac * (-R(2) * rho * dot3(v, PU)) - uu_raw / tau0);
       jp[1] += J;
     }
   }
@@ -160,7 +209,7 @@ __global__ void __launch_bounds__(NT) k_primal(PrimalArgs a) {
   using St = Store<S>;
   using R = typename St::real;
   const Grid& gr = a.g;
-  const int x = blockIdx.x * NT + threadIdx.x;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
   auto* A = static_cast<typename St::mem*>(a.f);
   const R* dp = static_cast<const R*>(a.d);
@@ -198,8 +247,9 @@ __global__ void __launch_bounds__(NT) k_primal(PrimalArgs a) {
 template <int Q, int S>
 static cudaError_t launch_primal_qs(const PrimalArgs& a, bool odd, bool les, int acc,
                                     cudaStream_t s) {
-  dim3 grid((a.g.nx + NT - 1) / NT, a.g.ny, a.g.nz);
-#define HLBM_L(O, L_, A_) k_primal<Q, S, O, L_, A_><<<grid, NT, 0, s>>>(a)
+  const int bx = a.g.bx;
+  dim3 grid((a.g.nx + bx - 1) / bx, a.g.ny, a.g.nz);
+#define HLBM_L(O, L_, A_) k_primal<Q, S, O, L_, A_><<<grid, bx, 0, s>>>(a)
 #define HLBM_LA(O, L_)                                   \
   do {                                                   \
     switch (acc) {                                       \

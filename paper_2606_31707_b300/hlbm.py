@@ -53,6 +53,9 @@ class hlbm_options(C.Structure):
         ("check_every", C.c_int),
         ("average_full_f", C.c_int),
         ("block_x", C.c_int),
+        ("adjoint_solver", C.c_int),
+        ("gmres_restart", C.c_int),
+        ("gmres_inner", C.c_int),
         ("stream", C.c_void_p),
         ("dev_alloc", _ALLOC),
         ("dev_free", _FREE),
@@ -95,6 +98,7 @@ def _load():
         "hlbm_configure": (C.c_int, [P, C.c_double, C.c_double, C.POINTER(hlbm_options)]),
         "hlbm_init_equilibrium": (C.c_int, [P, P, P, C.c_int, C.c_int]),
         "hlbm_run_primal": (C.c_int, [P, C.c_long, C.c_long]),
+        "hlbm_run_tangent": (C.c_int, [P, C.c_long, P, C.c_int, C.c_int, C.c_int, P]),
         "hlbm_objective": (C.c_int, [P, C.c_int, C.POINTER(C.c_double)]),
         "hlbm_solve_adjoint": (C.c_int, [P, C.c_int, C.c_int, C.c_double, C.c_long,
                                          C.POINTER(C.c_long), C.POINTER(C.c_double)]),
@@ -120,7 +124,7 @@ def _load():
 _lib = _load()
 EXPORTED = ("hlbm_velocity_set", "hlbm_default_options", "hlbm_create", "hlbm_configure",
             "hlbm_set_porosity",
-            "hlbm_init_equilibrium", "hlbm_run_primal", "hlbm_objective", "hlbm_solve_adjoint",
+            "hlbm_init_equilibrium", "hlbm_run_primal", "hlbm_run_tangent", "hlbm_objective", "hlbm_solve_adjoint",
             "hlbm_gradient", "hlbm_get_field", "hlbm_set_field", "hlbm_get_stats", "hlbm_save",
             "hlbm_load", "hlbm_last_error", "hlbm_destroy", "hlbm_objective_noalloc")
 
@@ -230,6 +234,14 @@ def hlbm_init_equilibrium(ctx, rho=None, u=None):
 
 def hlbm_run_primal(ctx, steps: int, avg_window: int):
     return _check(ctx, _lib.hlbm_run_primal(ctx, steps, avg_window))
+
+
+def hlbm_run_tangent(ctx, steps: int, delta, objective: int) -> np.ndarray:
+    p, dt, dev, keep = _buf(delta)
+    out = np.empty(steps, dtype=np.float64)
+    _check(ctx, _lib.hlbm_run_tangent(ctx, steps, p, dt, dev, objective,
+                                      C.c_void_p(out.ctypes.data)))
+    return out
 
 
 def hlbm_objective(ctx, objective: int) -> float:

@@ -21,12 +21,16 @@ class Solver:
                  storage: int = H.FP32, u_in: float = 0.05, regions=None,
                  objectives: int = H.OBJ_DRAG_FFA | H.OBJ_DISSIPATION, tau_adj: float = 0.0,
                  accum_stride: int = 1, check_every: int = 100, stream=None,
-                 u_solid=(0.0, 0.0, 0.0), average_full_f: bool = False):
+                 u_solid=(0.0, 0.0, 0.0), average_full_f: bool = False,
+                 adjoint_solver: int = 0, gmres_restart: int = 30, gmres_inner: int = 1):
         self.q = lattice
         self.dims = tuple(int(v) for v in dims)
         self.dim = 2 if lattice == 9 else 3
         opt = self._options(storage, u_in, regions, objectives, tau_adj, accum_stride,
                             check_every, u_solid, average_full_f)
+        opt.adjoint_solver = adjoint_solver
+        opt.gmres_restart = gmres_restart
+        opt.gmres_inner = gmres_inner
         if stream is not None:
             opt.stream = stream if isinstance(stream, int) else int(stream.cuda_stream)
         self.opt = opt
@@ -62,10 +66,14 @@ class Solver:
     def configure(self, tau: float, Cs: float = 0.0, u_in: float = 0.05, regions=None,
                   objectives: int = H.OBJ_DRAG_FFA | H.OBJ_DISSIPATION, tau_adj: float = 0.0,
                   accum_stride: int = 1, check_every: int = 100, u_solid=(0.0, 0.0, 0.0),
-                  average_full_f: bool = False):
+                  average_full_f: bool = False, adjoint_solver: int = 0, gmres_restart: int = 30,
+                  gmres_inner: int = 1):
         """New physical parameters for this context (same grid and storage)."""
         opt = self._options(self.opt.storage, u_in, regions, objectives, tau_adj, accum_stride,
                             check_every, u_solid, average_full_f)
+        opt.adjoint_solver = adjoint_solver
+        opt.gmres_restart = gmres_restart
+        opt.gmres_inner = gmres_inner
         H.hlbm_configure(self.ctx, tau, Cs, opt)
         self._design(opt)
 

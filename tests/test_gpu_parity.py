@@ -259,3 +259,32 @@ def test_checkpoint_resume_is_bitwise():
     assert np.array_equal(b.field(H.FIELD_GBAR_DISS), ga)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("q,dims,Cs,mode", [(9, (300, 24, 1), 0.0, oadj.EXACT),
+                                           (19, (140, 10, 4), 0.1, oadj.EXACT)])
+def test_gmres_adjoint_reaches_the_same_fixed_point_in_fewer_sweeps(q, dims, Cs, mode):
+    # restarted GMRES on the adjoint fixed point (opt.adjoint_solver = 1)
+    P, d, R = _case(q, dims, Cs, tau=0.8, u_in=0.04)
+    res = {}
+    for solver in (0, 1):
+        s = Solver(P.q, P.dims, P.tau0, P.Cs, storage=H.FP64, u_in=P.u_in, regions=R,
+                   adjoint_solver=solver, gmres_restart=40)
+        perm = direction_perm(s.xi, P)
+        s.set_porosity(d)
+        s.run_primal(2999, 0)
+        fbar = s.field(H.FIELD_F)[np.argsort(perm)]
+        s.run_primal(1, 1)
+        st, it, r = s.solve_adjoint(oobj.DISS, mode, 1e-12, 400000)
+        assert st == H.OK and r <= 1e-12
+        res[solver] = (s.gradient(), it)
+        s.close()
+    out = omf.run_primal(fbar, d, P, 1, 1, R, 3)
+    lin = oadj.Linearisation(fbar, d, P, mode, None, out["tau_t_bar"])
+    G = oadj.gradient(lin, oadj.solve_adjoint_direct(lin, out[("gbar", oobj.DISS)]),
+                      out[("dJdd_bar", oobj.DISS)])
+    b = R.design_box
+    Gref = G[b[4]:b[5], b[2]:b[3], b[0]:b[1]]
+    assert rel_l2(res[1][0], Gref) <= 1e-9
+    assert rel_l2(res[0][0], Gref) <= 1e-9
+    assert res[1][1] < res[0][1]
