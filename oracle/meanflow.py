@@ -27,7 +27,7 @@ def run_primal(f, d, P: Params, steps: int, avg_window: int, regions=None,
         raise ValueError("need 1 <= avg_window <= steps")
     first = steps - avg_window
     acc = dict(fsum=np.zeros_like(f), tsum=np.zeros(f.shape[1:]), n=0)
-    objs = [o for o in (obj.FFA, obj.DISS) if objective_mask & o] if regions is not None else []
+    objs = [o for o in (obj.FFA, obj.DISS, obj.MEA) if objective_mask & o] if regions is not None else []
     for o in objs:
         acc[("g", o)] = np.zeros_like(f)
         acc[("dd", o)] = np.zeros(f.shape[1:])

@@ -26,6 +26,76 @@ from .lattice import CS2
 
 FFA = 1
 DISS = 2
+MEA = 4
+
+
+def surface_nodes(d, P: Params):
+    """Gamma_s of the momentum-exchange drag (Sec. 4.1) for a smooth porosity
+    field.  Reading: the fluid-side boundary nodes of the solid, i.e. cells
+    with d >= 1/2 that have a lattice neighbour x + xi_i (inside the domain in
+    x, periodic in y and z) with d < 1/2."""
+    nz, ny, nx = P.shape
+    solid = d < 0.5
+    surf = np.zeros_like(solid)
+    x = np.arange(nx)
+    for i in range(1, P.q):
+        cx, cy, cz = (int(c) for c in P.xi[i])
+        nb = np.roll(solid, shift=(-cz, -cy), axis=(0, 1))
+        xs = x + cx
+        ok = (xs >= 0) & (xs < nx)
+        shifted = np.zeros_like(solid)
+        shifted[..., ok] = nb[..., xs[ok]]
+        surf |= shifted
+    return surf & ~solid
+
+
+def mea_value(f, d, P: Params):
+    """J_MEA (Sec. 4.1, Eq. obj_mea) with n = e_x, the flow direction:
+    (1/A) sum_{x in Gamma_s} sum_i xi_ix (f_i(x + xi_i) - f_ibar(x)), A the
+    number of surface nodes (unit lattice area).  Terms whose neighbour
+    x + xi_i leaves the domain in x are left out."""
+    surf = surface_nodes(d, P)
+    A = max(int(surf.sum()), 1)
+    nz, ny, nx = P.shape
+    x = np.arange(nx)
+    total = 0.0
+    for i in range(P.q):
+        cx, cy, cz = (int(c) for c in P.xi[i])
+        if cx == 0:
+            continue
+        fn = np.roll(f[i], shift=(-cz, -cy), axis=(0, 1))
+        xs = x + cx
+        ok = (xs >= 0) & (xs < nx)
+        term = np.zeros(P.shape)
+        term[..., ok] = fn[..., xs[ok]] - f[P.opp[i]][..., ok]
+        total += cx * float(term[surf].sum())
+    return total / A
+
+
+def mea_partials(d, P: Params):
+    """dJ_MEA/df (constant: J_MEA is linear in f) and dJ_MEA/dd = 0 (the
+    surface set is held fixed)."""
+    surf = surface_nodes(d, P)
+    A = max(int(surf.sum()), 1)
+    nz, ny, nx = P.shape
+    g = np.zeros((P.q,) + P.shape)
+    x = np.arange(nx)
+    for i in range(P.q):
+        cx, cy, cz = (int(c) for c in P.xi[i])
+        if cx == 0:
+            continue
+        # + xi_ix f_i(y) for y = x + xi_i with x on the surface
+        src = np.roll(surf, shift=(cz, cy), axis=(0, 1))
+        xs = x - cx
+        ok = (xs >= 0) & (xs < nx)
+        hit = np.zeros(P.shape, dtype=bool)
+        hit[..., ok] = src[..., xs[ok]]
+        g[i] += cx * hit / A
+        # - xi_ix f_ibar(x) for x on the surface whose neighbour is in the domain
+        okx = np.zeros(P.shape, dtype=bool)
+        okx[..., (x + cx >= 0) & (x + cx < nx)] = True
+        g[P.opp[i]] -= cx * (surf & okx) / A
+    return g, np.zeros(P.shape)
 
 
 def _region_mask(P: Params, objective, regions):
@@ -57,6 +127,8 @@ def cell_values(f, d, P: Params, objective, regions):
 
 
 def value(f, d, P: Params, objective, regions):
+    if objective == MEA:
+        return mea_value(f, d, P)
     return float(cell_values(f, d, P, objective, regions).sum())
 
 
@@ -106,6 +178,8 @@ def tau_derivative(s, P: Params, dPi, tau_base):
 
 def partials(f, d, P: Params, objective, regions):
     """(dJ/df (q, nz, ny, nx), dJ/dd (nz, ny, nx)) of the instantaneous objective."""
+    if objective == MEA:
+        return mea_partials(d, P)
     L = local_derivatives(f, d, P)
     s = L["state"]
     mask = _region_mask(P, objective, regions)

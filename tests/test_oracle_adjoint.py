@@ -237,3 +237,37 @@ def test_symmetric_geometry_gives_symmetric_gradient():
     ny = P.dims[1]
     refl = G[:, (-np.arange(ny)) % ny, :]
     assert np.abs(G - refl).max() <= 1e-10 * np.abs(G).max()
+
+
+def test_mea_surface_nodes_and_linearity():
+    # Sec. 4.1: J_MEA is linear in f, so its derivative is exact under any
+    # finite difference; surface nodes are fluid cells next to solid ones
+    P, d, R = _tiny_case(9, 0.0, sym=True)
+    surf = obj.surface_nodes(d, P)
+    assert surf.sum() > 0 and not (surf & (d < 0.5)).any()
+    f, _ = _state(P, 31)
+    g, gd = obj.partials(f, d, P, obj.MEA, R)
+    assert np.abs(gd).max() == 0
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(f.shape)
+    lhs = obj.value(f + 0.37 * v, d, P, obj.MEA, R) - obj.value(f, d, P, obj.MEA, R)
+    assert abs(lhs - 0.37 * float((g * v).sum())) <= 1e-12 * max(1.0, abs(lhs))
+    # a uniform flow past no body exerts no force
+    Pe = Params(9, P.dims, tau0=0.8, u_in=0.04)
+    assert obj.mea_value(hlbm.initial_state(Pe), np.ones(P.shape), Pe) == 0.0
+
+
+def test_mea_steady_gradient_vs_central_fd():
+    P, d, R = _tiny_case(9, 0.0)
+    f = _steady(P, d)
+    g, gd = obj.partials(f, d, P, obj.MEA, R)
+    lin = adj.Linearisation(f, d, P, adj.EXACT)
+    G = adj.gradient(lin, adj.solve_adjoint_direct(lin, g), gd)
+    rng = np.random.default_rng(23)
+    v = rng.standard_normal(d.shape) * (np.abs(d - 0.5) > 0.1)   # keep the surface set fixed
+    h = 1e-6
+    Jp = obj.value(_steady_from(f, d + h * v, P), d + h * v, P, obj.MEA, R)
+    Jm = obj.value(_steady_from(f, d - h * v, P), d - h * v, P, obj.MEA, R)
+    fd = (Jp - Jm) / (2 * h)
+    an = float((G * v).sum())
+    assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-6)
