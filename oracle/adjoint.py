@@ -29,7 +29,11 @@ operator only.
 
 The Jacobians are assembled as scipy.sparse matrices from per-cell dense
 q x q blocks written out by the chain rule; tests pin them against central
-differences of ``hlbm.step``.
+differences of ``hlbm.step``.  For the recursive regularised collision
+(Sec. 2.2) the blocks are taken by complex-step differentiation of
+``hlbm.collide_rr`` (Squire and Trapp, 1998: f'(x) = Im f(x + i h)/h, exact
+to rounding for tiny h since nothing is subtracted), with the same
+EXACT / FTA / tau_adj semantics.
 """
 from __future__ import annotations
 
@@ -48,8 +52,49 @@ def cell_index(P: Params):
     return np.arange(nx * ny * nz).reshape(nz, ny, nx)
 
 
+CSTEP = 1e-30
+
+
+def _rr_complex(fc, dc, P: Params, mode, tau_base, tau_t_bar):
+    """collide_rr on complex inputs with the relaxation time of ``mode``."""
+    from .hlbm import collide_rr, equilibrium3, noneq_stress, porous_velocity, tau_of_norm
+    if P.Cs > 0.0 and mode == FTA:
+        tau = tau_base + tau_t_bar
+    elif P.Cs > 0.0:
+        rho, u = moments(fc, P)
+        Pi = noneq_stress(fc, equilibrium3(rho, porous_velocity(u, dc, P), P), P)
+        n2 = np.einsum("ab...,ab...->...", Pi, Pi)
+        # |Pi| -> 0: the derivative of |Pi| is taken as 0 there (as for BGK)
+        small = n2.real <= 1e-60
+        norm = np.where(small, 0.0, np.sqrt(np.where(small, 1.0, n2)))
+        tau = tau_of_norm(norm, tau_base, P)
+    else:
+        tau = np.full(P.shape, float(tau_base))
+    return collide_rr(fc, dc, P, tau=tau)
+
+
+def rr_collision_jacobians(f, d, P: Params, mode=EXACT, tau_adj=None, tau_t_bar=None):
+    """dC_i/df_j and dC_i/dd of the recursive regularised collision by complex
+    steps: perturbing f_j (or d) in every cell at once gives column j of
+    every cell's block, the collision being local."""
+    tau_base = P.tau0 if tau_adj is None else float(tau_adj)
+    if P.Cs > 0.0 and mode == FTA and tau_t_bar is None:
+        raise ValueError("FTA needs the averaged turbulent relaxation time")
+    q = P.q
+    JC = np.empty((q, q) + P.shape)
+    for j in range(q):
+        fc = f.astype(np.complex128)
+        fc[j] += 1j * CSTEP
+        JC[:, j] = _rr_complex(fc, d.astype(np.complex128), P, mode, tau_base, tau_t_bar).imag / CSTEP
+    dc = d + 1j * CSTEP
+    Cd = _rr_complex(f.astype(np.complex128), dc, P, mode, tau_base, tau_t_bar).imag / CSTEP
+    return JC, Cd
+
+
 def collision_jacobians(f, d, P: Params, mode=EXACT, tau_adj=None, tau_t_bar=None):
     """Per-cell dC_i/df_j (q, q, nz, ny, nx) and dC_i/dd (q, nz, ny, nx) at f."""
+    if P.collision == "rr":
+        return rr_collision_jacobians(f, d, P, mode, tau_adj, tau_t_bar)
     tau_base = P.tau0 if tau_adj is None else float(tau_adj)
     L = obj.local_derivatives(f, d, P)
     s = local_state(f, d, P, tau_base)

@@ -1,5 +1,7 @@
 """Primal HLBM in FP64: moments, porous equilibrium, Smagorinsky tau_eff,
-BGK collision, streaming and the inflow/outflow nodes.
+BGK collision, the third-order recursive regularised collision of the
+turbulent model (Sec. 2.2, Eq. HRRLBM), streaming and the inflow/outflow
+nodes.
 
 State layout: ``f`` has shape (q, nz, ny, nx); x is the fastest axis and
 nz = 1 in 2D.  A 'canonical state' f^n is the post-streaming,
@@ -27,10 +29,14 @@ class Params:
     Cs: float = 0.0                     # Smagorinsky constant (0: plain BGK)
     u_in: float = 0.05                  # inflow velocity
     u_s: Tuple[float, float, float] = (0.0, 0.0, 0.0)  # solid velocity
+    collision: str = "bgk"              # "bgk" (Eq. 2) or "rr" (Eq. HRRLBM)
 
     def __post_init__(self):
+        if self.collision not in ("bgk", "rr"):
+            raise ValueError("collision must be 'bgk' or 'rr'")
         self.xi, self.w, self.opp = velocity_set(self.q)
         self.xif = self.xi.astype(np.float64)
+        self.H2, self.H3 = hermite_tensors(self.xif, 2 if self.q == 9 else 3)
 
     @property
     def shape(self):
@@ -41,6 +47,20 @@ class Params:
     def nu0(self):
         # nu = c_s^2 (tau - 1/2)   (Sec. 2.1, viscosity-relaxation relation)
         return CS2 * (self.tau0 - 0.5)
+
+
+def hermite_tensors(xi, dim):
+    """Hermite polynomials of the discrete velocities (Sec. 2.2):
+    H2_ab = xi_a xi_b - c_s^2 delta_ab, shape (q, 3, 3);
+    H3_abc = xi_a xi_b xi_c - c_s^2 (xi_a delta_bc + xi_b delta_ac + xi_c delta_ab),
+    shape (q, 3, 3, 3).  Indices run over the lattice's ``dim`` axes (the
+    z entries are zero in 2D)."""
+    I = np.diag([1.0, 1.0, 1.0 if dim == 3 else 0.0])
+    H2 = np.einsum("ia,ib->iab", xi, xi) - CS2 * I[None]
+    H3 = (np.einsum("ia,ib,ic->iabc", xi, xi, xi)
+          - CS2 * (np.einsum("ia,bc->iabc", xi, I) + np.einsum("ib,ac->iabc", xi, I)
+                   + np.einsum("ic,ab->iabc", xi, I)))
+    return H2, H3
 
 
 def tau_from_reynolds(u0: float, L: float, Re: float) -> float:
@@ -103,9 +123,13 @@ def tau_effective(Pi, tau_base, P: Params):
     norm = np.sqrt(np.einsum("ab...,ab...->...", Pi, Pi))
     if P.Cs == 0.0:
         return np.full(norm.shape, float(tau_base)), norm
+    return tau_of_norm(norm, tau_base, P), norm
+
+
+def tau_of_norm(norm, tau_base, P: Params):
+    """The positive root above as a function of ||Pi|| (also for complex input)."""
     c = (P.Cs ** 2 / CS2) * math.sqrt(2.0) / (2.0 * CS2)   # = 9 sqrt(2)/2 * Cs^2
-    te = 0.5 * (tau_base + np.sqrt(tau_base * tau_base + 4.0 * c * norm))
-    return te, norm
+    return 0.5 * (tau_base + np.sqrt(tau_base * tau_base + 4.0 * c * norm))
 
 
 def local_state(f, d, P: Params, tau_base=None):
@@ -120,9 +144,64 @@ def local_state(f, d, P: Params, tau_base=None):
     return dict(rho=rho, u=u, ut=ut, feq=feq, Pi=Pi, tau=te, norm=norm)
 
 
+def equilibrium3(rho, ut, P: Params):
+    """Third-order Hermite equilibrium of the recursive regularised model
+    (Sec. 2.2): w_i (a0^(0) + H1_i.a0^(1)/c_s^2 + H2_i:a0^(2)/(2 c_s^4)
+    + H3_i:a0^(3)/(6 c_s^6)) with a0^(0) = rho and a0^(n) = a0^(n-1) u~,
+    ':' the full tensor contraction."""
+    a1 = rho * ut
+    a2 = np.einsum("a...,b...->ab...", a1, ut)
+    a3 = np.einsum("ab...,c...->abc...", a2, ut)
+    h1 = np.tensordot(P.xif, a1, axes=(1, 0))
+    h2 = np.tensordot(P.H2, a2, axes=([1, 2], [0, 1]))
+    h3 = np.tensordot(P.H3, a3, axes=([1, 2, 3], [0, 1, 2]))
+    wexp = P.w.reshape((P.q,) + (1,) * rho.ndim)
+    return wexp * (rho[None] + h1 / CS2 + h2 / (2 * CS2 ** 2) + h3 / (6 * CS2 ** 3))
+
+
+def regularised_noneq(fneq, ut, P: Params):
+    """f^(1) of Sec. 2.2: the non-equilibrium part expanded in Hermite
+    polynomials up to third order.  Reading: a1^(n) = sum_i H_i^(n) f^neq_i
+    for n <= 2 (f^neq = f - f^eq), and the third-order coefficient is built
+    recursively, a1^(3)_abc = u~_a a1^(2)_bc + u~_b a1^(2)_ac + u~_c a1^(2)_ab,
+    as in the recursive regularised schemes the paper builds on."""
+    a0 = fneq.sum(axis=0)
+    a1 = np.tensordot(P.xif.T, fneq, axes=(1, 0))
+    a2 = np.tensordot(P.H2.transpose(1, 2, 0), fneq, axes=(2, 0))
+    a3 = (np.einsum("a...,bc...->abc...", ut, a2) + np.einsum("b...,ac...->abc...", ut, a2)
+          + np.einsum("c...,ab...->abc...", ut, a2))
+    h1 = np.tensordot(P.xif, a1, axes=(1, 0))
+    h2 = np.tensordot(P.H2, a2, axes=([1, 2], [0, 1]))
+    h3 = np.tensordot(P.H3, a3, axes=([1, 2, 3], [0, 1, 2]))
+    wexp = P.w.reshape((P.q,) + (1,) * a0.ndim)
+    return wexp * (a0[None] + h1 / CS2 + h2 / (2 * CS2 ** 2) + h3 / (6 * CS2 ** 3))
+
+
+def collide_rr(f, d, P: Params, tau=None, tau_base=None):
+    """Recursive regularised collision f* = f^eq + (1 - 1/tau_eff) f^(1)
+    (Sec. 2.2, Eq. HRRLBM) with the third-order porous equilibrium at
+    (rho, u~).  tau_eff is the Smagorinsky relaxation time of the
+    non-equilibrium stress (Eq. tauEff; unchanged from the BGK model, since
+    the third-order terms do not alter second moments), or the given
+    ``tau`` (frozen)."""
+    if tau_base is None:
+        tau_base = P.tau0
+    rho, u = moments(f, P)
+    ut = porous_velocity(u, d, P)
+    feq = equilibrium3(rho, ut, P)
+    fneq = f - feq
+    if tau is None:
+        tau, _ = tau_effective(noneq_stress(f, feq, P), tau_base, P)
+    f1 = regularised_noneq(fneq, ut, P)
+    return feq + (1.0 - 1.0 / tau) * f1
+
+
 def collide(f, d, P: Params):
-    """BGK relaxation f* = f - (f - f^eq)/tau_eff (Sec. 2.1, Eq. 2)."""
+    """One collision: BGK relaxation f* = f - (f - f^eq)/tau_eff (Sec. 2.1,
+    Eq. 2), or the recursive regularised collision when P.collision = "rr"."""
     s = local_state(f, d, P)
+    if P.collision == "rr":
+        return collide_rr(f, d, P, tau=s["tau"]), s
     return f - (f - s["feq"]) / s["tau"], s
 
 
