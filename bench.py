@@ -48,7 +48,7 @@ CS2 = 1.0 / 3.0
 # its capture reports traffic null.  Summaries: profiles/*.md.
 MEASURED_DRAM = {
     # profiles/k_primal_karman2d_re100.md (ncu --set full, one launch per AA parity)
-    ("58a4fea437ffb0bf", "karman2d_re100", "fp32", "primal_step_accumulate"): 31_817_000,
+    ("58a4fea437ffb0bf", "karman2d_re100", "fp32", "bgk", "primal_step_accumulate"): 31_817_000,
 }
 
 
@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--tau-adj", type=float, default=0.0,
                     help="adjoint relaxation time (0: tau0), the regularisation of Sec. 5.4")
     ap.add_argument("--adjoint-max-iter", type=int, default=20000)
+    ap.add_argument("--collision", default="bgk", choices=["bgk", "rr"],
+                    help="BGK (Sec. 2.1) or the recursive regularised collision (Sec. 2.2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", default=None, choices=["fp64", "fp32", "fp16dev", "bf16dev"],
@@ -107,7 +109,7 @@ def job_shape(wl, args):
 # algorithmic bytes per lattice update
 # ---------------------------------------------------------------------------
 
-def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False):
+def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False, rr=False):
     """Algorithmic bytes per lattice update of each kernel (reads + writes).
 
     Averaging step: the populations and porosity of a plain step plus, for
@@ -117,7 +119,9 @@ def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False):
     (16 B + 8 B, amortised 1.5 B).  Sums: density and momentum (1 + D), all q
     populations and tau_eff - tau0 when Cs > 0, and inside the objective
     regions the dJ/df coefficients (2 on the drag plane, 1 + D + D(D+1)/2 in
-    the dissipation box) and dJ/dd."""
+    the dissipation box) and dJ/dd.  The regularised collision (rr) keeps the
+    D(D+1)/2 second moments instead of the q populations, and its adjoint
+    record is rho, u, omega and the stress (2 + D + D(D+1)/2 planes)."""
     q = wl.q
     nx, ny, nz = wl.dims
     N = nx * ny * nz
@@ -129,9 +133,12 @@ def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False):
     diss_cells = (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
     les = wl.Cs > 0
     sb = 16.0 if real_bytes == 8 else 8.0 + 24.0 / 16
-    acc = plain + sb * (1 + D) + (sb * (q + 1) if les else 0)
+    if rr:
+        acc = plain + sb * (1 + D + D * (D + 1) // 2) + (sb if les else 0)
+    else:
+        acc = plain + sb * (1 + D) + (sb * (q + 1) if les else 0)
     acc += (ffa_cells * sb * 2 + diss_cells * sb * (1 + D + D * (D + 1) // 2 + 1)) / N
-    rec = q if exact_rec else D + 2
+    rec = D + 2 + D * (D + 1) // 2 if rr else (q if exact_rec else D + 2)
     adj_ffa = (2 * q + rec + 1) * real_bytes + ffa_cells * q * real_bytes / N
     adj_diss = (2 * q + rec + 1) * real_bytes + diss_cells * q * real_bytes / N
     return dict(plain=plain, acc=acc, adj_ffa=adj_ffa, adj_diss=adj_diss)
@@ -227,7 +234,8 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream(device=dev)
     s = Solver(wl.q, wl.dims, tau_of(wl), wl.Cs, storage=storage_code(H, wl), u_in=wl.u0,
                regions=wl.regions, stream=stream, tau_adj=args.tau_adj,
-               adjoint_solver=1 if args.adjoint_solver == "gmres" else 0)
+               adjoint_solver=1 if args.adjoint_solver == "gmres" else 0,
+               collision=H.COLL_RR if args.collision == "rr" else H.COLL_BGK)
     mode = H.ADJ_EXACT if args.adjoint_mode == "exact" else H.ADJ_FTA
     N = wl.cells
     D = 2 if wl.q == 9 else 3
@@ -339,7 +347,8 @@ def roofline_of(res, args, H_storage_bytes, real_bytes):
     wl = res["wl"]
     N = wl.cells
     bm = bytes_model(wl, H_storage_bytes, real_bytes,
-                     exact_rec=(wl.Cs > 0 and args.adjoint_mode == "exact"))
+                     exact_rec=(wl.Cs > 0 and args.adjoint_mode == "exact"),
+                     rr=args.collision == "rr")
     ph = res["phase"]
     cand = []
     if ph["plain_launch"]:
@@ -353,7 +362,7 @@ def roofline_of(res, args, H_storage_bytes, real_bytes):
     per_launch_s = ms * 1e-3 / launches
     achieved = bpl * N / per_launch_s / 1e9
     src_hash = kernel_source_hash()
-    traffic = MEASURED_DRAM.get((src_hash, wl.name, wl.storage, name))
+    traffic = MEASURED_DRAM.get((src_hash, wl.name, wl.storage, args.collision, name))
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -483,7 +492,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": wl.name, "grid": list(wl.dims),
                    "lattice": f"D{2 if wl.q == 9 else 3}Q{wl.q}", "storage": wl.storage,
-                   "Re": wl.Re, "u0": wl.u0, "primal_steps": res["steps"],
+                   "collision": args.collision, "Re": wl.Re, "u0": wl.u0, "primal_steps": res["steps"],
                    "avg_window": res["W"], "objectives": ["drag_ffa", "dissipation"],
                    "adjoint": {"mode": args.adjoint_mode, "tau_adj": args.tau_adj or None,
                                "solver": args.adjoint_solver,

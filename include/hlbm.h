@@ -55,8 +55,23 @@ enum {
   HLBM_BF16DEV = 3  /* bfloat16 storage of f_i - w_i, float arithmetic */
 };
 
-/* objectives: bit mask for accumulation, single value for solve/gradient */
-enum { HLBM_OBJ_DRAG_FFA = 1, HLBM_OBJ_DISSIPATION = 2 };
+/* objectives: bit mask for accumulation, single value for solve/gradient.
+ * HLBM_OBJ_DRAG_MEA is the momentum-exchange drag of Sec. 4.1 over the
+ * fluid-side surface nodes (d >= 1/2 next to d < 1/2), flow direction x,
+ * normalised by the number of surface nodes; it is linear in f, so its
+ * average is taken as J(f_bar) and its derivative is constant (averaging it
+ * turns on average_full_f); the surface set is held fixed (dJ/dd = 0). */
+enum { HLBM_OBJ_DRAG_FFA = 1, HLBM_OBJ_DISSIPATION = 2, HLBM_OBJ_DRAG_MEA = 4 };
+
+/* collision model: BGK (Sec. 2.1, Eq. 2; Smagorinsky tau_eff when Cs > 0) or
+ * the third-order recursive regularised collision of the turbulent model
+ * (Sec. 2.2, Eq. HRRLBM): f* = f^eq3(rho, u~) + (1 - 1/tau_eff) f^(1), f^eq3
+ * the third-order Hermite equilibrium and f^(1) the non-equilibrium part
+ * expanded to third order with the recursive third-order coefficient
+ * u~ (x) Pi.  Its averages keep the second moments of f instead of f itself,
+ * and its adjoint reads only (rho, u, Pi) of f_bar.  The tangent-linear step
+ * supports BGK only. */
+enum { HLBM_COLL_BGK = 0, HLBM_COLL_RR = 1 };
 
 /* adjoint linearisation: full Jacobian or frozen turbulence (Sec. 5.4) */
 enum { HLBM_ADJ_EXACT = 0, HLBM_ADJ_FTA = 1 };
@@ -124,12 +139,15 @@ typedef struct {
                            (operator = two sweeps), same stopping criterion */
   int gmres_restart;    /* Krylov basis size of solver 1 (default 30, <= 64) */
   int gmres_inner;      /* pairs of sweeps per operator application of solver 1
-                           (>= 1): GMRES then solves (I - M^(2k)) mu = c_k, the
-                           same fixed point with the fast modes pre-damped */
+                           (>= 1; default 100): GMRES then solves
+                           (I - M^(2k)) mu = c_k, the same fixed point with the
+                           fast modes pre-damped */
   void* stream;         /* cudaStream_t to issue work on; NULL = own stream */
   void* (*dev_alloc)(size_t bytes, void* user); /* NULL = cudaMalloc */
   void (*dev_free)(void* ptr, void* user);      /* NULL = cudaFree */
   void* alloc_user;
+  int collision;        /* HLBM_COLL_BGK (default) or HLBM_COLL_RR; fixed at
+                           hlbm_create (hlbm_configure rejects a change) */
 } hlbm_options;
 
 /* Velocity set of the library's direction order: xi (q x 3 ints, may be

@@ -139,6 +139,172 @@ __device__ __forceinline__ void transpose_collide(const LinCell<Q, R, EXACT>& c,
   }
 }
 
+// ----------------------------------------------------------------------------
+// Recursive regularised collision (Sec. 2.2, Eq. HRRLBM) transposed.  The
+// collision depends on f only through rho, j = sum xi f and M2 = sum xi xi f,
+// so (C_f^T mu)_j = G_rho + G_j . xi_j + xi_j . G_M . xi_j, where G_* are the
+// derivatives of L = sum_i mu_i C_i with respect to those moments.  They
+// are taken by reverse-mode differentiation of L written in the variables
+// (rho, u~, a1 = j - rho u~, Pi = M2 - rho u~ u~ - c_s^2 (rho - 1) I, omega):
+//   L = rho (s0 + 3 s1.u~ + 9/2 C2 - 3/2 s0 u~.u~) + 9/2 rho (A3 - (s1.u~) u~.u~)
+//       + (1 - omega) F,
+//   F = 3 s1.a1 + 9/2 (CP - s0 tr Pi / 3) + 9/2 (3 B3 - (s1.u~) tr Pi - 2 s1.Pi u~),
+// with the weighted sums of mu over the lattice (c = xi.u~, p = xi.Pi.xi)
+//   s0 = sum w mu, s1 = sum w mu xi, C2 = sum w mu c^2, A3 = sum w mu c^3,
+//   CP = sum w mu p, B3 = sum w mu c p,
+// and their derivatives V1 = sum w mu c xi, T1 = sum w mu c^2 xi,
+// T2 = sum w mu p xi, s2 = sum w mu xi xi, T3 = sum w mu c xi xi.
+// The exact LES variant adds the dependence of omega on |Pi|.  The
+// derivative with respect to u~ also gives the porosity gradient,
+// dL/dd = (dL/du~) . (u - u_s).
+// ----------------------------------------------------------------------------
+template <class R, bool EXACT> struct RRCell {
+  R rho, om, d;
+  Vec3<R> u, ut;
+  Sym<R> P;
+  R nP, tau;  // EXACT only
+};
+
+template <int Q, class R, bool EXACT>
+__device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
+                                         RRCell<R, EXACT>& c) {
+  constexpr int D = Lat<Q>::D;
+  const R* rec = static_cast<const R*>(a.rec);
+  const long long rp = a.rec_pitch;
+  c.d = d;
+  c.rho = rec[cell];
+  c.u.x = rec[rp + cell];
+  c.u.y = rec[2 * rp + cell];
+  c.u.z = D == 3 ? rec[3 * rp + cell] : R(0);
+  c.om = rec[(D + 1) * rp + cell];
+  const R* pp = rec + (D + 2) * rp + cell;
+  if constexpr (D == 2) {
+    c.P = Sym<R>{pp[0], pp[rp], R(0), pp[2 * rp], R(0), R(0)};
+  } else {
+    c.P = Sym<R>{pp[0], pp[rp], pp[2 * rp], pp[3 * rp], pp[4 * rp], pp[5 * rp]};
+  }
+  const R one_d = R(1) - d;
+  const Vec3<R> us{par<R>(a.us[0], a.us_f[0]), par<R>(a.us[1], a.us_f[1]),
+                   par<R>(a.us[2], a.us_f[2])};
+  c.ut = Vec3<R>{d * c.u.x + one_d * us.x, d * c.u.y + one_d * us.y, d * c.u.z + one_d * us.z};
+  if constexpr (EXACT) {
+    c.nP = sqrt_r<R>(sym_norm2(c.P));
+    c.tau = tau_smagorinsky<R>(par<R>(a.tau_b, a.tau_b_f), par<R>(a.kles, a.kles_f), c.nP);
+    c.om = R(1) / c.tau;
+  }
+}
+
+template <int Q, class R>
+__device__ __forceinline__ void add_xi(Vec3<R>& v, int i, R s) {
+  using L = Lat<Q>;
+  if (L::cx(i)) v.x += L::cx(i) > 0 ? s : -s;
+  if (L::cy(i)) v.y += L::cy(i) > 0 ? s : -s;
+  if (L::cz(i)) v.z += L::cz(i) > 0 ? s : -s;
+}
+
+template <int Q, class R>
+__device__ __forceinline__ void add_xixi(Sym<R>& S, int i, R s) {
+  using L = Lat<Q>;
+  const int a = L::cx(i), b = L::cy(i), c = L::cz(i);
+  if (a) S.xx += s;
+  if (b) S.yy += s;
+  if (c) S.zz += s;
+  if (a && b) S.xy += a * b > 0 ? s : -s;
+  if (a && c) S.xz += a * c > 0 ? s : -s;
+  if (b && c) S.yz += b * c > 0 ? s : -s;
+}
+
+// mu <- C_f^T mu at one cell; gut (optional) receives dL/du~
+template <int Q, class R, bool EXACT>
+__device__ __forceinline__ void rr_transpose(const RRCell<R, EXACT>& c, R (&mu)[Q],
+                                             const AdjointArgs& a, Vec3<R>* gut) {
+  using L = Lat<Q>;
+  constexpr bool D3 = L::D == 3;
+  const Vec3<R>& ut = c.ut;
+  const Sym<R>& P = c.P;
+  const R uu = dot3(ut, ut);
+  const R trP = P.xx + P.yy + P.zz;
+  R s0 = 0, C2 = 0, A3 = 0, B3 = 0, CP = 0;
+  Vec3<R> s1{0, 0, 0}, V1{0, 0, 0}, T1{0, 0, 0}, T2{0, 0, 0};
+  Sym<R> s2{0, 0, 0, 0, 0, 0}, T3{0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const R wm = R(L::w(i)) * mu[i];
+    const R cu = xi_dot<Q>(i, ut);
+    const R xPx = xi_P_xi<Q>(i, P);
+    s0 += wm;
+    C2 += wm * cu * cu;
+    A3 += wm * cu * cu * cu;
+    B3 += wm * cu * xPx;
+    CP += wm * xPx;
+    add_xi<Q>(s1, i, wm);
+    add_xi<Q>(V1, i, wm * cu);
+    add_xi<Q>(T1, i, wm * cu * cu);
+    add_xi<Q>(T2, i, wm * xPx);
+    add_xixi<Q>(s2, i, wm);
+    add_xixi<Q>(T3, i, wm * cu);
+  }
+  const R rho = c.rho, om = c.om, c1 = R(1) - om;
+  const R su = dot3(s1, ut);
+  const Vec3<R> a1{rho * (c.u.x - ut.x), rho * (c.u.y - ut.y), rho * (c.u.z - ut.z)};
+  const Vec3<R> Ps1 = sym_mul(P, s1);
+  const R sPu = dot3(Ps1, ut);
+  const R F = R(3) * dot3(s1, a1) + R(4.5) * (CP - s0 * trP * R(1.0 / 3.0)) +
+              R(4.5) * (R(3) * B3 - su * trP - R(2) * sPu);
+  R Lrho = s0 + R(3) * su + R(4.5) * C2 - R(1.5) * s0 * uu + R(4.5) * (A3 - su * uu);
+  const Vec3<R> La1{R(3) * c1 * s1.x, R(3) * c1 * s1.y, R(3) * c1 * s1.z};
+  // dL/dPi (symmetric, dL = G : dPi)
+  const R k45 = R(4.5) * c1;
+  const R diag = -s0 * R(1.0 / 3.0) - su;
+  Sym<R> G{k45 * (s2.xx + diag + R(3) * T3.xx - R(2) * s1.x * ut.x),
+           k45 * (s2.yy + diag + R(3) * T3.yy - R(2) * s1.y * ut.y),
+           D3 ? k45 * (s2.zz + diag + R(3) * T3.zz - R(2) * s1.z * ut.z) : R(0),
+           k45 * (s2.xy + R(3) * T3.xy - (s1.x * ut.y + ut.x * s1.y)),
+           k45 * (s2.xz + R(3) * T3.xz - (s1.x * ut.z + ut.x * s1.z)),
+           k45 * (s2.yz + R(3) * T3.yz - (s1.y * ut.z + ut.y * s1.z))};
+  if constexpr (EXACT) {
+    if (c.nP > pi_eps<R>()) {
+      // omega(|Pi|): dL/dPi += (-F)(-omega^2) k / ((2 tau - tau_b) |Pi|) Pi
+      const R e = F * om * om * par<R>(a.kles, a.kles_f) /
+                  ((R(2) * c.tau - par<R>(a.tau_b, a.tau_b_f)) * c.nP);
+      G.xx += e * P.xx; G.yy += e * P.yy; G.zz += e * P.zz;
+      G.xy += e * P.xy; G.xz += e * P.xz; G.yz += e * P.yz;
+    }
+  }
+  // explicit dL/du~
+  Vec3<R> Lu;
+  Lu.x = rho * (R(3) * s1.x + R(9) * V1.x - R(3) * s0 * ut.x) +
+         R(4.5) * rho * (R(3) * T1.x - s1.x * uu - R(2) * su * ut.x) +
+         k45 * (R(3) * T2.x - trP * s1.x - R(2) * Ps1.x);
+  Lu.y = rho * (R(3) * s1.y + R(9) * V1.y - R(3) * s0 * ut.y) +
+         R(4.5) * rho * (R(3) * T1.y - s1.y * uu - R(2) * su * ut.y) +
+         k45 * (R(3) * T2.y - trP * s1.y - R(2) * Ps1.y);
+  Lu.z = rho * (R(3) * s1.z + R(9) * V1.z - R(3) * s0 * ut.z) +
+         R(4.5) * rho * (R(3) * T1.z - s1.z * uu - R(2) * su * ut.z) +
+         k45 * (R(3) * T2.z - trP * s1.z - R(2) * Ps1.z);
+  // through a1 = j - rho u~ and Pi = M2 - rho u~ u~ - (rho - 1)/3 I
+  const Vec3<R> Gu = sym_mul(G, ut);
+  const Vec3<R> Gut{Lu.x - rho * La1.x - R(2) * rho * Gu.x, Lu.y - rho * La1.y - R(2) * rho * Gu.y,
+                    Lu.z - rho * La1.z - R(2) * rho * Gu.z};
+  Lrho += -dot3(La1, ut) - dot3(ut, Gu) - (G.xx + G.yy + G.zz) * R(1.0 / 3.0);
+  // through u~ = d j / rho + (1 - d) u_s
+  const R dr = c.d / rho;
+  const Vec3<R> Gj{La1.x + dr * Gut.x, La1.y + dr * Gut.y, La1.z + dr * Gut.z};
+  Lrho -= dr * dot3(Gut, c.u);
+#pragma unroll
+  for (int j = 0; j < Q; ++j) mu[j] = Lrho + xi_dot<Q>(j, Gj) + xi_P_xi<Q>(j, G);
+  if (gut) *gut = Gut;
+}
+
+template <int Q, class R, bool EXACT>
+__device__ __forceinline__ void transpose_collide(const RRCell<R, EXACT>& c, R (&mu)[Q],
+                                                  const AdjointArgs& a) {
+  rr_transpose<Q, R, EXACT>(c, mu, a, nullptr);
+}
+
+template <int Q, class R, bool EXACT, bool RR> struct CellOf { using T = LinCell<Q, R, EXACT>; };
+template <int Q, class R, bool EXACT> struct CellOf<Q, R, EXACT, true> { using T = RRCell<R, EXACT>; };
+
 template <int Q, class R>
 __device__ __forceinline__ void add_source(const AdjointArgs& a, int x, int y, int z, R (&v)[Q]) {
   if (x >= a.sb[0] && x < a.sb[1] && y >= a.sb[2] && y < a.sb[3] && z >= a.sb[4] && z < a.sb[5]) {
@@ -196,7 +362,7 @@ __device__ __forceinline__ void residual_io(const AdjointArgs& a, long long cell
   if (RES == 2) rp += (double)acc;
 }
 
-template <int Q, class R, bool ODD, bool EXACT, int RES>
+template <int Q, class R, bool ODD, bool EXACT, int RES, bool RR>
 __global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
   constexpr int S = RealStore<R>::S;
   const Grid& g = a.g;
@@ -210,7 +376,7 @@ __global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
     const Rows rows = make_rows<Lat<Q>::D>(g, y, z);
     R v[Q];
     aa_load<Q, S, ODD, -1>(A, g, rows, x, cell, v);
-    LinCell<Q, R, EXACT> c;
+    typename CellOf<Q, R, EXACT, RR>::T c;
     load_lin<Q, R, EXACT>(a, cell, dp[cell], c);
     transpose_collide<Q, R, EXACT>(c, v, a);
     add_source<Q, R>(a, x, y, z, v);
@@ -218,7 +384,7 @@ __global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
     if (x == g.nx - 2) {
       R vo[Q];
       aa_load<Q, S, ODD, -1>(A, g, rows, x + 1, cell + 1, vo);
-      LinCell<Q, R, EXACT> co;
+      typename CellOf<Q, R, EXACT, RR>::T co;
       load_lin<Q, R, EXACT>(a, cell + 1, dp[cell + 1], co);
       transpose_collide<Q, R, EXACT>(co, vo, a);
       add_source<Q, R>(a, x + 1, y, z, vo);
@@ -243,12 +409,12 @@ __global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
 
 int adjoint_blocks(const Grid& g) { return ((g.nx + g.bx - 1) / g.bx) * g.ny * g.nz; }
 
-template <int Q, class R>
+template <int Q, class R, bool RR>
 static cudaError_t launch_adj_qr(const AdjointArgs& a, bool odd, bool exact, int res,
                                  cudaStream_t s) {
   const int bx = a.g.bx;
   dim3 grid((a.g.nx + bx - 1) / bx, a.g.ny, a.g.nz);
-#define HLBM_A(O, E, RS) k_adjoint<Q, R, O, E, RS><<<grid, bx, 0, s>>>(a)
+#define HLBM_A(O, E, RS) k_adjoint<Q, R, O, E, RS, RR><<<grid, bx, 0, s>>>(a)
 #define HLBM_AR(O, E) \
   do { if (res == 0) HLBM_A(O, E, 0); else if (res == 1) HLBM_A(O, E, 1); else HLBM_A(O, E, 2); } while (0)
   if (!odd) { if (!exact) HLBM_AR(false, false); else HLBM_AR(false, true); }
@@ -258,13 +424,20 @@ static cudaError_t launch_adj_qr(const AdjointArgs& a, bool odd, bool exact, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint(const AdjointArgs& a, int q, bool dbl, bool odd, bool exact, int res,
-                           cudaStream_t s) {
-  if (q == 9) return dbl ? launch_adj_qr<9, double>(a, odd, exact, res, s)
-                         : launch_adj_qr<9, float>(a, odd, exact, res, s);
-  if (q == 19) return dbl ? launch_adj_qr<19, double>(a, odd, exact, res, s)
-                          : launch_adj_qr<19, float>(a, odd, exact, res, s);
+template <bool RR>
+static cudaError_t launch_adj_c(const AdjointArgs& a, int q, bool dbl, bool odd, bool exact, int res,
+                                cudaStream_t s) {
+  if (q == 9) return dbl ? launch_adj_qr<9, double, RR>(a, odd, exact, res, s)
+                         : launch_adj_qr<9, float, RR>(a, odd, exact, res, s);
+  if (q == 19) return dbl ? launch_adj_qr<19, double, RR>(a, odd, exact, res, s)
+                          : launch_adj_qr<19, float, RR>(a, odd, exact, res, s);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adjoint(const AdjointArgs& a, int q, bool dbl, bool odd, bool exact, int res,
+                           bool rr, cudaStream_t s) {
+  return rr ? launch_adj_c<true>(a, q, dbl, odd, exact, res, s)
+            : launch_adj_c<false>(a, q, dbl, odd, exact, res, s);
 }
 
 // ----------------------------------------------------------------------------
@@ -278,7 +451,7 @@ __global__ void __launch_bounds__(NT) k_prep(PrepArgs a) {
   const long long cell = cell_of(g, x, blockIdx.y, blockIdx.z);
   R* rec = static_cast<R*>(a.rec);
   const long long rp = a.rec_pitch;
-  if (a.exact) {
+  if (a.exact && !a.rr) {
 #pragma unroll
     for (int i = 0; i < Q; ++i)
       rec[(long long)i * rp + cell] = (R)(a.fsum[(long long)i * g.N + cell] * a.inv_n);
@@ -294,6 +467,24 @@ __global__ void __launch_bounds__(NT) k_prep(PrepArgs a) {
   rec[2 * rp + cell] = (R)(a.msum[2 * g.N + cell] * a.inv_n * ir);
   if (Lat<Q>::D == 3) rec[3 * rp + cell] = (R)(a.msum[3 * g.N + cell] * a.inv_n * ir);
   rec[(Lat<Q>::D + 1) * rp + cell] = (R)(1.0 / tau);
+  if (a.rr) {
+    // non-equilibrium stress of f_bar: Pi = M2 - rho u~ u~ - (rho - 1)/3 I
+    constexpr int D = Lat<Q>::D;
+    const double d = (double)static_cast<const R*>(a.d)[cell];
+    double ut[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < D; ++k) ut[k] = d * a.msum[(1 + k) * g.N + cell] * a.inv_n * ir + (1.0 - d) * a.us[k];
+    const double t = (rho - 1.0) / 3.0;
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    // plane order of the sums and of the record: 2D xx, yy, xy; 3D xx, yy, zz, xy, xz, yz
+    const int map2[3] = {0, 1, 3};
+    const int np = D == 2 ? 3 : 6;
+    for (int k = 0; k < np; ++k) {
+      const int e = D == 2 ? map2[k] : k;
+      double v = a.msum[(long long)(1 + D + k) * g.N + cell] * a.inv_n - rho * ut[ia[e]] * ut[ib[e]];
+      if (e < 3) v -= t;
+      rec[(long long)(D + 2 + k) * rp + cell] = (R)v;
+    }
+  }
 }
 
 cudaError_t launch_prep(const PrepArgs& a, int q, bool dbl, cudaStream_t s) {
@@ -345,13 +536,134 @@ cudaError_t launch_source(const SourceArgs& a, int q, bool dbl, int* nblocks, cu
 }
 
 // ----------------------------------------------------------------------------
+// momentum-exchange drag J_MEA (Sec. 4.1, Eq. obj_mea), n = e_x:
+//   J = (1/A) sum_{x in Gamma_s} sum_i xi_ix (f_i(x + xi_i) - f_ibar(x)),
+// Gamma_s the fluid-side surface nodes (d >= 1/2 with a lattice neighbour of
+// d < 1/2), A their number; terms whose neighbour leaves the domain in x are
+// left out.  J is linear in f, so its time average is J(f_bar) and its
+// derivative is the constant
+//   dJ/df_j(y) = (xi_jx / A) [1(y - xi_j in Gamma_s) + 1(y in Gamma_s, y - xi_j in domain)].
+// ----------------------------------------------------------------------------
+template <int Q, class R>
+__device__ __forceinline__ bool is_surface(const R* d, const Grid& g, const Rows& rows, int x,
+                                           long long cell) {
+  if (!(d[cell] >= R(0.5))) return false;
+  using L = Lat<Q>;
+  bool hit = false;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int xn = x + L::cx(i);
+    if (xn < 0 || xn >= g.nx) continue;
+    hit |= d[rows.r[L::cy(i) + 1][L::cz(i) + 1] + xn] < R(0.5);
+  }
+  return hit;
+}
+
+template <int Q, class R>
+__global__ void __launch_bounds__(NT) k_mea_eval(const double* fsum, double inv_n, const void* dv,
+                                                 Grid g, double* part_j, double* part_n) {
+  using L = Lat<Q>;
+  const R* d = static_cast<const R*>(dv);
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  double jv = 0.0, nv = 0.0;
+  if (x < g.nx) {
+    const long long cell = cell_of(g, x, y, z);
+    const Rows rows = make_rows<L::D>(g, y, z);
+    if (is_surface<Q, R>(d, g, rows, x, cell)) {
+      nv = 1.0;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (L::cx(i) == 0) continue;
+        const int xn = x + L::cx(i);
+        if (xn < 0 || xn >= g.nx) continue;
+        const long long nb = rows.r[L::cy(i) + 1][L::cz(i) + 1] + xn;
+        // deviations suffice: w_i = w_ibar cancels
+        const double t = fsum[(long long)i * g.N + nb] - fsum[(long long)L::opp(i) * g.N + cell];
+        jv += (L::cx(i) > 0 ? t : -t) * inv_n;
+      }
+    }
+  }
+  __shared__ double sh[NT / 32];
+  const double sj = block_sum<NT>(jv, sh);
+  const double sn = block_sum<NT>(nv, sh);
+  if (threadIdx.x == 0) {
+    part_j[block_linear()] = sj;
+    part_n[block_linear()] = sn;
+  }
+}
+
+template <int Q, class R>
+__global__ void __launch_bounds__(NT) k_mea_source(const void* dv, Grid g, double inv_area, void* srcv,
+                                                   double* red) {
+  using L = Lat<Q>;
+  const R* d = static_cast<const R*>(dv);
+  R* src = static_cast<R*>(srcv);
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  double acc = 0.0;
+  if (x < g.nx) {
+    const long long cell = cell_of(g, x, y, z);
+    const Rows rows = make_rows<L::D>(g, y, z);
+    const bool here = is_surface<Q, R>(d, g, rows, x, cell);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      double gv = 0.0;
+      if (L::cx(j) != 0) {
+        const int xb = x - L::cx(j);
+        if (xb >= 0 && xb < g.nx) {
+          // rows of y - xi_j: the neighbour in direction opp(j)
+          const int o = L::opp(j);
+          const long long nb = rows.r[L::cy(o) + 1][L::cz(o) + 1] + xb;
+          const int yb = y - L::cy(j), zb = z - L::cz(j);
+          const int yw = yb < 0 ? yb + g.ny : (yb >= g.ny ? yb - g.ny : yb);
+          const int zw = zb < 0 ? zb + g.nz : (zb >= g.nz ? zb - g.nz : zb);
+          const Rows rb = make_rows<L::D>(g, yw, zw);
+          const double cnt = (is_surface<Q, R>(d, g, rb, xb, nb) ? 1.0 : 0.0) + (here ? 1.0 : 0.0);
+          gv = (L::cx(j) > 0 ? cnt : -cnt) * inv_area;
+        }
+      }
+      src[(long long)j * g.N + cell] = (R)gv;
+      acc += gv * gv;
+    }
+  }
+  __shared__ double sh[NT / 32];
+  const double sm = block_sum<NT>(acc, sh);
+  if (threadIdx.x == 0) red[block_linear()] = sm;
+}
+
+cudaError_t launch_mea_eval(const double* fsum, double inv_n, const void* d, const Grid& g, int q,
+                            bool dbl, double* part_j, double* part_n, int* nblocks, cudaStream_t s) {
+  dim3 grid((g.nx + NT - 1) / NT, g.ny, g.nz);
+  *nblocks = (int)(grid.x * grid.y * grid.z);
+#define HLBM_ME(QQ, RR) k_mea_eval<QQ, RR><<<grid, NT, 0, s>>>(fsum, inv_n, d, g, part_j, part_n)
+  if (q == 9) { if (dbl) HLBM_ME(9, double); else HLBM_ME(9, float); }
+  else if (q == 19) { if (dbl) HLBM_ME(19, double); else HLBM_ME(19, float); }
+  else return cudaErrorInvalidValue;
+#undef HLBM_ME
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mea_source(const void* d, const Grid& g, int q, bool dbl, double inv_area,
+                              void* src, double* red, int* nblocks, cudaStream_t s) {
+  dim3 grid((g.nx + NT - 1) / NT, g.ny, g.nz);
+  *nblocks = (int)(grid.x * grid.y * grid.z);
+#define HLBM_MS(QQ, RR) k_mea_source<QQ, RR><<<grid, NT, 0, s>>>(d, g, inv_area, src, red)
+  if (q == 9) { if (dbl) HLBM_MS(9, double); else HLBM_MS(9, float); }
+  else if (q == 19) { if (dbl) HLBM_MS(19, double); else HLBM_MS(19, float); }
+  else return cudaErrorInvalidValue;
+#undef HLBM_MS
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
 // gradient: G = dJ/dd_bar + sum_i mu_i dC_i/dd over the design box
 //   dC_i/dd = omega w_i rho (3 xi_i.v + 9 (xi_i.u~)(xi_i.v) - 3 u~.v),  v = u - u_s
 //   so sum_i mu_i dC_i/dd = omega rho (s - 3 u~ s0) . v;
 //   exact LES adds (sum_i mu_i (f^eq_i - f_i)) d omega/dd with
 //   Pi : dPi/dd = -2 rho v . Pi . u~.
 // ----------------------------------------------------------------------------
-template <int Q, class R, bool EXACT>
+template <int Q, class R, bool EXACT, bool RR>
 __global__ void __launch_bounds__(NT) k_gradient(GradArgs ga) {
   constexpr int S = RealStore<R>::S;
   const int bx = ga.box[1] - ga.box[0], by = ga.box[3] - ga.box[2];
@@ -371,24 +683,38 @@ __global__ void __launch_bounds__(NT) k_gradient(GradArgs ga) {
   a.tau_b_f = ga.tau_b_f;
   a.kles_f = ga.kles_f;
   for (int k = 0; k < 3; ++k) { a.us[k] = ga.us[k]; a.us_f[k] = ga.us_f[k]; }
-  LinCell<Q, R, EXACT> c;
-  load_lin<Q, R, EXACT>(a, cell, static_cast<const R*>(ga.d)[cell], c);
-  R s0, m0;
-  Vec3<R> s;
-  contract<Q, R>(mu, c.ut, s0, s, m0);
-  const Vec3<R> v{c.u.x - par<R>(ga.us[0], ga.us_f[0]), c.u.y - par<R>(ga.us[1], ga.us_f[1]),
-                  c.u.z - par<R>(ga.us[2], ga.us_f[2])};
-  const Vec3<R> gv{s.x - R(3) * c.ut.x * s0, s.y - R(3) * c.ut.y * s0, s.z - R(3) * c.ut.z * s0};
-  R val = c.om * c.rho * dot3(gv, v);
-  if constexpr (EXACT) {
-    if (c.nP > pi_eps<R>()) {
-      R sn = 0;
+  R val;
+  if constexpr (RR) {
+    RRCell<R, EXACT> c;
+    load_lin<Q, R, EXACT>(a, cell, static_cast<const R*>(ga.d)[cell], c);
+    R mt[Q];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) sn += mu[i] * c.fneq[i];
-      const R pdd = -R(2) * c.rho * dot3(v, sym_mul(c.P, c.ut));
-      // (sum mu (feq - f)) * (-om^2) * k pdd / ((2 tau - tau_b) |Pi|)
-      val += sn * c.om * c.om * par<R>(ga.kles, ga.kles_f) * pdd /
-             ((R(2) * c.tau - par<R>(ga.tau_b, ga.tau_b_f)) * c.nP);
+    for (int i = 0; i < Q; ++i) mt[i] = mu[i];
+    Vec3<R> gut;
+    rr_transpose<Q, R, EXACT>(c, mt, a, &gut);
+    const Vec3<R> v{c.u.x - par<R>(ga.us[0], ga.us_f[0]), c.u.y - par<R>(ga.us[1], ga.us_f[1]),
+                    c.u.z - par<R>(ga.us[2], ga.us_f[2])};
+    val = dot3(gut, v);
+  } else {
+    LinCell<Q, R, EXACT> c;
+    load_lin<Q, R, EXACT>(a, cell, static_cast<const R*>(ga.d)[cell], c);
+    R s0, m0;
+    Vec3<R> s;
+    contract<Q, R>(mu, c.ut, s0, s, m0);
+    const Vec3<R> v{c.u.x - par<R>(ga.us[0], ga.us_f[0]), c.u.y - par<R>(ga.us[1], ga.us_f[1]),
+                    c.u.z - par<R>(ga.us[2], ga.us_f[2])};
+    const Vec3<R> gv{s.x - R(3) * c.ut.x * s0, s.y - R(3) * c.ut.y * s0, s.z - R(3) * c.ut.z * s0};
+    val = c.om * c.rho * dot3(gv, v);
+    if constexpr (EXACT) {
+      if (c.nP > pi_eps<R>()) {
+        R sn = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) sn += mu[i] * c.fneq[i];
+        const R pdd = -R(2) * c.rho * dot3(v, sym_mul(c.P, c.ut));
+        // (sum mu (feq - f)) * (-om^2) * k pdd / ((2 tau - tau_b) |Pi|)
+        val += sn * c.om * c.om * par<R>(ga.kles, ga.kles_f) * pdd /
+               ((R(2) * c.tau - par<R>(ga.tau_b, ga.tau_b_f)) * c.nP);
+      }
     }
   }
   double G = (double)val;
@@ -401,11 +727,16 @@ __global__ void __launch_bounds__(NT) k_gradient(GradArgs ga) {
   }
 }
 
-cudaError_t launch_gradient(const GradArgs& a, int q, bool dbl, bool exact, cudaStream_t s) {
+cudaError_t launch_gradient(const GradArgs& a, int q, bool dbl, bool exact, bool rr, cudaStream_t s) {
   const int bx = a.box[1] - a.box[0], by = a.box[3] - a.box[2], bz = a.box[5] - a.box[4];
   dim3 grid((bx + NT - 1) / NT, by, bz);
-#define HLBM_G(QQ, RR) \
-  do { if (exact) k_gradient<QQ, RR, true><<<grid, NT, 0, s>>>(a); else k_gradient<QQ, RR, false><<<grid, NT, 0, s>>>(a); } while (0)
+#define HLBM_G(QQ, RT)                                                              \
+  do {                                                                              \
+    if (rr) { if (exact) k_gradient<QQ, RT, true, true><<<grid, NT, 0, s>>>(a);        \
+              else k_gradient<QQ, RT, false, true><<<grid, NT, 0, s>>>(a); }           \
+    else { if (exact) k_gradient<QQ, RT, true, false><<<grid, NT, 0, s>>>(a);          \
+           else k_gradient<QQ, RT, false, false><<<grid, NT, 0, s>>>(a); }             \
+  } while (0)
   if (q == 9) { if (dbl) HLBM_G(9, double); else HLBM_G(9, float); }
   else if (q == 19) { if (dbl) HLBM_G(19, double); else HLBM_G(19, float); }
   else return cudaErrorInvalidValue;

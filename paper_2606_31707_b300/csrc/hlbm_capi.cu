@@ -36,7 +36,9 @@ struct hlbm_ctx {
   int phase = 0;  // 0: natural layout, next primal kernel is even
   long steps_done = 0;
   // averages
-  double* msum = nullptr;   // (1 + D) x N sums of rho, rho u
+  bool rr = false;          // recursive regularised collision (Sec. 2.2)
+  int mplanes = 3;          // planes of msum: 1 + D, + D(D+1)/2 with rr
+  double* msum = nullptr;   // mplanes x N sums of rho - 1, rho u[, xi xi (f - w)]
   double* fsum = nullptr;   // q x N sums of f (full_f only, or set by the caller)
   bool full_f = false;
   double pmat[2][10 * 19] = {};  // least-squares inverse of the dJ/df coefficient basis
@@ -215,7 +217,10 @@ int check_box(const hlbm_ctx* c, const int b[6]) {
 }
 
 void objective_box(const hlbm_ctx* c, int obj, int box[6]) {
-  if (obj == HLBM_OBJ_DRAG_FFA) {
+  if (obj == HLBM_OBJ_DRAG_MEA) {
+    const int b[6] = {0, c->g.nx, 0, c->g.ny, 0, c->g.nz};
+    std::memcpy(box, b, sizeof b);
+  } else if (obj == HLBM_OBJ_DRAG_FFA) {
     box[0] = c->opt.ffa_x; box[1] = c->opt.ffa_x + 1;
     box[2] = c->opt.ffa_y0; box[3] = c->opt.ffa_y1;
     box[4] = c->opt.ffa_z0; box[5] = c->opt.ffa_z1;
@@ -224,20 +229,24 @@ void objective_box(const hlbm_ctx* c, int obj, int box[6]) {
   }
 }
 
-int obj_slot(int obj) { return obj == HLBM_OBJ_DRAG_FFA ? 0 : (obj == HLBM_OBJ_DISSIPATION ? 1 : -1); }
+int obj_slot(int obj) {
+  return obj == HLBM_OBJ_DRAG_FFA ? 0
+         : obj == HLBM_OBJ_DISSIPATION ? 1
+         : obj == HLBM_OBJ_DRAG_MEA ? 2 : -1;
+}
 
 size_t coef_bytes(const hlbm_ctx* c, int o) { return (size_t)ncoef(o, c->D) * c->g.N * 8; }
 
 int ensure_averages(hlbm_ctx* c, int mask) {
   const long long N = c->g.N;
   const size_t qN = (size_t)c->q * N * 8;
-  if (!c->msum && !(c->msum = (double*)dalloc(c, (size_t)(1 + c->D) * N * 8)))
+  if (!c->msum && !(c->msum = (double*)dalloc(c, (size_t)c->mplanes * N * 8)))
     return set_err(c, HLBM_ENOMEM, "msum");
   if (c->full_f && !c->fsum && !(c->fsum = (double*)dalloc(c, qN))) return set_err(c, HLBM_ENOMEM, "fsum");
   if (!c->tsum && !(c->tsum = (double*)dalloc(c, (size_t)N * 8))) return set_err(c, HLBM_ENOMEM, "tsum");
   const bool stage = !real_is_double(c);
   if (stage) {
-    if (!c->mstage && !(c->mstage = (float*)dalloc(c, (size_t)(1 + c->D) * N * 4))) return set_err(c, HLBM_ENOMEM, "mstage");
+    if (!c->mstage && !(c->mstage = (float*)dalloc(c, (size_t)c->mplanes * N * 4))) return set_err(c, HLBM_ENOMEM, "mstage");
     if (c->full_f && !c->fstage && !(c->fstage = (float*)dalloc(c, (size_t)c->q * N * 4))) return set_err(c, HLBM_ENOMEM, "fstage");
     if (!c->tstage && !(c->tstage = (float*)dalloc(c, (size_t)N * 4))) return set_err(c, HLBM_ENOMEM, "tstage");
   }
@@ -256,10 +265,10 @@ int reset_averages(hlbm_ctx* c, int mask) {
   int rc = ensure_averages(c, mask);
   if (rc) return rc;
   const long long N = c->g.N;
-  HLBM_TRY(c, cudaMemsetAsync(c->msum, 0, (size_t)(1 + c->D) * N * 8, c->stream), "memset");
+  HLBM_TRY(c, cudaMemsetAsync(c->msum, 0, (size_t)c->mplanes * N * 8, c->stream), "memset");
   if (c->fsum) HLBM_TRY(c, cudaMemsetAsync(c->fsum, 0, (size_t)c->q * N * 8, c->stream), "memset");
   HLBM_TRY(c, cudaMemsetAsync(c->tsum, 0, (size_t)N * 8, c->stream), "memset");
-  if (c->mstage) HLBM_TRY(c, cudaMemsetAsync(c->mstage, 0, (size_t)(1 + c->D) * N * 4, c->stream), "memset");
+  if (c->mstage) HLBM_TRY(c, cudaMemsetAsync(c->mstage, 0, (size_t)c->mplanes * N * 4, c->stream), "memset");
   if (c->fstage) HLBM_TRY(c, cudaMemsetAsync(c->fstage, 0, (size_t)c->q * N * 4, c->stream), "memset");
   if (c->tstage) HLBM_TRY(c, cudaMemsetAsync(c->tstage, 0, (size_t)N * 4, c->stream), "memset");
   for (int o = 0; o < 2; ++o) {
@@ -365,6 +374,8 @@ void hlbm_default_options(hlbm_options* o, const int dims[3]) {
   std::memcpy(o->design_box, box, sizeof box);
   o->accum_stride = 1;
   o->check_every = 100;
+  o->gmres_restart = 30;
+  o->gmres_inner = 100;
 }
 
 int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau, double Cs,
@@ -414,7 +425,13 @@ int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau, doub
     c->g.bx = bx;
   }
   c->nblk = (long long)((dims[0] + c->g.bx - 1) / c->g.bx) * dims[1] * dims[2];
-  c->full_f = c->opt.average_full_f != 0 || Cs > 0.0;
+  if (c->opt.collision != HLBM_COLL_BGK && c->opt.collision != HLBM_COLL_RR) { delete c; return HLBM_EINVAL; }
+  c->rr = c->opt.collision == HLBM_COLL_RR;
+  c->mplanes = 1 + c->D + (c->rr ? c->D * (c->D + 1) / 2 : 0);
+  // the exact LES linearisation of BGK and J_MEA (linear in f: J_bar = J(f_bar))
+  // need f_bar; the regularised collision reads only moments up to order 2
+  c->full_f = c->opt.average_full_f != 0 || (Cs > 0.0 && !c->rr) ||
+              (c->opt.objectives & HLBM_OBJ_DRAG_MEA);
   // least-squares inverse P = (V^T V)^-1 V^T of the coefficient basis V (q x nc)
   for (int o = 0; o < 2; ++o) {
     const int nc = ncoef(o, c->D), q = c->q;
@@ -495,6 +512,8 @@ int hlbm_configure(hlbm_ctx* c, double tau, double Cs, const hlbm_options* opt) 
   if (!(tau > 0.5) || !(Cs >= 0.0) || !std::isfinite(tau) || !std::isfinite(Cs))
     return set_err(c, HLBM_EINVAL, "need tau > 0.5 and Cs >= 0");
   if (opt) {
+    if (opt->collision != c->opt.collision)
+      return set_err(c, HLBM_EINVAL, "the collision model is fixed when the context is created");
     int ffa[6] = {opt->ffa_x, opt->ffa_x + 1, opt->ffa_y0, opt->ffa_y1, opt->ffa_z0, opt->ffa_z1};
     if (!check_box(c, ffa) || !check_box(c, opt->diss_box) || !check_box(c, opt->design_box))
       return set_err(c, HLBM_EINVAL, "region outside the grid");
@@ -518,7 +537,8 @@ int hlbm_configure(hlbm_ctx* c, double tau, double Cs, const hlbm_options* opt) 
   c->Cs = Cs;
   c->kles = 4.5 * std::sqrt(2.0) * Cs * Cs;
   c->nu0 = (tau - 0.5) / 3.0;
-  c->full_f = c->full_f || c->opt.average_full_f != 0 || Cs > 0.0;
+  c->full_f = c->full_f || c->opt.average_full_f != 0 || (Cs > 0.0 && !c->rr) ||
+              (c->opt.objectives & HLBM_OBJ_DRAG_MEA);
   c->nsamples = 0;
   c->acc_mask = 0;
   c->generation++;
@@ -616,7 +636,7 @@ static int primal_steps(hlbm_ctx* c, const PrimalArgs& a, bool les, int acc_base
       int ph = c->phase;
       for (long k = 0; ok && k < kGraphSteps; ++k) {
         const int v = step_variant(acc_base, k, kGraphSteps + 1);  // interior block: flush on % kStage
-        ok = launch_primal(a, c->q, c->storage, ph == 1, les, v, c->stream) == cudaSuccess;
+        ok = launch_primal(a, c->q, c->storage, ph == 1, les, v, c->rr, c->stream) == cudaSuccess;
         ph ^= 1;
       }
       if (cudaStreamEndCapture(c->stream, &graph) != cudaSuccess) ok = false;
@@ -645,7 +665,7 @@ static int primal_steps(hlbm_ctx* c, const PrimalArgs& a, bool les, int acc_base
   }
   for (; done < count; ++done) {
     const int v = step_variant(acc_base, done, count);
-    cudaError_t e = CNT(c, launch_primal)(a, c->q, c->storage, c->phase == 1, les, v, c->stream);
+    cudaError_t e = CNT(c, launch_primal)(a, c->q, c->storage, c->phase == 1, les, v, c->rr, c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "primal launch");
     c->phase ^= 1;
   }
@@ -656,7 +676,7 @@ int hlbm_run_primal(hlbm_ctx* c, long steps, long W) {
   if (!c) return HLBM_EINVAL;
   if (steps < 0 || W < 0 || W > steps) return set_err(c, HLBM_EINVAL, "need 0 <= avg_window <= steps");
   int rc;
-  const int mask = c->opt.objectives & 3;
+  const int mask = c->opt.objectives & 7;
   if (W > 0) {
     rc = reset_averages(c, mask);
     if (rc) return rc;
@@ -682,7 +702,7 @@ int hlbm_run_primal(hlbm_ctx* c, long steps, long W) {
     for (long n = first; n < steps; ++n) {
       const bool acc = ((n - first) % stride) == 0;
       const int v = acc ? step_variant(acc_base, samples, nsamp) : 0;
-      cudaError_t e = CNT(c, launch_primal)(a, c->q, c->storage, c->phase == 1, les, v, c->stream);
+      cudaError_t e = CNT(c, launch_primal)(a, c->q, c->storage, c->phase == 1, les, v, c->rr, c->stream);
       if (e != cudaSuccess) return cuda_check(c, e, "primal launch");
       c->phase ^= 1;
       ++launches;
@@ -712,7 +732,8 @@ int hlbm_run_tangent(hlbm_ctx* c, long steps, const void* delta, int dtype, int 
                      int objective, double* jdot_out) {
   if (!c || !delta || !jdot_out || steps < 1) return HLBM_EINVAL;
   const int o = obj_slot(objective);
-  if (o < 0) return set_err(c, HLBM_EINVAL, "unknown objective");
+  if (o < 0 || o > 1) return set_err(c, HLBM_EINVAL, "tangent: drag (far field) or dissipation");
+  if (c->rr) return set_err(c, HLBM_EINVAL, "tangent: BGK collision only");
   const long long N = c->g.N;
   const size_t rb = real_bytes(c);
   const size_t fd_bytes = (size_t)c->q * c->g.pitch * rb;
@@ -777,6 +798,25 @@ int hlbm_objective(hlbm_ctx* c, int obj, double* J) {
   const int o = obj_slot(obj);
   if (o < 0) return set_err(c, HLBM_EINVAL, "unknown objective");
   if (c->nsamples < 1 || !(c->acc_mask & obj)) return set_err(c, HLBM_ESTATE, "objective not averaged");
+  if (obj == HLBM_OBJ_DRAG_MEA) {
+    if (!c->fsum) return set_err(c, HLBM_ESTATE, "J_MEA needs the averaged f");
+    const long long nbm = (long long)((c->g.nx + NT - 1) / NT) * c->g.ny * c->g.nz;
+    if (c->red_n < 2 * nbm) {
+      dfree(c, c->red);
+      c->red = (double*)dalloc(c, (size_t)(2 * nbm) * 8);
+      c->red_n = c->red ? 2 * nbm : 0;
+      if (!c->red) return set_err(c, HLBM_ENOMEM, "reduction buffer");
+    }
+    int nb = 0;
+    HLBM_TRY(c, CNT(c, launch_mea_eval)(c->fsum, 1.0 / (double)c->nsamples, c->d, c->g, c->q,
+                                        real_is_double(c), c->red, c->red + nbm, &nb, c->stream), "mea");
+    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, nb, c->scal_dev, c->stream), "reduce");
+    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red + nbm, nb, c->scal_dev + 1, c->stream), "reduce");
+    HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 16, cudaMemcpyDeviceToHost, c->stream), "copy");
+    HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+    *J = c->scal_host[0] / (c->scal_host[1] > 0 ? c->scal_host[1] : 1.0);
+    return HLBM_OK;
+  }
   HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->jblk[o], c->nblk, c->scal_dev, c->stream), "reduce");
   HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
   HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
@@ -788,10 +828,13 @@ static int prepare_linearisation(hlbm_ctx* c, int mode) {
   const bool exact_les = (mode == HLBM_ADJ_EXACT) && c->Cs > 0.0;
   const double tau_b = c->opt.tau_adj > 0.0 ? c->opt.tau_adj : c->tau0;
   const int want = exact_les ? 1 : 0;
-  const int rec_mode_key = exact_les ? 1 : (mode == HLBM_ADJ_FTA && c->Cs > 0.0 ? 2 : 0);
+  // record kinds: 0 BGK, 1 BGK exact LES (f_bar), 2 BGK frozen turbulence,
+  // 3 RR (rho, u, omega, Pi), 4 RR exact LES (omega from Pi in the kernels)
+  int rec_mode_key = exact_les ? 1 : (mode == HLBM_ADJ_FTA && c->Cs > 0.0 ? 2 : 0);
+  if (c->rr) rec_mode_key = exact_les ? 4 : 3;
   if (c->rec && c->rec_mode == rec_mode_key && c->rec_taub == tau_b && c->rec_generation == c->generation)
     return HLBM_OK;
-  const int planes = want ? c->q : c->D + 2;
+  const int planes = c->rr ? c->D + 2 + c->D * (c->D + 1) / 2 : (want ? c->q : c->D + 2);
   const size_t bytes = (size_t)planes * c->g.N * real_bytes(c);
   if (c->rec_bytes < bytes) {
     dfree(c, c->rec);
@@ -799,7 +842,7 @@ static int prepare_linearisation(hlbm_ctx* c, int mode) {
     c->rec_bytes = c->rec ? bytes : 0;
     if (!c->rec) return set_err(c, HLBM_ENOMEM, "record");
   }
-  if (want && !c->fsum) return set_err(c, HLBM_ESTATE, "exact LES linearisation needs the averaged f");
+  if (want && !c->rr && !c->fsum) return set_err(c, HLBM_ESTATE, "exact LES linearisation needs the averaged f");
   PrepArgs p{};
   p.fsum = c->fsum;
   p.msum = c->msum;
@@ -810,6 +853,9 @@ static int prepare_linearisation(hlbm_ctx* c, int mode) {
   p.g = c->g;
   p.tau_b = tau_b;
   p.exact = want;
+  p.rr = c->rr ? 1 : 0;
+  p.d = c->d;
+  for (int k = 0; k < 3; ++k) p.us[k] = c->opt.u_solid[k];
   HLBM_TRY(c, CNT(c, launch_prep)(p, c->q, real_is_double(c), c->stream), "prep");
   c->rec_mode = rec_mode_key;
   c->rec_taub = tau_b;
@@ -890,8 +936,8 @@ static int adjoint_gmres(hlbm_ctx* c, const AdjointArgs& a, bool dbl, bool exact
   auto pair = [&](const AdjointArgs& aa) -> cudaError_t {
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < inner && e == cudaSuccess; ++k) {
-      e = CNT(c, launch_adjoint)(aa, c->q, dbl, false, exact, 0, st);
-      if (e == cudaSuccess) e = CNT(c, launch_adjoint)(aa, c->q, dbl, true, exact, 0, st);
+      e = CNT(c, launch_adjoint)(aa, c->q, dbl, false, exact, 0, c->rr, st);
+      if (e == cudaSuccess) e = CNT(c, launch_adjoint)(aa, c->q, dbl, true, exact, 0, c->rr, st);
       sweeps += 2;
     }
     return e;
@@ -1005,7 +1051,8 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
   objective_box(c, obj, sb);
   const long long vol = (long long)(sb[1] - sb[0]) * (sb[3] - sb[2]) * (sb[5] - sb[4]);
   const long long nb_src = (long long)((sb[1] - sb[0] + NT - 1) / NT) * (sb[3] - sb[2]) * (sb[5] - sb[4]);
-  const long long need_red = nb_adj > nb_src ? nb_adj : nb_src;
+  long long need_red = nb_adj > nb_src ? nb_adj : nb_src;
+  if (need_red < 2 * nb_src) need_red = 2 * nb_src;  // J_MEA: values and counts
   if (c->red_n < need_red) {
     dfree(c, c->red);
     c->red = (double*)dalloc(c, (size_t)need_red * 8);
@@ -1021,19 +1068,32 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
   }
   int rc = prepare_linearisation(c, mode);
   if (rc) return rc;
-  const bool exact = c->rec_mode == 1;
+  const bool exact = c->rec_mode == 1 || c->rec_mode == 4;
 
   HLBM_TRY(c, cudaEventRecord(c->ev0, c->stream), "event");
-  SourceArgs sa{};
-  sa.gsum = c->gsum[o];
-  sa.obj_slot = o;
-  sa.inv_n = 1.0 / (double)c->nsamples;
-  sa.src = c->src;
-  std::memcpy(sa.box, sb, sizeof sa.box);
-  sa.g = c->g;
-  sa.red = c->red;
   int nbs = 0;
-  HLBM_TRY(c, CNT(c, launch_source)(sa, c->q, dbl, &nbs, c->stream), "source");
+  if (obj == HLBM_OBJ_DRAG_MEA) {
+    // constant dJ_MEA/df over the grid; first the number of surface nodes
+    if (!c->fsum) return set_err(c, HLBM_ESTATE, "J_MEA needs the averaged f");
+    HLBM_TRY(c, CNT(c, launch_mea_eval)(c->fsum, 1.0 / (double)c->nsamples, c->d, c->g, c->q, dbl,
+                                        c->red, c->red + nb_src, &nbs, c->stream), "mea");
+    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red + nb_src, nbs, c->scal_dev, c->stream), "reduce");
+    HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
+    HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+    const double area = c->scal_host[0] > 0 ? c->scal_host[0] : 1.0;
+    HLBM_TRY(c, CNT(c, launch_mea_source)(c->d, c->g, c->q, dbl, 1.0 / area, c->src, c->red, &nbs,
+                                          c->stream), "source");
+  } else {
+    SourceArgs sa{};
+    sa.gsum = c->gsum[o];
+    sa.obj_slot = o;
+    sa.inv_n = 1.0 / (double)c->nsamples;
+    sa.src = c->src;
+    std::memcpy(sa.box, sb, sizeof sa.box);
+    sa.g = c->g;
+    sa.red = c->red;
+    HLBM_TRY(c, CNT(c, launch_source)(sa, c->q, dbl, &nbs, c->stream), "source");
+  }
   HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, nbs, c->scal_dev, c->stream), "reduce");
   HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
   HLBM_TRY(c, cudaMemsetAsync(c->lam, 0, lam_bytes, c->stream), "memset");
@@ -1059,7 +1119,7 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
     for (long j = 0; j < chunk; ++j) {
       const bool odd = (j & 1) != 0;
       const int res = j == chunk - 2 ? 1 : (j == chunk - 1 ? 2 : 0);
-      cudaError_t e = launch_adjoint(a, c->q, dbl, odd, exact, res, c->stream);
+      cudaError_t e = launch_adjoint(a, c->q, dbl, odd, exact, res, c->rr, c->stream);
       if (e != cudaSuccess) return e;
     }
     cudaError_t e = launch_finalize_sum(c->red, nb_adj, c->scal_dev, c->stream);
@@ -1147,12 +1207,13 @@ static int run_gradient(hlbm_ctx* c, const int box[6], double* out, double* mu_o
   for (int k = 0; k < 3; ++k) { ga.us[k] = c->opt.u_solid[k]; ga.us_f[k] = (float)ga.us[k]; }
   ga.tau_b_f = (float)ga.tau_b;
   ga.kles_f = (float)ga.kles;
-  ga.ddsum = c->ddsum[o];
+  ga.ddsum = o < 2 ? c->ddsum[o] : nullptr;  // dJ_MEA/dd = 0
   ga.inv_n = 1.0 / (double)c->nsamples;
   std::memcpy(ga.box, box, sizeof ga.box);
   ga.out = out;
   ga.mu_out = mu_out;
-  HLBM_TRY(c, CNT(c, launch_gradient)(ga, c->q, real_is_double(c), c->rec_mode == 1, c->stream), "gradient");
+  HLBM_TRY(c, CNT(c, launch_gradient)(ga, c->q, real_is_double(c), c->rec_mode == 1 || c->rec_mode == 4,
+                                      c->rr, c->stream), "gradient");
   return HLBM_OK;
 }
 
@@ -1282,7 +1343,7 @@ int hlbm_set_field(hlbm_ctx* c, int which, const void* data, int dtype, int on_d
   // a set field defines a window of one sample: rescale existing sums
   if (c->nsamples > 1) {
     const double s = 1.0 / (double)c->nsamples;
-    CNT(c, launch_scale)(c->msum, (long long)(1 + c->D) * N, s, c->stream);
+    CNT(c, launch_scale)(c->msum, (long long)c->mplanes * N, s, c->stream);
     if (c->fsum) CNT(c, launch_scale)(c->fsum, qN, s, c->stream);
     CNT(c, launch_scale)(c->tsum, N, s, c->stream);
     for (int o = 0; o < 2; ++o) {
@@ -1308,7 +1369,7 @@ int hlbm_set_field(hlbm_ctx* c, int which, const void* data, int dtype, int on_d
   if (rc) return rc;
   switch (which) {
     case HLBM_FIELD_FBAR:
-      HLBM_TRY(c, CNT(c, launch_set_fbar)(c->stage, c->q, N, c->fsum, c->msum, c->stream), "fbar");
+      HLBM_TRY(c, CNT(c, launch_set_fbar)(c->stage, c->q, N, c->fsum, c->msum, c->rr, c->stream), "fbar");
       break;
     case HLBM_FIELD_GBAR_FFA:
     case HLBM_FIELD_GBAR_DISS: {
@@ -1337,7 +1398,7 @@ int hlbm_get_stats(const hlbm_ctx* c, hlbm_stats* out) {
 // checkpoint file: header, then the raw population array and the FP64 sums
 struct CkptHeader {
   char magic[8];
-  int q, storage, nx, ny, nz, phase, acc_mask, has_fsum;
+  int q, storage, nx, ny, nz, phase, acc_mask, has_fsum, mplanes, pad;
   long long steps_done, nsamples;
 };
 
@@ -1346,8 +1407,9 @@ int hlbm_save(hlbm_ctx* c, const char* path) {
   FILE* fp = std::fopen(path, "wb");
   if (!fp) return set_err(c, HLBM_EINVAL, "cannot open %s", path);
   CkptHeader h{};
-  std::memcpy(h.magic, "HLBMCK2", 8);
+  std::memcpy(h.magic, "HLBMCK3", 8);
   h.has_fsum = c->fsum != nullptr;
+  h.mplanes = c->mplanes;
   h.q = c->q; h.storage = c->storage; h.nx = c->g.nx; h.ny = c->g.ny; h.nz = c->g.nz;
   h.phase = c->phase; h.acc_mask = c->nsamples > 0 ? c->acc_mask : 0;
   h.steps_done = c->steps_done; h.nsamples = c->nsamples;
@@ -1367,7 +1429,7 @@ int hlbm_save(hlbm_ctx* c, const char* path) {
   int rc = dump(c->f, (size_t)c->q * c->g.pitch * pop_elem_bytes(c->storage));
   if (!rc) rc = dump(c->d, (size_t)c->g.N * real_bytes(c));
   if (!rc && h.nsamples > 0) {
-    rc = dump(c->msum, (size_t)(1 + c->D) * c->g.N * 8);
+    rc = dump(c->msum, (size_t)c->mplanes * c->g.N * 8);
     if (!rc && h.has_fsum) rc = dump(c->fsum, (size_t)c->q * c->g.N * 8);
     if (!rc) rc = dump(c->tsum, (size_t)c->g.N * 8);
     for (int o = 0; o < 2 && !rc; ++o) {
@@ -1387,8 +1449,9 @@ int hlbm_load(hlbm_ctx* c, const char* path) {
   FILE* fp = std::fopen(path, "rb");
   if (!fp) return set_err(c, HLBM_EINVAL, "cannot open %s", path);
   CkptHeader h{};
-  if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "HLBMCK2", 8) != 0 ||
-      h.q != c->q || h.storage != c->storage || h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz) {
+  if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "HLBMCK3", 8) != 0 ||
+      h.q != c->q || h.storage != c->storage || h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz ||
+      h.mplanes != c->mplanes) {
     std::fclose(fp);
     return set_err(c, HLBM_EINVAL, "checkpoint does not match this context");
   }
@@ -1408,7 +1471,7 @@ int hlbm_load(hlbm_ctx* c, const char* path) {
   if (!rc) rc = load(c->d, (size_t)c->g.N * real_bytes(c));
   if (!rc && h.nsamples > 0) {
     rc = ensure_averages(c, h.acc_mask);
-    if (!rc) rc = load(c->msum, (size_t)(1 + c->D) * c->g.N * 8);
+    if (!rc) rc = load(c->msum, (size_t)c->mplanes * c->g.N * 8);
     if (!rc && h.has_fsum) {
       if (!c->fsum && !(c->fsum = (double*)dalloc(c, (size_t)c->q * c->g.N * 8))) rc = HLBM_ENOMEM;
       if (!rc) rc = load(c->fsum, (size_t)c->q * c->g.N * 8);

@@ -24,7 +24,8 @@ struct PrimalArgs {
   double nu0;         // molecular viscosity (tau0 - 1/2)/3
   float tau0_f, kles_f, u_in_f, us_f[3], nu0_f;  // the same in float for FP32 kernels
   // averaging (only read when the ACC variant runs)
-  double* msum;       // (1 + D) x N running sums of rho - 1 and rho u (moments of f)
+  double* msum;       // (1 + D) x N running sums of rho - 1 and rho u (moments of f);
+                      // RR adds D(D+1)/2 planes of sum xi xi (f - w): xx, yy[, zz], xy[, xz, yz]
   double* fsum;       // q x N running sum of f - w (only with the full-f variant)
   double* tsum;       // N running sum of tau_eff - tau0 (LES only)
   double* gsum[2];    // ncoef(obj) x N running sums of the coefficients of dJ/df
@@ -73,7 +74,7 @@ constexpr int kStage = 16;  // samples staged in FP32 before folding into FP64
 // acc: 0 no averaging, else ACC_ON | optional ACC_FULL (also average f) |
 // optional ACC_FLUSH (fold the FP32 staging into the FP64 sums)
 cudaError_t launch_primal(const PrimalArgs& a, int q, int storage, bool odd, bool les, int acc,
-                          cudaStream_t s);
+                          bool rr, cudaStream_t s);
 // out[k] (k < q, per cell) = scale * sum_c coef[c] b_c(xi_k): expand coefficient sums
 cudaError_t launch_expand_coef(const double* coef, int obj_slot, int q, long long N, double scale,
                                double* out, cudaStream_t s);
@@ -82,7 +83,7 @@ cudaError_t launch_project_coef(const double* g, const double* Pmat, int obj_slo
                                 long long N, double* coef, cudaStream_t s);
 // fsum = f - w and msum = (rho - 1, rho u) of the q x N field f (a set f_bar)
 cudaError_t launch_set_fbar(const double* f, int q, long long N, double* fsum, double* msum,
-                            cudaStream_t s);
+                            bool rr, cudaStream_t s);
 // out = fsum * scale + w (readout of f_bar)
 cudaError_t launch_fbar_out(const double* fsum, int q, long long N, double scale, double* out,
                             cudaStream_t s);
@@ -113,14 +114,18 @@ cudaError_t launch_fill_real(void* v, bool dbl, long long n, double value, cudaS
 // --------------------------------------------------------------------------
 struct PrepArgs {
   const double* fsum;  // q x N sums of f - w (EXACT with LES)
-  const double* msum;  // (1 + D) x N sums of rho - 1, rho u (BGK / FTA)
+  const double* msum;  // moment sums (see PrimalArgs::msum)
   const double* tsum;  // N (FTA with LES) or null
   double inv_n;        // 1 / number of samples
-  void* rec;           // real planes: BGK/FTA (rho, ux, uy[, uz], omega); EXACT: q planes of f_bar - w
+  void* rec;           // real planes: BGK/FTA (rho, ux, uy[, uz], omega); EXACT: q planes of
+                       // f_bar - w; RR: (rho, ux, uy[, uz], omega, Pi xx, yy[, zz], xy[, xz, yz])
   long long rec_pitch;
   Grid g;
   double tau_b;        // tau0 or tau_adj
   int exact;           // 1: EXACT with LES (store f_bar), 0: compact record
+  int rr;              // 1: recursive regularised collision (record with Pi)
+  const void* d;       // porosity (real), RR only
+  double us[3];        // solid velocity, RR only
 };
 cudaError_t launch_prep(const PrepArgs& a, int q, bool dbl, cudaStream_t s);
 
@@ -152,8 +157,15 @@ struct AdjointArgs {
 };
 // res: 0 plain, 1 write the snapshot (even kernels), 2 compare (odd kernels)
 cudaError_t launch_adjoint(const AdjointArgs& a, int q, bool dbl, bool odd, bool exact, int res,
-                           cudaStream_t s);
+                           bool rr, cudaStream_t s);
 int adjoint_blocks(const Grid& g);
+
+// momentum-exchange drag: J(f_bar) per-block partials and surface-node counts
+cudaError_t launch_mea_eval(const double* fsum, double inv_n, const void* d, const Grid& g, int q,
+                            bool dbl, double* part_j, double* part_n, int* nblocks, cudaStream_t s);
+// its constant dJ/df over the whole grid (src: q planes of N), ||.||^2 partials in red
+cudaError_t launch_mea_source(const void* d, const Grid& g, int q, bool dbl, double inv_area,
+                              void* src, double* red, int* nblocks, cudaStream_t s);
 
 struct GradArgs {
   const void* lam;     // adjoint AA array in natural layout (next kernel even)
@@ -170,6 +182,6 @@ struct GradArgs {
   double* out;         // box volume, x fastest
   double* mu_out;      // optional q x N output of mu (whole grid when box is the domain)
 };
-cudaError_t launch_gradient(const GradArgs& a, int q, bool dbl, bool exact, cudaStream_t s);
+cudaError_t launch_gradient(const GradArgs& a, int q, bool dbl, bool exact, bool rr, cudaStream_t s);
 
 }  // namespace hlbm

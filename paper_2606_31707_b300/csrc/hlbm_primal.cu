@@ -75,8 +75,21 @@ struct AccSlot {
 //   only the density and velocity of f_bar), all of f - w when ACC == 2 (the
 //   exact LES linearisation needs f_bar itself), tau_eff - tau0 (LES), and per
 //   objective the coefficients of dJ/df in the basis of coef_basis(), dJ/dd
-//   and J.
-template <int Q, int S, bool ODD, bool LES, int ACC>
+//   and J.  With the recursive regularised collision (RR) also the second
+//   moments sum xi xi (f - w): its linearisation reads rho, u and the
+//   non-equilibrium stress of f_bar, all functions of moments up to order 2.
+//
+// RR selects the third-order recursive regularised collision of the
+// turbulent model (Sec. 2.2, Eq. HRRLBM) instead of BGK:
+//   f*_i = f^eq3_i + (1 - omega) f1_i,
+//   f^eq3_i = f^eq_i + w_i rho (9/2) c (c^2 - u~.u~),    c = xi_i . u~,
+//   f1_i = w_i [3 xi_i.a1 + (9/2)(xi_i Pi xi_i - tr Pi / 3)
+//               + (9/2)(3 c xi_i Pi xi_i - c tr Pi - 2 xi_i . Pi u~)],
+// with a1 = rho (u - u~), Pi the non-equilibrium stress, the recursive
+// third-order coefficient a1^(3) = u~ (x) Pi (symmetrised) contracted with
+// the third Hermite polynomial (the xxx and xyz entries vanish on D2Q9 and
+// D3Q19).
+template <int Q, int S, bool ODD, bool LES, int ACC, bool RR>
 __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
     const PrimalArgs& a, typename Store<S>::mem* A, const Rows& rows, int x, int y, int z,
     long long cell,
@@ -105,10 +118,8 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
   R nP = 0;
   const bool diss_here = ACC > 0 && (a.obj_mask & 2) && x >= a.db[0] && x < a.db[1] &&
                          y >= a.db[2] && y < a.db[3] && z >= a.db[4] && z < a.db[5];
-  if (LES || diss_here) {
-    P = second_moment<Q>(fneq);
-    nP = sqrt_r<R>(sym_norm2(P));
-  }
+  if (LES || diss_here || RR) P = second_moment<Q>(fneq);
+  if (LES || diss_here) nP = sqrt_r<R>(sym_norm2(P));
   const R kles = par<R>(a.kles, a.kles_f);
   if (LES) tau = tau_smagorinsky<R>(tau0, kles, nP);
   const R om = R(1) / tau;
@@ -119,10 +130,11 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
                           z >= a.ffa[3] && z < a.ffa[4];
     constexpr int NCD = 1 + D + D * (D + 1) / 2;  // dissipation coefficients
     // old values of every sum this cell updates, loaded together
-    AccSlot<R, ACC> sm[1 + D], sg0[2], sg1[NCD], sdd, st;
+    constexpr int NM = 1 + D + (RR ? D * (D + 1) / 2 : 0);  // moment sums
+    AccSlot<R, ACC> sm[NM], sg0[2], sg1[NCD], sdd, st;
     AccSlot<R, ACC> sf[(ACC & ACC_FULL) != 0 ? Q : 1];
 #pragma unroll
-    for (int k = 0; k < 1 + D; ++k) sm[k].load(a.msum, a.mstage, (long long)k * N + cell);
+    for (int k = 0; k < NM; ++k) sm[k].load(a.msum, a.mstage, (long long)k * N + cell);
     if constexpr ((ACC & ACC_FULL) != 0) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) sf[i].load(a.fsum, a.fstage, (long long)i * N + cell);
@@ -142,6 +154,21 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
     sm[1].store(a.msum, a.mstage, N + cell, m.x);
     sm[2].store(a.msum, a.mstage, 2 * N + cell, m.y);
     if (D == 3) sm[D].store(a.msum, a.mstage, (long long)D * N + cell, m.z);
+    if constexpr (RR) {
+      // sum_i xi_i xi_i (f_i - w_i) = Pi + rho u~ u~ + (rho - 1)/3 I
+      const R t = drho * R(1.0 / 3.0);
+      const R m2[6] = {P.xx + rho * ut.x * ut.x + t, P.yy + rho * ut.y * ut.y + t,
+                       P.zz + rho * ut.z * ut.z + t, P.xy + rho * ut.x * ut.y,
+                       P.xz + rho * ut.x * ut.z, P.yz + rho * ut.y * ut.z};
+      if constexpr (D == 2) {
+        sm[3].store(a.msum, a.mstage, 3LL * N + cell, m2[0]);
+        sm[4].store(a.msum, a.mstage, 4LL * N + cell, m2[1]);
+        sm[5].store(a.msum, a.mstage, 5LL * N + cell, m2[3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sm[4 + k].store(a.msum, a.mstage, (long long)(4 + k) * N + cell, m2[k]);
+      }
+    }
     if constexpr ((ACC & ACC_FULL) != 0) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) sf[i].store(a.fsum, a.fstage, (long long)i * N + cell, g[i]);
@@ -198,14 +225,37 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
     }
   }
 
+  if constexpr (RR) {
+    const Vec3<R> a1{m.x - rho * ut.x, m.y - rho * ut.y, m.z - rho * ut.z};
+    const R trP = P.xx + P.yy + P.zz;
+    const Vec3<R> PU = sym_mul(P, ut);
+    const R c1 = R(1) - om;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) g[i] -= om * fneq[i];
+    for (int i = 0; i < Q; ++i) {
+      const R w = R(Lat<Q>::w(i));
+      const R cu = xi_dot<Q>(i, ut);
+      const R xPx = xi_P_xi<Q>(i, P);
+      const R e3 = w * R(4.5) * rho * cu * (cu * cu - uu);
+      const R f1 = w * (R(3) * xi_dot<Q>(i, a1) + R(4.5) * (xPx - trP * R(1.0 / 3.0)) +
+                        R(4.5) * (R(3) * cu * xPx - cu * trP - R(2) * xi_dot<Q>(i, PU)));
+      g[i] = (g[i] - fneq[i]) + e3 + c1 * f1;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] -= om * fneq[i];
+  }
   aa_store<Q, S, ODD, +1>(A, gr, rows, x, cell, g);
   return u;
 }
 
-template <int Q, int S, bool ODD, bool LES, int ACC>
-__global__ void __launch_bounds__(NT) k_primal(PrimalArgs a) {
+// Resident blocks per SM requested for the averaging variants (caps their
+// registers at 65536 / (NT * HLBM_ACC_MINB)); 1 leaves the choice to ptxas.
+#ifndef HLBM_ACC_MINB
+#define HLBM_ACC_MINB 1
+#endif
+
+template <int Q, int S, bool ODD, bool LES, int ACC, bool RR>
+__global__ void __launch_bounds__(NT, (ACC > 0 ? HLBM_ACC_MINB : 1)) k_primal(PrimalArgs a) {
   using St = Store<S>;
   using R = typename St::real;
   const Grid& gr = a.g;
@@ -223,12 +273,12 @@ __global__ void __launch_bounds__(NT) k_primal(PrimalArgs a) {
     } else {
       aa_load<Q, S, ODD, +1>(A, gr, rows, x, cell, g);
     }
-    const Vec3<R> u = cell_update<Q, S, ODD, LES, ACC>(a, A, rows, x, y, z, cell, g, dp[cell], jp);
+    const Vec3<R> u = cell_update<Q, S, ODD, LES, ACC, RR>(a, A, rows, x, y, z, cell, g, dp[cell], jp);
     if (x == gr.nx - 2) {
       // outflow node: f^eq(1, u(nx-2)), then relaxed and streamed like any cell
       R go[Q];
       equilibrium_dev<Q, R>(go, R(0), u);
-      cell_update<Q, S, ODD, LES, ACC>(a, A, rows, x + 1, y, z, cell + 1, go, dp[cell + 1], jp);
+      cell_update<Q, S, ODD, LES, ACC, RR>(a, A, rows, x + 1, y, z, cell + 1, go, dp[cell + 1], jp);
     }
   }
   if constexpr (ACC > 0) {
@@ -244,12 +294,12 @@ __global__ void __launch_bounds__(NT) k_primal(PrimalArgs a) {
   }
 }
 
-template <int Q, int S>
+template <int Q, int S, bool RR>
 static cudaError_t launch_primal_qs(const PrimalArgs& a, bool odd, bool les, int acc,
                                     cudaStream_t s) {
   const int bx = a.g.bx;
   dim3 grid((a.g.nx + bx - 1) / bx, a.g.ny, a.g.nz);
-#define HLBM_L(O, L_, A_) k_primal<Q, S, O, L_, A_><<<grid, bx, 0, s>>>(a)
+#define HLBM_L(O, L_, A_) k_primal<Q, S, O, L_, A_, RR><<<grid, bx, 0, s>>>(a)
 #define HLBM_LA(O, L_)                                   \
   do {                                                   \
     switch (acc) {                                       \
@@ -268,24 +318,31 @@ static cudaError_t launch_primal_qs(const PrimalArgs& a, bool odd, bool les, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_primal(const PrimalArgs& a, int q, int storage, bool odd, bool les, int acc,
-                          cudaStream_t s) {
+template <bool RR>
+static cudaError_t launch_primal_c(const PrimalArgs& a, int q, int storage, bool odd, bool les,
+                                   int acc, cudaStream_t s) {
   if (q == 9) {
     switch (storage) {
-      case ST_F64: return launch_primal_qs<9, ST_F64>(a, odd, les, acc, s);
-      case ST_F32: return launch_primal_qs<9, ST_F32>(a, odd, les, acc, s);
-      case ST_F16: return launch_primal_qs<9, ST_F16>(a, odd, les, acc, s);
-      case ST_BF16: return launch_primal_qs<9, ST_BF16>(a, odd, les, acc, s);
+      case ST_F64: return launch_primal_qs<9, ST_F64, RR>(a, odd, les, acc, s);
+      case ST_F32: return launch_primal_qs<9, ST_F32, RR>(a, odd, les, acc, s);
+      case ST_F16: return launch_primal_qs<9, ST_F16, RR>(a, odd, les, acc, s);
+      case ST_BF16: return launch_primal_qs<9, ST_BF16, RR>(a, odd, les, acc, s);
     }
   } else if (q == 19) {
     switch (storage) {
-      case ST_F64: return launch_primal_qs<19, ST_F64>(a, odd, les, acc, s);
-      case ST_F32: return launch_primal_qs<19, ST_F32>(a, odd, les, acc, s);
-      case ST_F16: return launch_primal_qs<19, ST_F16>(a, odd, les, acc, s);
-      case ST_BF16: return launch_primal_qs<19, ST_BF16>(a, odd, les, acc, s);
+      case ST_F64: return launch_primal_qs<19, ST_F64, RR>(a, odd, les, acc, s);
+      case ST_F32: return launch_primal_qs<19, ST_F32, RR>(a, odd, les, acc, s);
+      case ST_F16: return launch_primal_qs<19, ST_F16, RR>(a, odd, les, acc, s);
+      case ST_BF16: return launch_primal_qs<19, ST_BF16, RR>(a, odd, les, acc, s);
     }
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_primal(const PrimalArgs& a, int q, int storage, bool odd, bool les, int acc,
+                          bool rr, cudaStream_t s) {
+  return rr ? launch_primal_c<true>(a, q, storage, odd, les, acc, s)
+            : launch_primal_c<false>(a, q, storage, odd, les, acc, s);
 }
 
 // ----------------------------------------------------------------------------
@@ -528,7 +585,7 @@ __global__ void k_project_coef(const double* gin, ProjMat P, int obj_slot, long 
 }
 
 template <int Q>
-__global__ void k_set_fbar(const double* f, long long N, double* fsum, double* msum) {
+__global__ void k_set_fbar(const double* f, long long N, double* fsum, double* msum, bool rr) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
        c += (long long)gridDim.x * blockDim.x) {
     double gv[Q];
@@ -544,6 +601,17 @@ __global__ void k_set_fbar(const double* f, long long N, double* fsum, double* m
     msum[N + c] = m.x;
     msum[2 * N + c] = m.y;
     if (Lat<Q>::D == 3) msum[3 * N + c] = m.z;
+    if (rr) {
+      const Sym<double> M2 = second_moment<Q, double>(gv);
+      if (Lat<Q>::D == 2) {
+        msum[3 * N + c] = M2.xx;
+        msum[4 * N + c] = M2.yy;
+        msum[5 * N + c] = M2.xy;
+      } else {
+        const double v[6] = {M2.xx, M2.yy, M2.zz, M2.xy, M2.xz, M2.yz};
+        for (int k = 0; k < 6; ++k) msum[(4 + k) * N + c] = v[k];
+      }
+    }
   }
 }
 
@@ -582,9 +650,9 @@ cudaError_t launch_project_coef(const double* g, const double* Pmat, int obj_slo
 }
 
 cudaError_t launch_set_fbar(const double* f, int q, long long N, double* fsum, double* msum,
-                            cudaStream_t s) {
-  if (q == 9) k_set_fbar<9><<<util_blocks(N), 256, 0, s>>>(f, N, fsum, msum);
-  else if (q == 19) k_set_fbar<19><<<util_blocks(N), 256, 0, s>>>(f, N, fsum, msum);
+                            bool rr, cudaStream_t s) {
+  if (q == 9) k_set_fbar<9><<<util_blocks(N), 256, 0, s>>>(f, N, fsum, msum, rr);
+  else if (q == 19) k_set_fbar<19><<<util_blocks(N), 256, 0, s>>>(f, N, fsum, msum, rr);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -21,8 +21,9 @@ LIB_PATH = os.path.join(HERE, "libhlbm.so")
 
 D2Q9, D3Q19 = 9, 19
 FP64, FP32, FP16DEV, BF16DEV = 0, 1, 2, 3
-OBJ_DRAG_FFA, OBJ_DISSIPATION = 1, 2
+OBJ_DRAG_FFA, OBJ_DISSIPATION, OBJ_DRAG_MEA = 1, 2, 4
 ADJ_EXACT, ADJ_FTA = 0, 1
+COLL_BGK, COLL_RR = 0, 1
 DTYPE_F64, DTYPE_F32 = 0, 1
 (FIELD_RHO, FIELD_U, FIELD_F, FIELD_FBAR, FIELD_GBAR_FFA, FIELD_GBAR_DISS, FIELD_DJDD_FFA,
  FIELD_DJDD_DISS, FIELD_TAU_T, FIELD_LAMBDA, FIELD_POROSITY) = range(11)
@@ -60,6 +61,7 @@ class hlbm_options(C.Structure):
         ("dev_alloc", _ALLOC),
         ("dev_free", _FREE),
         ("alloc_user", C.c_void_p),
+        ("collision", C.c_int),
     ]
 
 

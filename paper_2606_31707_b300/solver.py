@@ -22,7 +22,8 @@ class Solver:
                  objectives: int = H.OBJ_DRAG_FFA | H.OBJ_DISSIPATION, tau_adj: float = 0.0,
                  accum_stride: int = 1, check_every: int = 100, stream=None,
                  u_solid=(0.0, 0.0, 0.0), average_full_f: bool = False,
-                 adjoint_solver: int = 0, gmres_restart: int = 30, gmres_inner: int = 1):
+                 adjoint_solver: int = 0, gmres_restart: int = 30, gmres_inner: int = 100,
+                 collision: int = H.COLL_BGK):
         self.q = lattice
         self.dims = tuple(int(v) for v in dims)
         self.dim = 2 if lattice == 9 else 3
@@ -31,6 +32,7 @@ class Solver:
         opt.adjoint_solver = adjoint_solver
         opt.gmres_restart = gmres_restart
         opt.gmres_inner = gmres_inner
+        opt.collision = collision
         if stream is not None:
             opt.stream = stream if isinstance(stream, int) else int(stream.cuda_stream)
         self.opt = opt
@@ -67,13 +69,14 @@ class Solver:
                   objectives: int = H.OBJ_DRAG_FFA | H.OBJ_DISSIPATION, tau_adj: float = 0.0,
                   accum_stride: int = 1, check_every: int = 100, u_solid=(0.0, 0.0, 0.0),
                   average_full_f: bool = False, adjoint_solver: int = 0, gmres_restart: int = 30,
-                  gmres_inner: int = 1):
+                  gmres_inner: int = 100):
         """New physical parameters for this context (same grid and storage)."""
         opt = self._options(self.opt.storage, u_in, regions, objectives, tau_adj, accum_stride,
                             check_every, u_solid, average_full_f)
         opt.adjoint_solver = adjoint_solver
         opt.gmres_restart = gmres_restart
         opt.gmres_inner = gmres_inner
+        opt.collision = self.opt.collision
         H.hlbm_configure(self.ctx, tau, Cs, opt)
         self._design(opt)
 

@@ -267,9 +267,9 @@ def test_gmres_adjoint_reaches_the_same_fixed_point_in_fewer_sweeps(q, dims, Cs,
     # restarted GMRES on the adjoint fixed point (opt.adjoint_solver = 1)
     P, d, R = _case(q, dims, Cs, tau=0.8, u_in=0.04)
     res = {}
-    for solver in (0, 1):
+    for solver, inner in ((0, 1), (1, 1), (2, 20)):
         s = Solver(P.q, P.dims, P.tau0, P.Cs, storage=H.FP64, u_in=P.u_in, regions=R,
-                   adjoint_solver=solver, gmres_restart=40)
+                   adjoint_solver=min(solver, 1), gmres_restart=40, gmres_inner=inner)
         perm = direction_perm(s.xi, P)
         s.set_porosity(d)
         s.run_primal(2999, 0)
@@ -287,4 +287,30 @@ def test_gmres_adjoint_reaches_the_same_fixed_point_in_fewer_sweeps(q, dims, Cs,
     Gref = G[b[4]:b[5], b[2]:b[3], b[0]:b[1]]
     assert rel_l2(res[1][0], Gref) <= 1e-9
     assert rel_l2(res[0][0], Gref) <= 1e-9
+    assert rel_l2(res[2][0], Gref) <= 1e-9
     assert res[1][1] < res[0][1]
+
+
+@pytest.mark.parametrize("q,dims", [(9, (300, 24, 1)), (19, (140, 10, 4))])
+def test_mea_drag_objective_and_gradient_match_oracle(q, dims):
+    # momentum-exchange drag (Sec. 4.1): J(f_bar) and the steady adjoint gradient
+    P, d, R = _case(q, dims, 0.0, tau=0.8, u_in=0.04)
+    s = Solver(P.q, P.dims, P.tau0, 0.0, storage=H.FP64, u_in=P.u_in, regions=R,
+               objectives=H.OBJ_DRAG_FFA | H.OBJ_DISSIPATION | H.OBJ_DRAG_MEA)
+    perm = direction_perm(s.xi, P)
+    s.set_porosity(d)
+    s.run_primal(2999, 0)
+    fbar = s.field(H.FIELD_F)[np.argsort(perm)]
+    s.run_primal(1, 1)
+    J = s.objective(H.OBJ_DRAG_MEA)
+    Jref = oobj.mea_value(fbar, d, P)
+    assert abs(J - Jref) <= 1e-10 * max(abs(Jref), 1e-12)
+    st, it, r = s.solve_adjoint(H.OBJ_DRAG_MEA, H.ADJ_EXACT, 1e-12, 400000)
+    assert st == H.OK
+    Gg = s.gradient()
+    s.close()
+    g, gd = oobj.mea_partials(d, P)
+    lin = oadj.Linearisation(fbar, d, P, oadj.EXACT)
+    G = oadj.gradient(lin, oadj.solve_adjoint_direct(lin, g), gd)
+    b = R.design_box
+    assert rel_l2(Gg, G[b[4]:b[5], b[2]:b[3], b[0]:b[1]]) <= 1e-9
