@@ -1,7 +1,8 @@
 """Pins of the FP64 oracle's primal against what the paper and the
 mathematics fix: lattice isotropy, equilibrium moments, collision
 invariants, the Smagorinsky tau_eff definition, exact discrete Darcy decay,
-the viscosity-relaxation relation (shear-wave decay) and fixed points."""
+the viscosity-relaxation relation (shear-wave decay), the plane-Poiseuille and
+Brinkman porous-channel closed forms, and fixed points."""
 import math
 
 import numpy as np
@@ -165,3 +166,60 @@ def test_tau_from_reynolds_matches_configs():
     assert abs(hlbm.tau_from_reynolds(0.05, 20, 20) - 0.65) < 1e-15
     assert abs(hlbm.tau_from_reynolds(0.04, 50, 100) - 0.56) < 1e-15
     assert abs(hlbm.tau_from_reynolds(0.05, 60, 40) - 0.725) < 1e-15
+
+
+def _channel_steady(dp, tau=1.0, ny=9, nx=64, u_in=0.02):
+    """Steady flow through a y-periodic channel whose row y = 0 is solid
+    (d = 0, so the walls sit at y = 0 and y = ny) filled with porosity dp,
+    driven by the uniform inflow; returns the profile u_x(y) and the
+    pressure gradient (1/rho) dp/dx in the middle of the channel."""
+    from oracle import adjoint as adj
+    P = Params(9, (nx, ny, 1), tau0=tau, u_in=u_in)
+    d = np.full(P.shape, dp)
+    d[0, 0, :] = 0.0
+    f = hlbm.initial_state(P)
+    for _ in range(200):
+        f = hlbm.step(f, d, P)
+    f, res = adj.newton_steady(f, d, P, iters=12)
+    assert res < 1e-13
+    rho, u = hlbm.moments(f, P)
+    x0 = nx // 2
+    prof = u[0, 0, :, x0].copy()
+    prof[0] = 0.0  # the solid row is the wall node, not channel flow
+    G = CS2 * (rho[0, 1:, x0 + 5] - rho[0, 1:, x0 - 5]).mean() / 10 / rho[0, 1:, x0].mean()
+    return prof, G, P
+
+
+def test_plane_poiseuille_closed_form():
+    # Sec. 2.1 in a channel: with tau = 1 a solid (d = 0) row relaxes to rest
+    # each step, a no-slip node.  Fully developed, nu u'' = (1/rho) dp/dx, so
+    # u = A y (H - y) with -2 nu A = (1/rho) dp/dx.
+    prof, G, P = _channel_steady(1.0)
+    H = P.dims[1]
+    y = np.arange(H)
+    para = y * (H - y)
+    A = (prof * para).sum() / (para ** 2).sum()
+    assert np.abs(prof - A * para).max() <= 1e-4 * np.abs(A * para).max()
+    assert abs(-2 * P.nu0 * A / G - 1.0) <= 1e-3
+
+
+@pytest.mark.parametrize("dp", [0.97, 0.9, 0.7])
+def test_brinkman_porous_channel_closed_form(dp):
+    # Eq. 1 / Eq. 3 in the same channel filled with porosity d (reading 3).
+    # With tau = 1 the collision returns f^eq(rho, d u), so for a fully
+    # developed flow u(y) e_x the moments after streaming give, to first order
+    # in u and in the pressure gradient, the discrete Brinkman balance
+    #   d nu (u(y+1) - 2 u(y) + u(y-1)) - (1 - d) u(y) = (1/rho) dp/dx = G,
+    # whose solution with u(0) = u(H) = 0 is
+    #   u = (G/beta) (cosh(k (y - H/2)) / cosh(k H/2) - 1),
+    #   beta = 1 - d,  2 (cosh k - 1) = beta / (d nu).
+    prof, G, P = _channel_steady(dp)
+    H = P.dims[1]
+    y = np.arange(H)
+    beta = (1.0 - dp) / P.tau0
+    k = math.acosh(1.0 + beta / (2.0 * dp * P.nu0))
+    shape = np.cosh(k * (y - H / 2)) / math.cosh(k * H / 2) - 1.0
+    shape[0] = 0.0
+    A = (prof * shape).sum() / (shape ** 2).sum()
+    assert np.abs(prof - A * shape).max() <= 1e-4 * np.abs(A * shape).max()
+    assert abs(A / (G / beta) - 1.0) <= 1e-3
