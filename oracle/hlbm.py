@@ -30,6 +30,7 @@ class Params:
     u_in: float = 0.05                  # inflow velocity
     u_s: Tuple[float, float, float] = (0.0, 0.0, 0.0)  # solid velocity
     collision: str = "bgk"              # "bgk" (Eq. 2) or "rr" (Eq. HRRLBM)
+    u_in_profile: Optional[np.ndarray] = None  # (nz, ny) inflow u_x per row; None: uniform u_in
 
     def __post_init__(self):
         if self.collision not in ("bgk", "rr"):
@@ -244,7 +245,14 @@ def apply_boundary(f, P: Params):
     throughout."""
     f = f.copy()
     nz, ny, nx = P.shape
-    f[..., 0] = inflow_state(P, (nz, ny))
+    if P.u_in_profile is None:
+        f[..., 0] = inflow_state(P, (nz, ny))
+    else:
+        # a prescribed velocity profile (e.g. the parabolic channel inflow of
+        # the Schaefer-Turek benchmark, Sec. 5.1)
+        u = np.zeros((3, nz, ny))
+        u[0] = P.u_in_profile
+        f[..., 0] = equilibrium(np.ones((nz, ny)), u, P)
     rho, u = moments(f[..., nx - 2], P)
     f[..., nx - 1] = equilibrium(np.ones_like(rho), u, P)
     return f

@@ -223,3 +223,36 @@ def test_brinkman_porous_channel_closed_form(dp):
     A = (prof * shape).sum() / (shape ** 2).sum()
     assert np.abs(prof - A * shape).max() <= 1e-4 * np.abs(A * shape).max()
     assert abs(A / (G / beta) - 1.0) <= 1e-3
+
+
+def test_parabolic_inflow_profile_channel():
+    # the prescribed-profile inflow node (the channel inflow of Sec. 5.1),
+    # f = f^eq(1, u_in(y) e_x), in the tau = 1 channel: the inflow column
+    # holds the profile, the developed flow carries the same flux through every
+    # column and is the Poiseuille profile with -2 nu A = (1/rho) dp/dx.
+    # (The equilibrium node fixes rho = 1 while the interior carries the
+    # pressure drop, so the flux is below that of the prescribed profile.)
+    from oracle import adjoint as adj
+    ny, nx = 9, 48
+    y = np.arange(ny)
+    prof_in = 4 * 0.03 * y * (ny - y) / ny ** 2
+    P = Params(9, (nx, ny, 1), tau0=1.0, u_in=0.02, u_in_profile=prof_in[None, :])
+    d = np.ones(P.shape)
+    d[0, 0, :] = 0.0
+    f = hlbm.initial_state(P)
+    for _ in range(200):
+        f = hlbm.step(f, d, P)
+    f, res = adj.newton_steady(f, d, P, iters=12)
+    assert res < 1e-13
+    rho, u = hlbm.moments(f, P)
+    assert np.abs(u[0, 0, :, 0] - prof_in).max() < 1e-15
+    flux = (rho[0] * u[0, 0]).sum(axis=0)
+    assert np.abs(flux[nx // 3:2 * nx // 3] - flux[nx // 2]).max() <= 1e-5 * flux[nx // 2]
+    x0 = nx // 2
+    prof = u[0, 0, :, x0].copy()
+    prof[0] = 0.0
+    para = y * (ny - y)
+    A = (prof * para).sum() / (para ** 2).sum()
+    assert np.abs(prof - A * para).max() <= 1e-4 * np.abs(A * para).max()
+    G = CS2 * (rho[0, 1:, x0 + 5] - rho[0, 1:, x0 - 5]).mean() / 10 / rho[0, 1:, x0].mean()
+    assert abs(-2 * P.nu0 * A / G - 1.0) <= 1e-3
