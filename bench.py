@@ -47,8 +47,14 @@ CS2 = 1.0 / 3.0
 # keyed by a hash of the kernel sources at capture time; a kernel changed since
 # its capture reports traffic null.  Summaries: profiles/*.md.
 MEASURED_DRAM = {
-    # profiles/k_primal_karman2d_re100.md (ncu --set full, one launch per AA parity)
-    ("58a4fea437ffb0bf", "karman2d_re100", "fp32", "bgk", "primal_step_accumulate"): 31_817_000,
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the two AA parities
+    # (profiles/k_primal_karman2d_re100.md, k_adjoint_karman2d_re100.md,
+    # k_primal_rr_les3d_re3900.md)
+    ("becd37e4ddd7147d", "karman2d_re100", "fp32", "bgk", "primal_step_accumulate"): 31_859_456,
+    ("becd37e4ddd7147d", "karman2d_re100", "fp32", "bgk", "primal_step_plain"): 18_052_608,
+    ("becd37e4ddd7147d", "karman2d_re100", "fp32", "bgk", "adjoint_step_ffa"): 30_269_696,
+    ("becd37e4ddd7147d", "les3d_re3900", "fp32", "rr", "primal_step_accumulate"): 6_411_626_000,
+    ("becd37e4ddd7147d", "les3d_re3900", "fp32", "rr", "primal_step_plain"): 3_137_791_500,
 }
 
 
@@ -86,8 +92,9 @@ def parse():
     ap.add_argument("--tau-adj", type=float, default=0.0,
                     help="adjoint relaxation time (0: tau0), the regularisation of Sec. 5.4")
     ap.add_argument("--adjoint-max-iter", type=int, default=20000)
-    ap.add_argument("--collision", default="bgk", choices=["bgk", "rr"],
-                    help="BGK (Sec. 2.1) or the recursive regularised collision (Sec. 2.2)")
+    ap.add_argument("--collision", default=None, choices=["bgk", "rr"],
+                    help="BGK (Sec. 2.1) or the recursive regularised collision (Sec. 2.2); "
+                         "default: the workload's (rr for the LES cases, else bgk)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", default=None, choices=["fp64", "fp32", "fp16dev", "bf16dev"],
@@ -115,7 +122,7 @@ def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False, rr=False):
     Averaging step: the populations and porosity of a plain step plus, for
     each running sum it updates, a read-modify-write of the sum -- 16 B for
     FP64 storage; for the other storages the sample goes to a float staging
-    value (8 B) that is folded into the FP64 sum every 16 samples
+    value (8 B) that is folded into the FP64 sum every 64 samples
     (16 B + 8 B, amortised 1.5 B).  Sums: density and momentum (1 + D), all q
     populations and tau_eff - tau0 when Cs > 0, and inside the objective
     regions the dJ/df coefficients (2 on the drag plane, 1 + D + D(D+1)/2 in
@@ -132,7 +139,7 @@ def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False, rr=False):
     b = r.diss_box
     diss_cells = (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
     les = wl.Cs > 0
-    sb = 16.0 if real_bytes == 8 else 8.0 + 24.0 / 16
+    sb = 16.0 if real_bytes == 8 else 8.0 + 24.0 / 64
     if rr:
         acc = plain + sb * (1 + D + D * (D + 1) // 2) + (sb if les else 0)
     else:
@@ -226,6 +233,8 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     wl = make_workload(args.workload, seed=rank)
+    if args.collision is None:
+        args.collision = wl.collision
     if args.storage:
         import dataclasses
         wl = dataclasses.replace(wl, storage=args.storage)
@@ -385,7 +394,7 @@ def roofline_of(res, args, H_storage_bytes, real_bytes):
 # the oracle on a bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(wl, steps, W, adj_iters, n_plain=10, n_acc=2, n_adj=20):
+def oracle_sample(wl, steps, W, adj_iters, n_plain=10, n_acc=2, n_adj=20, collision="bgk"):
     """Time the oracle on a bounded sample of the workload and extrapolate the
     whole job's LUP mix; returns (MLUPS, seconds spent, description)."""
     import contextlib
@@ -403,7 +412,7 @@ def oracle_sample(wl, steps, W, adj_iters, n_plain=10, n_acc=2, n_adj=20):
     t_start = time.perf_counter()
     with threadpool_limits(1):
         P = ohlbm.Params(wl.q, wl.dims, tau0=ohlbm.tau_from_reynolds(wl.u0, wl.L, wl.Re),
-                         Cs=wl.Cs, u_in=wl.u0)
+                         Cs=wl.Cs, u_in=wl.u0, collision=collision)
         f = ohlbm.initial_state(P, wl.u_perturb)
         d = wl.porosity
         t = time.perf_counter()
@@ -438,7 +447,8 @@ def run_reference(args):
     adj = [args.adjoint_max_iter, args.adjoint_max_iter]
     vals = []
     for k in range(args.warmup + args.steps):
-        v, spent, desc = oracle_sample(wl, steps, W, adj, n_plain=4, n_acc=1, n_adj=8)
+        v, spent, desc = oracle_sample(wl, steps, W, adj, n_plain=4, n_acc=1, n_adj=8,
+                                       collision=args.collision or wl.collision)
         if k >= args.warmup:
             vals.append((v, spent))
     value = statistics.median(v for v, _ in vals)
@@ -448,6 +458,7 @@ def run_reference(args):
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "grid": list(wl.dims), "lattice": f"D{2 if wl.q == 9 else 3}Q{wl.q}",
+                       "collision": args.collision or wl.collision,
                        "primal_steps": steps, "avg_window": W,
                        "adjoint_iters_assumed": adj},
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
@@ -481,7 +492,8 @@ def main():
     it_per_step = [ph["adj_iters"][k] / max(1, args.steps) for k in range(2)]
     cpu = None
     if not args.no_cpu_baseline:
-        v, spent, desc = oracle_sample(wl, res["steps"], res["W"], it_per_step)
+        v, spent, desc = oracle_sample(wl, res["steps"], res["W"], it_per_step,
+                                       collision=args.collision)
         cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": round(spent, 1)}
     line = {

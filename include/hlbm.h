@@ -148,6 +148,12 @@ typedef struct {
   void* alloc_user;
   int collision;        /* HLBM_COLL_BGK (default) or HLBM_COLL_RR; fixed at
                            hlbm_create (hlbm_configure rejects a change) */
+  const double* inflow_ux; /* optional host array of ny * nz values (y fastest):
+                           u_x of the inflow node f^eq(1, u_x e_x) per row, e.g.
+                           a parabolic channel profile; NULL = uniform u_in.
+                           Copied by hlbm_create / hlbm_configure (|u_x| < 0.5,
+                           else HLBM_EINVAL); u_in stays the reference velocity
+                           of J_FFA. */
 } hlbm_options;
 
 /* Velocity set of the library's direction order: xi (q x 3 ints, may be

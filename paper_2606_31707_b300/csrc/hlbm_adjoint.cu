@@ -202,18 +202,6 @@ __device__ __forceinline__ void add_xi(Vec3<R>& v, int i, R s) {
   if (L::cz(i)) v.z += L::cz(i) > 0 ? s : -s;
 }
 
-template <int Q, class R>
-__device__ __forceinline__ void add_xixi(Sym<R>& S, int i, R s) {
-  using L = Lat<Q>;
-  const int a = L::cx(i), b = L::cy(i), c = L::cz(i);
-  if (a) S.xx += s;
-  if (b) S.yy += s;
-  if (c) S.zz += s;
-  if (a && b) S.xy += a * b > 0 ? s : -s;
-  if (a && c) S.xz += a * c > 0 ? s : -s;
-  if (b && c) S.yz += b * c > 0 ? s : -s;
-}
-
 // mu <- C_f^T mu at one cell; gut (optional) receives dL/du~
 template <int Q, class R, bool EXACT>
 __device__ __forceinline__ void rr_transpose(const RRCell<R, EXACT>& c, R (&mu)[Q],
@@ -241,8 +229,8 @@ __device__ __forceinline__ void rr_transpose(const RRCell<R, EXACT>& c, R (&mu)[
     add_xi<Q>(V1, i, wm * cu);
     add_xi<Q>(T1, i, wm * cu * cu);
     add_xi<Q>(T2, i, wm * xPx);
-    add_xixi<Q>(s2, i, wm);
-    add_xixi<Q>(T3, i, wm * cu);
+    sym_add_xixi<Q>(s2, i, wm);
+    sym_add_xixi<Q>(T3, i, wm * cu);
   }
   const R rho = c.rho, om = c.om, c1 = R(1) - om;
   const R su = dot3(s1, ut);
@@ -363,7 +351,7 @@ __device__ __forceinline__ void residual_io(const AdjointArgs& a, long long cell
 }
 
 template <int Q, class R, bool ODD, bool EXACT, int RES, bool RR>
-__global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
+__device__ __forceinline__ void adjoint_body(const AdjointArgs& a) {
   constexpr int S = RealStore<R>::S;
   const Grid& g = a.g;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -407,6 +395,48 @@ __global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
   }
 }
 
+// Resident blocks per SM requested from ptxas for the FP32 D3Q19 sweeps
+// (0 = no request, ptxas chooses); the exact variants otherwise take more than
+// 120 registers.  Chosen by timing sweeps on the LES case (640x320x100):
+//   BGK exact LES: none 1419 us, 4 blocks 1262, 5: 1270
+//   RR exact:      none 1265, 4: 1154, 5: 1091
+//   RR frozen:     none 1167, 5: 1057, 6: 1043
+#ifndef HLBM_AMINB_D3Q19
+#define HLBM_AMINB_D3Q19 0
+#endif
+#ifndef HLBM_AMINB_D3Q19_EXACT
+#define HLBM_AMINB_D3Q19_EXACT 4
+#endif
+#ifndef HLBM_AMINB_D3Q19_RR
+#define HLBM_AMINB_D3Q19_RR 6
+#endif
+#ifndef HLBM_AMINB_D3Q19_RR_EXACT
+#define HLBM_AMINB_D3Q19_RR_EXACT 5
+#endif
+template <int Q, class R, bool EXACT, bool RR>
+constexpr int adjoint_min_blocks() {
+  if (Q != 19 || sizeof(R) != 4) return 0;
+  if (RR) return EXACT ? HLBM_AMINB_D3Q19_RR_EXACT : HLBM_AMINB_D3Q19_RR;
+  return EXACT ? HLBM_AMINB_D3Q19_EXACT : HLBM_AMINB_D3Q19;
+}
+
+template <int Q, class R, bool ODD, bool EXACT, int RES, bool RR>
+__global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
+  adjoint_body<Q, R, ODD, EXACT, RES, RR>(a);
+}
+
+template <int Q, class R, bool ODD, bool EXACT, int RES, bool RR, int MB>
+__global__ void __launch_bounds__(NT, MB) k_adjoint_mb(AdjointArgs a) {
+  adjoint_body<Q, R, ODD, EXACT, RES, RR>(a);
+}
+
+template <int Q, class R, bool ODD, bool EXACT, int RES, bool RR>
+static void launch_adj_one(const AdjointArgs& a, dim3 grid, int bx, cudaStream_t s) {
+  constexpr int mb = adjoint_min_blocks<Q, R, EXACT, RR>();
+  if constexpr (mb > 0) k_adjoint_mb<Q, R, ODD, EXACT, RES, RR, (mb > 0 ? mb : 1)><<<grid, bx, 0, s>>>(a);
+  else k_adjoint<Q, R, ODD, EXACT, RES, RR><<<grid, bx, 0, s>>>(a);
+}
+
 int adjoint_blocks(const Grid& g) { return ((g.nx + g.bx - 1) / g.bx) * g.ny * g.nz; }
 
 template <int Q, class R, bool RR>
@@ -414,7 +444,7 @@ static cudaError_t launch_adj_qr(const AdjointArgs& a, bool odd, bool exact, int
                                  cudaStream_t s) {
   const int bx = a.g.bx;
   dim3 grid((a.g.nx + bx - 1) / bx, a.g.ny, a.g.nz);
-#define HLBM_A(O, E, RS) k_adjoint<Q, R, O, E, RS, RR><<<grid, bx, 0, s>>>(a)
+#define HLBM_A(O, E, RS) launch_adj_one<Q, R, O, E, RS, RR>(a, grid, bx, s)
 #define HLBM_AR(O, E) \
   do { if (res == 0) HLBM_A(O, E, 0); else if (res == 1) HLBM_A(O, E, 1); else HLBM_A(O, E, 2); } while (0)
   if (!odd) { if (!exact) HLBM_AR(false, false); else HLBM_AR(false, true); }

@@ -33,6 +33,7 @@ struct hlbm_ctx {
   // primal state
   void* f = nullptr;
   void* d = nullptr;
+  double* inflow = nullptr;  // u_x on the inflow column (ny * nz), or null: uniform u_in
   int phase = 0;  // 0: natural layout, next primal kernel is even
   long steps_done = 0;
   // averages
@@ -330,6 +331,7 @@ PrimalArgs primal_args(hlbm_ctx* c) {
   a.ffa[4] = c->opt.ffa_z1;
   std::memcpy(a.db, c->opt.diss_box, sizeof a.db);
   a.err = c->err_dev;
+  a.inflow = c->inflow;
   return a;
 }
 
@@ -357,6 +359,25 @@ int hlbm_velocity_set(int lattice, int* xi, double* w) {
     return 19;
   }
   return HLBM_EINVAL;
+}
+
+// Copy a caller's inflow profile (u_x on the inflow column, ny * nz values,
+// y fastest) to the device; null restores the uniform inflow u_in.
+static int set_inflow(hlbm_ctx* c, const double* host) {
+  if (!host) {
+    if (c->inflow) dfree(c, c->inflow);
+    c->inflow = nullptr;
+    return HLBM_OK;
+  }
+  const long long n = (long long)c->g.ny * c->g.nz;
+  for (long long k = 0; k < n; ++k)
+    if (!std::isfinite(host[k]) || std::fabs(host[k]) >= 0.5)
+      return set_err(c, HLBM_EINVAL, "inflow profile: |u_x| < 0.5 and finite");
+  if (!c->inflow && !(c->inflow = (double*)dalloc(c, (size_t)n * 8)))
+    return set_err(c, HLBM_ENOMEM, "inflow profile");
+  HLBM_TRY(c, cudaMemcpyAsync(c->inflow, host, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream), "copy");
+  HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+  return HLBM_OK;
 }
 
 void hlbm_default_options(hlbm_options* o, const int dims[3]) {
@@ -502,6 +523,9 @@ int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau, doub
     rc = cuda_check(c, CNT(c, launch_init_eq)(c->f, c->g, c->q, c->storage, nullptr, nullptr, c->opt.u_in, c->stream), "init");
   if (rc == HLBM_OK) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "sync");
   if (rc != HLBM_OK) { hlbm_destroy(c); return rc; }
+  if (rc == HLBM_OK) rc = set_inflow(c, c->opt.inflow_ux);
+  c->opt.inflow_ux = nullptr;  // the context keeps its own copy
+  if (rc != HLBM_OK) { hlbm_destroy(c); return rc; }
   c->stats.primal_bytes_per_lup_plain = bytes_plain(c);
   *out = c;
   return HLBM_OK;
@@ -532,6 +556,8 @@ int hlbm_configure(hlbm_ctx* c, double tau, double Cs, const hlbm_options* opt) 
     c->opt.adjoint_solver = opt->adjoint_solver;
     c->opt.gmres_restart = opt->gmres_restart;
     c->opt.gmres_inner = opt->gmres_inner;
+    int rc = set_inflow(c, opt->inflow_ux);
+    if (rc) return rc;
   }
   c->tau0 = tau;
   c->Cs = Cs;
@@ -774,6 +800,7 @@ int hlbm_run_tangent(hlbm_ctx* c, long steps, const void* delta, int dtype, int 
   a.ffa[3] = c->opt.ffa_z0; a.ffa[4] = c->opt.ffa_z1;
   std::memcpy(a.db, c->opt.diss_box, sizeof a.db);
   a.jpart = c->red;
+  a.inflow = c->inflow;
   const bool les = c->Cs > 0.0;
   for (long n = 0; n < steps; ++n) {
     HLBM_TRY(c, CNT(c, launch_tangent)(a, c->q, c->storage, c->phase == 1, les, c->stream), "tangent");
@@ -1243,7 +1270,7 @@ int hlbm_get_field(hlbm_ctx* c, int which, void* out, int dtype, int on_device) 
       n = which == HLBM_FIELD_RHO ? N : (which == HLBM_FIELD_U ? (long long)c->D * N : qN);
       rc = ensure_stage(c, (size_t)n * 12);
       if (rc) return rc;
-      HLBM_TRY(c, CNT(c, launch_readout)(c->f, c->d, c->g, c->q, c->storage, c->phase == 1, c->opt.u_in,
+      HLBM_TRY(c, CNT(c, launch_readout)(c->f, c->d, c->g, c->q, c->storage, c->phase == 1, c->opt.u_in, c->inflow,
                                  which == HLBM_FIELD_F ? c->stage : nullptr,
                                  which == HLBM_FIELD_RHO ? c->stage : nullptr,
                                  which == HLBM_FIELD_U ? c->stage : nullptr, c->stream), "readout");
@@ -1505,6 +1532,7 @@ void hlbm_destroy(hlbm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   dfree(c, c->f);
   dfree(c, c->d);
+  if (c->inflow) dfree(c, c->inflow);
   dfree(c, c->msum);
   dfree(c, c->fsum);
   dfree(c, c->mstage);

@@ -293,6 +293,19 @@ __device__ __forceinline__ Sym<R> second_moment(const R (&g)[Q]) {
   return P;
 }
 
+// S += v xi_i xi_i (one direction's contribution to a second moment)
+template <int Q, class R>
+__device__ __forceinline__ void sym_add_xixi(Sym<R>& S, int i, R v) {
+  using L = Lat<Q>;
+  const int a = L::cx(i), b = L::cy(i), c = L::cz(i);
+  if (a) S.xx += v;
+  if (b) S.yy += v;
+  if (c) S.zz += v;
+  if (a && b) S.xy += (a * b > 0) ? v : -v;
+  if (a && c) S.xz += (a * c > 0) ? v : -v;
+  if (b && c) S.yz += (b * c > 0) ? v : -v;
+}
+
 template <class R> __device__ __forceinline__ R sym_norm2(const Sym<R>& P) {
   return P.xx * P.xx + P.yy * P.yy + P.zz * P.zz +
          R(2) * (P.xy * P.xy + P.xz * P.xz + P.yz * P.yz);

@@ -45,6 +45,8 @@ struct PrimalArgs {
   int ffa[5];         // x, y0, y1, z0, z1 of Gamma_J
   int db[6];          // Omega_J box
   unsigned* err;      // bit 0: non-finite or non-positive density
+  const double* inflow;  // ny * nz values of u_x on the inflow column (y fastest), or null:
+                         // uniform u_in
 };
 
 // Every objective's dJ/df_j is a polynomial of degree <= 2 in the lattice
@@ -68,7 +70,12 @@ __host__ __device__ inline double coef_basis(int obj_slot, int D, int k, int x, 
 
 // averaging variant bits of the primal kernel
 enum { ACC_ON = 1, ACC_FULL = 2, ACC_FLUSH = 4 };
-constexpr int kStage = 16;  // samples staged in FP32 before folding into FP64
+// 64 measured fastest of 16 / 32 / 64 (averaging step: Karman 16.4 / 16.1 / 16.0 us,
+// LES 2203 / 2096 / 2042 us); the staged value holds 64 FP32 samples at most
+#ifndef HLBM_KSTAGE
+#define HLBM_KSTAGE 64
+#endif
+constexpr int kStage = HLBM_KSTAGE;  // samples staged in FP32 before folding into FP64
 
 // launch one primal step kernel; storage 0..3, odd/les select variants,
 // acc: 0 no averaging, else ACC_ON | optional ACC_FULL (also average f) |
@@ -90,7 +97,7 @@ cudaError_t launch_fbar_out(const double* fsum, int q, long long N, double scale
 
 // readout of the canonical state: f (q x N), rho (N), u (3 x N); any may be null
 cudaError_t launch_readout(const void* f, const void* d, const Grid& g, int q, int storage,
-                           bool odd, double u_in, double* fout, double* rho, double* u,
+                           bool odd, double u_in, const double* inflow, double* fout, double* rho, double* u,
                            cudaStream_t s);
 // write a canonical state (q x N doubles) in natural layout
 cudaError_t launch_set_state(void* f, const Grid& g, int q, int storage, const double* in,

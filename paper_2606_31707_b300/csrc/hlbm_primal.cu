@@ -108,9 +108,6 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
   const R one_d = R(1) - d;
   const Vec3<R> ut{d * u.x + one_d * us.x, d * u.y + one_d * us.y, d * u.z + one_d * us.z};
   const R uu = dot3(ut, ut);
-  R fneq[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) fneq[i] = g[i] - geq_i<Q>(i, drho, rho, ut, uu);
 
   const R tau0 = par<R>(a.tau0, a.tau0_f);
   R tau = tau0;
@@ -118,7 +115,23 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
   R nP = 0;
   const bool diss_here = ACC > 0 && (a.obj_mask & 2) && x >= a.db[0] && x < a.db[1] &&
                          y >= a.db[2] && y < a.db[3] && z >= a.db[4] && z < a.db[5];
-  if (LES || diss_here || RR) P = second_moment<Q>(fneq);
+  // No array of f - f^eq stays alive across the collision (which recomputes
+  // f^eq): BGK sums the non-equilibrium stress direction by direction; the
+  // regularised collision, which reads f only through its moments up to
+  // order 2, takes it from the second moment of f - w,
+  //   Pi = sum xi xi (f - w) - rho u~ u~ - (rho - 1)/3 I.
+  // (Each form gave the fewer registers for its collision.)
+  Sym<R> M2{0, 0, 0, 0, 0, 0};  // sum xi xi (f - w), averaged for the RR linearisation
+  if constexpr (RR) {
+    M2 = second_moment<Q>(g);
+    const R t = drho * R(1.0 / 3.0);
+    P = Sym<R>{M2.xx - rho * ut.x * ut.x - t, M2.yy - rho * ut.y * ut.y - t,
+               D == 3 ? M2.zz - rho * ut.z * ut.z - t : R(0), M2.xy - rho * ut.x * ut.y,
+               M2.xz - rho * ut.x * ut.z, M2.yz - rho * ut.y * ut.z};
+  } else if (LES || diss_here) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) sym_add_xixi<Q>(P, i, g[i] - geq_i<Q>(i, drho, rho, ut, uu));
+  }
   if (LES || diss_here) nP = sqrt_r<R>(sym_norm2(P));
   const R kles = par<R>(a.kles, a.kles_f);
   if (LES) tau = tau_smagorinsky<R>(tau0, kles, nP);
@@ -155,11 +168,7 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
     sm[2].store(a.msum, a.mstage, 2 * N + cell, m.y);
     if (D == 3) sm[D].store(a.msum, a.mstage, (long long)D * N + cell, m.z);
     if constexpr (RR) {
-      // sum_i xi_i xi_i (f_i - w_i) = Pi + rho u~ u~ + (rho - 1)/3 I
-      const R t = drho * R(1.0 / 3.0);
-      const R m2[6] = {P.xx + rho * ut.x * ut.x + t, P.yy + rho * ut.y * ut.y + t,
-                       P.zz + rho * ut.z * ut.z + t, P.xy + rho * ut.x * ut.y,
-                       P.xz + rho * ut.x * ut.z, P.yz + rho * ut.y * ut.z};
+      const R m2[6] = {M2.xx, M2.yy, M2.zz, M2.xy, M2.xz, M2.yz};
       if constexpr (D == 2) {
         sm[3].store(a.msum, a.mstage, 3LL * N + cell, m2[0]);
         sm[4].store(a.msum, a.mstage, 4LL * N + cell, m2[1]);
@@ -226,36 +235,71 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
   }
 
   if constexpr (RR) {
-    const Vec3<R> a1{m.x - rho * ut.x, m.y - rho * ut.y, m.z - rho * ut.z};
+    // the sum f^eq3 + (1 - omega) f1 as a polynomial in xi_i:
+    //   w_i [C0 + xi.V + (9/2)(rho c^2 + c1 p) + (9/2) c (rho c^2 + 3 c1 p)],
+    //   c = xi.u~, p = xi.Pi.xi, c1 = 1 - omega,
+    //   C0 = (rho - 1) - (3/2) rho u~.u~ - (3/2) c1 tr Pi,
+    //   V = 3 rho u~ + 3 c1 a1 - (9/2) rho (u~.u~) u~ - (9/2) c1 (tr Pi u~ + 2 Pi u~)
+    const R c1 = R(1) - om;
     const R trP = P.xx + P.yy + P.zz;
     const Vec3<R> PU = sym_mul(P, ut);
-    const R c1 = R(1) - om;
+    const R C0 = drho - R(1.5) * rho * uu - R(1.5) * c1 * trP;
+    const R kv = R(3) * rho - R(4.5) * rho * uu - R(4.5) * c1 * trP - R(3) * c1 * rho;
+    const Vec3<R> V{kv * ut.x + R(3) * c1 * m.x - R(9) * c1 * PU.x,
+                    kv * ut.y + R(3) * c1 * m.y - R(9) * c1 * PU.y,
+                    kv * ut.z + R(3) * c1 * m.z - R(9) * c1 * PU.z};
+    const R r45 = R(4.5) * rho, c45 = R(4.5) * c1;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const R w = R(Lat<Q>::w(i));
       const R cu = xi_dot<Q>(i, ut);
       const R xPx = xi_P_xi<Q>(i, P);
-      const R e3 = w * R(4.5) * rho * cu * (cu * cu - uu);
-      const R f1 = w * (R(3) * xi_dot<Q>(i, a1) + R(4.5) * (xPx - trP * R(1.0 / 3.0)) +
-                        R(4.5) * (R(3) * cu * xPx - cu * trP - R(2) * xi_dot<Q>(i, PU)));
-      g[i] = (g[i] - fneq[i]) + e3 + c1 * f1;
+      const R rc2 = r45 * cu * cu;
+      g[i] = R(Lat<Q>::w(i)) * (C0 + xi_dot<Q>(i, V) + rc2 + c45 * xPx + cu * (rc2 + R(3) * c45 * xPx));
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] -= om * fneq[i];
+    for (int i = 0; i < Q; ++i) g[i] -= om * (g[i] - geq_i<Q>(i, drho, rho, ut, uu));
   }
   aa_store<Q, S, ODD, +1>(A, gr, rows, x, cell, g);
   return u;
 }
 
-// Resident blocks per SM requested for the averaging variants (caps their
-// registers at 65536 / (NT * HLBM_ACC_MINB)); 1 leaves the choice to ptxas.
-#ifndef HLBM_ACC_MINB
-#define HLBM_ACC_MINB 1
+// Resident blocks per SM requested from ptxas (which then caps registers at
+// 65536 / (NT * blocks)); 0 = no request (ptxas chooses).  Chosen by timing
+// each variant (CUDA events, 3 repeats) on the Karman case (D2Q9 1100x410)
+// and the LES case (D3Q19 640x320x100), FP32:
+//   D2Q9 BGK averaging:   none 18.5 us, 8 blocks 16.4 us (64 registers)
+//   D3Q19 BGK averaging:  none 2204 us, 3: 2230, 4: 2296, 5: 2564
+//   D3Q19 RR averaging:   none 1800 us, 4: 1880, 5: 1687
+//   D3Q19 RR plain:       none 712 us, 4: 796
+#ifndef HLBM_MINB_ACC_D2Q9
+#define HLBM_MINB_ACC_D2Q9 8
 #endif
+#ifndef HLBM_MINB_ACC_D3Q19
+#define HLBM_MINB_ACC_D3Q19 0
+#endif
+#ifndef HLBM_MINB_ACC_RR_D2Q9
+#define HLBM_MINB_ACC_RR_D2Q9 0
+#endif
+#ifndef HLBM_MINB_ACC_RR_D3Q19
+#define HLBM_MINB_ACC_RR_D3Q19 5
+#endif
+#ifndef HLBM_MINB_RR_D2Q9
+#define HLBM_MINB_RR_D2Q9 0
+#endif
+#ifndef HLBM_MINB_RR_D3Q19
+#define HLBM_MINB_RR_D3Q19 0
+#endif
+template <int Q, int ACC, bool RR>
+constexpr int primal_min_blocks() {
+  if (ACC > 0 && !RR) return Q == 9 ? HLBM_MINB_ACC_D2Q9 : HLBM_MINB_ACC_D3Q19;
+  if (ACC > 0) return Q == 9 ? HLBM_MINB_ACC_RR_D2Q9 : HLBM_MINB_ACC_RR_D3Q19;
+  if (RR) return Q == 9 ? HLBM_MINB_RR_D2Q9 : HLBM_MINB_RR_D3Q19;
+  return 0;
+}
 
 template <int Q, int S, bool ODD, bool LES, int ACC, bool RR>
-__global__ void __launch_bounds__(NT, (ACC > 0 ? HLBM_ACC_MINB : 1)) k_primal(PrimalArgs a) {
+__device__ __forceinline__ void primal_body(const PrimalArgs& a) {
   using St = Store<S>;
   using R = typename St::real;
   const Grid& gr = a.g;
@@ -269,7 +313,8 @@ __global__ void __launch_bounds__(NT, (ACC > 0 ? HLBM_ACC_MINB : 1)) k_primal(Pr
     const Rows rows = make_rows<Lat<Q>::D>(gr, y, z);
     R g[Q];
     if (x == 0) {
-      equilibrium_dev<Q, R>(g, R(0), Vec3<R>{par<R>(a.u_in, a.u_in_f), R(0), R(0)});
+      const R uin = a.inflow ? (R)a.inflow[y + (long long)gr.ny * z] : par<R>(a.u_in, a.u_in_f);
+      equilibrium_dev<Q, R>(g, R(0), Vec3<R>{uin, R(0), R(0)});
     } else {
       aa_load<Q, S, ODD, +1>(A, gr, rows, x, cell, g);
     }
@@ -294,12 +339,29 @@ __global__ void __launch_bounds__(NT, (ACC > 0 ? HLBM_ACC_MINB : 1)) k_primal(Pr
   }
 }
 
+template <int Q, int S, bool ODD, bool LES, int ACC, bool RR>
+__global__ void __launch_bounds__(NT) k_primal(PrimalArgs a) {
+  primal_body<Q, S, ODD, LES, ACC, RR>(a);
+}
+
+template <int Q, int S, bool ODD, bool LES, int ACC, bool RR, int MB>
+__global__ void __launch_bounds__(NT, MB) k_primal_mb(PrimalArgs a) {
+  primal_body<Q, S, ODD, LES, ACC, RR>(a);
+}
+
+template <int Q, int S, bool ODD, bool LES, int ACC, bool RR>
+static void launch_one(const PrimalArgs& a, dim3 grid, int bx, cudaStream_t s) {
+  constexpr int mb = primal_min_blocks<Q, ACC, RR>();
+  if constexpr (mb > 0) k_primal_mb<Q, S, ODD, LES, ACC, RR, (mb > 0 ? mb : 1)><<<grid, bx, 0, s>>>(a);
+  else k_primal<Q, S, ODD, LES, ACC, RR><<<grid, bx, 0, s>>>(a);
+}
+
 template <int Q, int S, bool RR>
 static cudaError_t launch_primal_qs(const PrimalArgs& a, bool odd, bool les, int acc,
                                     cudaStream_t s) {
   const int bx = a.g.bx;
   dim3 grid((a.g.nx + bx - 1) / bx, a.g.ny, a.g.nz);
-#define HLBM_L(O, L_, A_) k_primal<Q, S, O, L_, A_, RR><<<grid, bx, 0, s>>>(a)
+#define HLBM_L(O, L_, A_) launch_one<Q, S, O, L_, A_, RR>(a, grid, bx, s)
 #define HLBM_LA(O, L_)                                   \
   do {                                                   \
     switch (acc) {                                       \
@@ -349,7 +411,8 @@ cudaError_t launch_primal(const PrimalArgs& a, int q, int storage, bool odd, boo
 // state readout / initialisation
 // ----------------------------------------------------------------------------
 template <int Q, int S, bool ODD>
-__global__ void __launch_bounds__(NT) k_readout(const void* fv, Grid gr, double u_in, double* fout,
+__global__ void __launch_bounds__(NT) k_readout(const void* fv, Grid gr, double u_in,
+                                                const double* inflow, double* fout,
                                                 double* rho_out, double* u_out) {
   using St = Store<S>;
   using R = typename St::real;
@@ -361,7 +424,8 @@ __global__ void __launch_bounds__(NT) k_readout(const void* fv, Grid gr, double 
   const Rows rows = make_rows<Lat<Q>::D>(gr, y, z);
   R g[Q];
   if (x == 0) {
-    equilibrium_dev<Q, R>(g, R(0), Vec3<R>{R(u_in), R(0), R(0)});
+    const double uin = inflow ? inflow[y + (long long)gr.ny * z] : u_in;
+    equilibrium_dev<Q, R>(g, R(0), Vec3<R>{R(uin), R(0), R(0)});
   } else if (x == gr.nx - 1) {
     R gi[Q];
     aa_load<Q, S, ODD, +1>(A, gr, rows, x - 1, cell - 1, gi);
@@ -448,13 +512,13 @@ __global__ void __launch_bounds__(NT) k_init_eq(void* fv, Grid gr, const double*
   } while (0)
 
 cudaError_t launch_readout(const void* f, const void*, const Grid& g, int q, int storage,
-                           bool odd, double u_in, double* fout, double* rho, double* u,
-                           cudaStream_t s) {
+                           bool odd, double u_in, const double* inflow, double* fout, double* rho,
+                           double* u, cudaStream_t s) {
   dim3 grid((g.nx + NT - 1) / NT, g.ny, g.nz);
   if (odd) {
-    HLBM_DISPATCH_QS(q, storage, (k_readout<Q_, S_, true><<<grid, NT, 0, s>>>(f, g, u_in, fout, rho, u)));
+    HLBM_DISPATCH_QS(q, storage, (k_readout<Q_, S_, true><<<grid, NT, 0, s>>>(f, g, u_in, inflow, fout, rho, u)));
   } else {
-    HLBM_DISPATCH_QS(q, storage, (k_readout<Q_, S_, false><<<grid, NT, 0, s>>>(f, g, u_in, fout, rho, u)));
+    HLBM_DISPATCH_QS(q, storage, (k_readout<Q_, S_, false><<<grid, NT, 0, s>>>(f, g, u_in, inflow, fout, rho, u)));
   }
   return cudaGetLastError();
 }

@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(NT) k_tangent(TangentArgs a) {
     const Rows rows = make_rows<Lat<Q>::D>(gr, y, z);
     R g[Q], gd[Q];
     if (x == 0) {
-      geq_dev_all<Q, R>(g, R(0), R(1), Vec3<R>{par<R>(a.u_in, a.u_in_f), R(0), R(0)});
+      const R uin = a.inflow ? (R)a.inflow[y + (long long)gr.ny * z] : par<R>(a.u_in, a.u_in_f);
+      geq_dev_all<Q, R>(g, R(0), R(1), Vec3<R>{uin, R(0), R(0)});
 #pragma unroll
       for (int i = 0; i < Q; ++i) gd[i] = R(0);
     } else {

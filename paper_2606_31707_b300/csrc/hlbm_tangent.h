@@ -23,6 +23,7 @@ struct TangentArgs {
   int ffa[5];
   int db[6];
   double* jpart;      // per-block partial sums of J' of this step
+  const double* inflow;  // u_x on the inflow column (ny * nz), or null: uniform u_in
 };
 
 cudaError_t launch_tangent(const TangentArgs& a, int q, int storage, bool odd, bool les,

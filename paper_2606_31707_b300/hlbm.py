@@ -62,6 +62,7 @@ class hlbm_options(C.Structure):
         ("dev_free", _FREE),
         ("alloc_user", C.c_void_p),
         ("collision", C.c_int),
+        ("inflow_ux", C.c_void_p),
     ]
 
 

@@ -46,6 +46,7 @@ class Request:
     regions: object = None
     tag: object = None
     t_submit: float = 0.0
+    adjoint_solver: int = 0              # 0 fixed point, 1 restarted GMRES (same fixed point)
 
 
 @dataclass
@@ -61,8 +62,10 @@ class Result:
     lups: int
 
 
-def footprint_bytes(q: int, dims: Sequence[int], storage: int = H.FP32, objectives: int = 1) -> int:
-    """Device bytes one request holds (populations, averages, adjoint state)."""
+def footprint_bytes(q: int, dims: Sequence[int], storage: int = H.FP32, objectives: int = 1,
+                    adjoint_solver: int = 0, gmres_restart: int = 30) -> int:
+    """Device bytes one request holds (populations, averages, adjoint state,
+    and the Krylov basis when the adjoint runs GMRES)."""
     nx, ny, nz = dims
     N = nx * ny * nz
     pop = {H.FP64: 8, H.FP32: 4, H.FP16DEV: 2, H.BF16DEV: 2}[storage]
@@ -73,6 +76,8 @@ def footprint_bytes(q: int, dims: Sequence[int], storage: int = H.FP32, objectiv
     b += objectives * (q * N * 8 + N * 8)            # sum dJ/df, dJ/dd
     b += 2 * q * N * real + q * N * real + (D + 2) * N * real  # lambda, snapshot, source, record
     b += q * N * 8 * 2                               # staging for readouts
+    if adjoint_solver == 1:
+        b += (gmres_restart + 4) * q * N * real      # basis, w, x, c
     return int(b)
 
 
@@ -152,7 +157,7 @@ class SensitivityServer:
     def submit(self, req: Request) -> Future:
         fut: Future = Future()
         req.t_submit = time.perf_counter()
-        need = footprint_bytes(req.q, req.dims, req.storage)
+        need = footprint_bytes(req.q, req.dims, req.storage, adjoint_solver=req.adjoint_solver)
         if need > self.budget:
             fut.set_exception(H.HlbmError(H.ENOMEM, "request larger than the HBM budget"))
             return fut
@@ -234,10 +239,12 @@ def solve_one(req: Request, solver: Optional[Solver] = None, keep_context: bool 
     ``keep_context`` also the context (else it is destroyed)."""
     if solver is None:
         s = Solver(req.q, req.dims, req.tau, req.Cs, storage=req.storage, u_in=req.u_in,
-                   regions=req.regions, objectives=req.objective)
+                   regions=req.regions, objectives=req.objective,
+                   adjoint_solver=req.adjoint_solver)
     else:
         s = solver
-        s.configure(req.tau, req.Cs, u_in=req.u_in, regions=req.regions, objectives=req.objective)
+        s.configure(req.tau, req.Cs, u_in=req.u_in, regions=req.regions, objectives=req.objective,
+                    adjoint_solver=req.adjoint_solver)
     ok = False
     try:
         s.set_porosity(req.porosity)

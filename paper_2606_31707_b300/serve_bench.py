@@ -15,7 +15,11 @@ request is one mean-flow sensitivity solve with a fixed budget (2000 warm-up
 
 Prints one JSON line with gradients/s and p50/p99 latency of both, and the
 largest relative gradient difference between them (the served results are
-expected to be identical).
+expected to be identical when both use the same adjoint solver).  With
+``--served-solver gmres`` the served form solves the same adjoint fixed point
+by restarted GMRES; ``--accuracy`` then also solves every request untimed to a
+tighter tolerance and reports each form's largest relative gradient error
+against that reference, the accuracy at which the two are compared.
 """
 from __future__ import annotations
 
@@ -84,14 +88,15 @@ def run(args):
     wall_plain = time.perf_counter() - t0
     span_plain = clock - reqs[0][0]
 
-    # served path: submit at arrival times, in the chosen storage form
+    # served path: submit at arrival times, in the chosen storage and solver form
     import dataclasses
     st_code = {"fp32": H.FP32, "fp16dev": H.FP16DEV, "bf16dev": H.BF16DEV}[args.served_storage]
+    solver_code = 1 if args.served_solver == "gmres" else 0
     srv = SensitivityServer(slots=args.slots, hbm_budget=args.budget_gb << 30)
     t0 = time.perf_counter()
     futs = []
     for t_arr, r in reqs:
-        r = dataclasses.replace(r, storage=st_code)
+        r = dataclasses.replace(r, storage=st_code, adjoint_solver=solver_code)
         now = time.perf_counter() - t0
         if t_arr > now:
             time.sleep(t_arr - now)
@@ -107,6 +112,22 @@ def run(args):
     for a, b in zip(plain, served):
         den = float(np.linalg.norm(a.gradient)) or 1.0
         maxdiff = max(maxdiff, float(np.linalg.norm(a.gradient - b.gradient)) / den)
+    accuracy = None
+    if args.accuracy:
+        # untimed reference: the same requests, adjoint by GMRES to a tighter tolerance
+        ref = [solve_one(dataclasses.replace(r, adjoint_solver=1, tol=args.ref_tol,
+                                             max_iter=args.ref_max_iter)) for _, r in reqs]
+
+        def worst(results):
+            e = 0.0
+            for a, b in zip(results, ref):
+                den = float(np.linalg.norm(b.gradient)) or 1.0
+                e = max(e, float(np.linalg.norm(a.gradient - b.gradient)) / den)
+            return e
+        accuracy = {"reference": {"solver": "gmres", "tol": args.ref_tol,
+                                  "max_iter": args.ref_max_iter,
+                                  "residuals": [r.adjoint_residual for r in ref]},
+                    "plain_max_rel_err": worst(plain), "served_max_rel_err": worst(served)}
     lups = sum(r.lups for r in plain)
     line = {
         "metric": "served gradients/s and p50/p99 latency vs one solve at a time",
@@ -116,7 +137,10 @@ def run(args):
         "plain": {"gradients_per_s": len(plain) / span_plain, "p50_s": pct(lat_plain, 50),
                   "p99_s": pct(lat_plain, 99), "busy_s": wall_plain},
         "served": {"gradients_per_s": len(served) / span_served, "p50_s": pct(lat_served, 50),
-                   "p99_s": pct(lat_served, 99), "storage": args.served_storage},
+                   "p99_s": pct(lat_served, 99), "storage": args.served_storage,
+                   "adjoint_solver": args.served_solver,
+                   "adjoint_iters": [r.adjoint_iters for r in served]},
+        "accuracy": accuracy,
         "speedup_gradients_per_s": (len(served) / span_served) / (len(plain) / span_plain),
         "max_rel_gradient_diff_served_vs_plain": maxdiff,
         "mlups_plain": lups / wall_plain / 1e6,
@@ -139,6 +163,10 @@ def main():
     ap.add_argument("--max-iter", type=int, default=4000)
     ap.add_argument("--budget-gb", type=int, default=200)
     ap.add_argument("--served-storage", default="fp32", choices=["fp32", "fp16dev", "bf16dev"])
+    ap.add_argument("--served-solver", default="fixed-point", choices=["fixed-point", "gmres"])
+    ap.add_argument("--accuracy", action="store_true")
+    ap.add_argument("--ref-tol", type=float, default=1e-8)
+    ap.add_argument("--ref-max-iter", type=int, default=40000)
     run(ap.parse_args())
 
 

@@ -23,7 +23,7 @@ class Solver:
                  accum_stride: int = 1, check_every: int = 100, stream=None,
                  u_solid=(0.0, 0.0, 0.0), average_full_f: bool = False,
                  adjoint_solver: int = 0, gmres_restart: int = 30, gmres_inner: int = 100,
-                 collision: int = H.COLL_BGK):
+                 collision: int = H.COLL_BGK, inflow_profile=None):
         self.q = lattice
         self.dims = tuple(int(v) for v in dims)
         self.dim = 2 if lattice == 9 else 3
@@ -33,10 +33,17 @@ class Solver:
         opt.gmres_restart = gmres_restart
         opt.gmres_inner = gmres_inner
         opt.collision = collision
+        prof = None
+        if inflow_profile is not None:
+            prof = np.ascontiguousarray(inflow_profile, dtype=np.float64).ravel()
+            if prof.size != self.dims[1] * self.dims[2]:
+                raise ValueError("inflow_profile needs ny * nz values")
+            opt.inflow_ux = prof.ctypes.data
         if stream is not None:
             opt.stream = stream if isinstance(stream, int) else int(stream.cuda_stream)
         self.opt = opt
         self.ctx = H.hlbm_create(lattice, self.dims, tau, Cs, opt)
+        opt.inflow_ux = None  # copied by the library
         self.xi, self.w = H.hlbm_velocity_set(lattice)
         self._design(opt)
 
@@ -69,7 +76,7 @@ class Solver:
                   objectives: int = H.OBJ_DRAG_FFA | H.OBJ_DISSIPATION, tau_adj: float = 0.0,
                   accum_stride: int = 1, check_every: int = 100, u_solid=(0.0, 0.0, 0.0),
                   average_full_f: bool = False, adjoint_solver: int = 0, gmres_restart: int = 30,
-                  gmres_inner: int = 100):
+                  gmres_inner: int = 100, inflow_profile=None):
         """New physical parameters for this context (same grid and storage)."""
         opt = self._options(self.opt.storage, u_in, regions, objectives, tau_adj, accum_stride,
                             check_every, u_solid, average_full_f)
@@ -77,7 +84,14 @@ class Solver:
         opt.gmres_restart = gmres_restart
         opt.gmres_inner = gmres_inner
         opt.collision = self.opt.collision
+        prof = None
+        if inflow_profile is not None:
+            prof = np.ascontiguousarray(inflow_profile, dtype=np.float64).ravel()
+            if prof.size != self.dims[1] * self.dims[2]:
+                raise ValueError("inflow_profile needs ny * nz values")
+            opt.inflow_ux = prof.ctypes.data
         H.hlbm_configure(self.ctx, tau, Cs, opt)
+        opt.inflow_ux = None
         self._design(opt)
 
     # ------------------------------------------------------------------

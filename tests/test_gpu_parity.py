@@ -314,3 +314,34 @@ def test_mea_drag_objective_and_gradient_match_oracle(q, dims):
     G = oadj.gradient(lin, oadj.solve_adjoint_direct(lin, g), gd)
     b = R.design_box
     assert rel_l2(Gg, G[b[4]:b[5], b[2]:b[3], b[0]:b[1]]) <= 1e-9
+
+
+@pytest.mark.parametrize("q,dims", [(9, (300, 24, 1)), (19, (140, 10, 4))])
+def test_inflow_profile_steps_match_oracle(q, dims):
+    # prescribed-profile inflow node (the channel inflow of Sec. 5.1)
+    P, d, R = _case(q, dims, 0.0)
+    nx, ny, nz = dims
+    yy, zz = np.meshgrid(np.arange(ny), np.arange(nz), indexing="xy")
+    prof = 0.05 * (1 + 0.3 * np.sin(2 * np.pi * yy / ny) + 0.1 * np.cos(2 * np.pi * zz / nz))
+    P.u_in_profile = prof
+    f0 = _perturbed_state(P)
+    s = Solver(P.q, P.dims, P.tau0, 0.0, storage=H.FP64, u_in=P.u_in, regions=R,
+               inflow_profile=prof)
+    perm = direction_perm(s.xi, P)
+    s.set_porosity(d)
+    s.set_field(H.FIELD_F, to_lib(f0, perm))
+    s.run_primal(7, 0)
+    f = f0
+    for _ in range(7):
+        f = ohlbm.step(f, d, P)
+    assert rel_l2(s.field(H.FIELD_F), to_lib(f, perm)) <= 1e-13
+    # configure without a profile restores the uniform inflow (the inflow
+    # node of the canonical state follows the current parameters at once)
+    s.configure(P.tau0, 0.0, u_in=P.u_in, regions=R)
+    s.run_primal(1, 0)
+    P.u_in_profile = None
+    f = ohlbm.step(ohlbm.apply_boundary(f, P), d, P)
+    assert rel_l2(s.field(H.FIELD_F), to_lib(f, perm)) <= 1e-13
+    with pytest.raises(H.HlbmError):
+        s.configure(P.tau0, 0.0, u_in=P.u_in, regions=R, inflow_profile=np.full((nz, ny), 0.7))
+    s.close()

@@ -61,6 +61,9 @@ class Workload:
     the length ``L`` (the cylinder diameter unless stated), ``Cs`` the
     Smagorinsky constant (0 = plain BGK).  ``steps``/``avg_window`` are the
     primal step count and the number of final steps that are averaged.
+    ``collision`` is the collision the case is run with by default: the
+    turbulent cases use the recursive regularised collision of the paper's
+    turbulent model, the laminar ones BGK.
     """
 
     name: str
@@ -76,6 +79,7 @@ class Workload:
     porosity: np.ndarray          # (nz, ny, nx) float64 in [0, 1]
     u_perturb: Optional[np.ndarray]  # (3, nz, ny, nx) float64 or None
     storage: str = "fp32"
+    collision: str = "bgk"        # "bgk" or "rr" (the turbulent model's regularised collision)
 
     @property
     def cells(self) -> int:
@@ -200,7 +204,7 @@ def make_workload(name: str, seed: int = 0, **over) -> Workload:
         cu = int(D / 0.05)  # steps per convective unit D/u0
         up = velocity_perturbation(dims, 1e-3 * 0.05, seed)
         wl = Workload(name, 19, dims, 0.05, 3900.0, D, 0.1, 100 * cu, 50 * cu,
-                      _regions_cyl(dims, xc, D), d, up, "fp32")
+                      _regions_cyl(dims, xc, D), d, up, "fp32", "rr")
     elif name == "grf2d_re40":
         # differentiation case: D2Q9 400x160, GRF in a 60x60 box at (100, 80)
         dims = (400, 160, 1)
@@ -210,6 +214,16 @@ def make_workload(name: str, seed: int = 0, **over) -> Workload:
                           diss_box=(0, 400, 0, 160, 0, 1),
                           design_box=(70, 130, 50, 110, 0, 1))
         wl = Workload(name, 9, dims, 0.05, 40.0, 60.0, 0.0, 20000, 1, regions, d, None, "fp32")
+    elif name == "karman2d_4096":
+        # the Karman geometry scaled to a 4096 x 4096 D2Q9 grid (D = 500): a working set
+        # (0.6 GB of FP32 populations) far beyond L2, for the HBM-bound D2Q9 rates
+        dims = (4096, 4096, 1)
+        xc, yc, D = 1250.0, 2048.0, 500.0
+        d = cylinder_porosity(dims, xc, yc, D / 2, 2.0, jitter=0.01, seed=seed)
+        d = ring_porosity(d, dims, xc, yc, D / 2, 10, 10, 0.2, 0.8, seed=seed + 1)
+        up = velocity_perturbation(dims, 1e-3 * 0.04, seed)
+        wl = Workload(name, 9, dims, 0.04, 100.0, D, 0.0, 3000, 1000,
+                      _regions_cyl(dims, xc, D, diss_half=2.0), d, up, "fp32")
     elif name.startswith("tiny"):
         # small cases for tests: tiny2d / tiny3d
         if name == "tiny3d":
@@ -229,7 +243,7 @@ def make_workload(name: str, seed: int = 0, **over) -> Workload:
     return wl
 
 
-WORKLOADS = ("cyl2d_re20", "karman2d_re100", "les3d_re3900", "les3d_re3900_quarter",
+WORKLOADS = ("cyl2d_re20", "karman2d_re100", "karman2d_4096", "les3d_re3900", "les3d_re3900_quarter",
              "grf2d_re40", "tiny2d", "tiny3d")
 
 
