@@ -275,3 +275,49 @@ def newton_steady(f, d, P: Params, iters=8, tol=1e-14):
         M = (sp.identity(n, format="csr") - lin.A).tocsc()
         f = f + spsolve(M, r.ravel()).reshape(f.shape)
     return f, res
+
+
+def unsteady_adjoint_gradient(f0, d, P: Params, T: int, objective, regions, checkpoint_every=None):
+    """Exact gradient of the short-horizon time average J_T = (1/T) sum_{n<T} J(f^n; d),
+    f^{n+1} = Phi(f^n; d) from a fixed f^0, by the discrete unsteady adjoint -- the
+    validation reference for the transient sensitivities (App. C), against which the
+    mean-flow adjoint is an approximation.
+
+    Backward sweep with the exact step Jacobians at every state:
+        lambda^T = 0,  lambda^n = A_n^T lambda^{n+1} + g_n / T   (n = T-1 .. 1),
+        dJ_T/dd = (1/T) sum_n dJ/dd(f^n) + sum_{n=0}^{T-2} D_n^T lambda^{n+1},
+    A_n = dPhi/df and D_n = dPhi/dd at f^n (outflow node linearised at the streamed
+    state: the exact derivative of the step).  The forward states are kept only at
+    checkpoints every c = ceil(sqrt(T)) steps and recomputed segment by segment
+    during the backward sweep.  Returns (gradient, J_T, forward steps taken)."""
+    c = checkpoint_every or int(np.ceil(np.sqrt(T)))
+    checkpoints = {}
+    f = f0.copy()
+    JT = 0.0
+    fwd = 0
+    for n in range(T):
+        if n % c == 0:
+            checkpoints[n] = f.copy()
+        JT += obj.value(f, d, P, objective, regions) / T
+        if n < T - 1:
+            f = step(f, d, P)
+            fwd += 1
+    lam = np.zeros_like(f0)
+    G = np.zeros(P.shape)
+    for start in sorted(checkpoints, reverse=True):
+        end = min(start + c, T)
+        seg = [checkpoints[start]]
+        for _ in range(start, end - 1):
+            seg.append(step(seg[-1], d, P))
+            fwd += 1
+        for n in range(end - 1, start - 1, -1):
+            fn = seg[n - start]
+            g, gd = obj.partials(fn, d, P, objective, regions)
+            G += gd / T
+            lin = Linearisation(fn, d, P, EXACT, outlet="streamed")
+            if n < T - 1:
+                # lam holds lambda^{n+1}: the step out of f^n carries D_n^T lambda^{n+1}
+                G += (lin.DT @ lam.ravel()).reshape(P.shape)
+            if n >= 1:
+                lam = (lin.AT @ lam.ravel()).reshape(f0.shape) + g / T
+    return G, JT, fwd
