@@ -73,3 +73,19 @@ def test_tangent_matches_central_differences_of_the_objective():
         Js.append(np.array(hist))
     fd = (Js[0] - Js[1]) / (2 * h)
     assert rel_l2(got[1:], fd[1:]) <= 1e-6
+
+
+@pytest.mark.parametrize("q,Cs", [(9, 0.0), (9, 0.15), (19, 0.1)])
+def test_tangent_mean_matches_the_unsteady_adjoint_reference(q, Cs):
+    # d J_T / dd . delta for the short-horizon average J_T = (1/T) sum_n J(f^n):
+    # the mean of the GPU tangent's per-step derivatives against the oracle's
+    # checkpointed unsteady adjoint (duality of forward and reverse mode)
+    P, d, R, delta = _case(q, Cs)
+    T = 30
+    s = Solver(q, P.dims, P.tau0, P.Cs, storage=H.FP64, u_in=P.u_in, regions=R)
+    s.set_porosity(d)
+    jd = H.hlbm_run_tangent(s.ctx, T, np.ascontiguousarray(delta.ravel()), oobj.DISS)
+    s.close()
+    G, _, _ = oadj.unsteady_adjoint_gradient(ohlbm.initial_state(P), d, P, T, oobj.DISS, R)
+    ref = float((G * delta).sum())
+    assert abs(float(np.mean(jd)) - ref) <= 1e-10 * max(abs(ref), 1e-12)
