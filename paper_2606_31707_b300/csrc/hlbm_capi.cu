@@ -238,6 +238,14 @@ int obj_slot(int obj) {
 
 size_t coef_bytes(const hlbm_ctx* c, int o) { return (size_t)ncoef(o, c->D) * c->g.N * 8; }
 
+// FP32 staging: the moment sums packed in float4 planes; the drag coefficients
+// in plain planes; the dissipation coefficients and dJ/dd packed together
+size_t mstage_bytes(const hlbm_ctx* c) { return (size_t)stage_planes4(c->mplanes) * c->g.N * 16; }
+size_t gstage_bytes(const hlbm_ctx* c, int o) {
+  return o == 0 ? (size_t)ncoef(0, c->D) * c->g.N * 4
+                : (size_t)stage_planes4(ncoef(1, c->D) + 1) * c->g.N * 16;
+}
+
 int ensure_averages(hlbm_ctx* c, int mask) {
   const long long N = c->g.N;
   const size_t qN = (size_t)c->q * N * 8;
@@ -247,14 +255,13 @@ int ensure_averages(hlbm_ctx* c, int mask) {
   if (!c->tsum && !(c->tsum = (double*)dalloc(c, (size_t)N * 8))) return set_err(c, HLBM_ENOMEM, "tsum");
   const bool stage = !real_is_double(c);
   if (stage) {
-    if (!c->mstage && !(c->mstage = (float*)dalloc(c, (size_t)c->mplanes * N * 4))) return set_err(c, HLBM_ENOMEM, "mstage");
+    if (!c->mstage && !(c->mstage = (float*)dalloc(c, mstage_bytes(c)))) return set_err(c, HLBM_ENOMEM, "mstage");
     if (c->full_f && !c->fstage && !(c->fstage = (float*)dalloc(c, (size_t)c->q * N * 4))) return set_err(c, HLBM_ENOMEM, "fstage");
     if (!c->tstage && !(c->tstage = (float*)dalloc(c, (size_t)N * 4))) return set_err(c, HLBM_ENOMEM, "tstage");
   }
   for (int o = 0; o < 2; ++o) {
     if (!(mask & (1 << o))) continue;
-    if (stage && !c->gstage[o] && !(c->gstage[o] = (float*)dalloc(c, coef_bytes(c, o) / 2))) return set_err(c, HLBM_ENOMEM, "gstage");
-    if (stage && !c->ddstage[o] && !(c->ddstage[o] = (float*)dalloc(c, (size_t)N * 4))) return set_err(c, HLBM_ENOMEM, "ddstage");
+    if (stage && !c->gstage[o] && !(c->gstage[o] = (float*)dalloc(c, gstage_bytes(c, o)))) return set_err(c, HLBM_ENOMEM, "gstage");
     if (!c->gsum[o] && !(c->gsum[o] = (double*)dalloc(c, coef_bytes(c, o)))) return set_err(c, HLBM_ENOMEM, "gsum");
     if (!c->ddsum[o] && !(c->ddsum[o] = (double*)dalloc(c, (size_t)N * 8))) return set_err(c, HLBM_ENOMEM, "ddsum");
     if (!c->jblk[o] && !(c->jblk[o] = (double*)dalloc(c, (size_t)c->nblk * 8))) return set_err(c, HLBM_ENOMEM, "jblk");
@@ -269,13 +276,12 @@ int reset_averages(hlbm_ctx* c, int mask) {
   HLBM_TRY(c, cudaMemsetAsync(c->msum, 0, (size_t)c->mplanes * N * 8, c->stream), "memset");
   if (c->fsum) HLBM_TRY(c, cudaMemsetAsync(c->fsum, 0, (size_t)c->q * N * 8, c->stream), "memset");
   HLBM_TRY(c, cudaMemsetAsync(c->tsum, 0, (size_t)N * 8, c->stream), "memset");
-  if (c->mstage) HLBM_TRY(c, cudaMemsetAsync(c->mstage, 0, (size_t)c->mplanes * N * 4, c->stream), "memset");
+  if (c->mstage) HLBM_TRY(c, cudaMemsetAsync(c->mstage, 0, mstage_bytes(c), c->stream), "memset");
   if (c->fstage) HLBM_TRY(c, cudaMemsetAsync(c->fstage, 0, (size_t)c->q * N * 4, c->stream), "memset");
   if (c->tstage) HLBM_TRY(c, cudaMemsetAsync(c->tstage, 0, (size_t)N * 4, c->stream), "memset");
   for (int o = 0; o < 2; ++o) {
     if (!(mask & (1 << o))) continue;
-    if (c->gstage[o]) HLBM_TRY(c, cudaMemsetAsync(c->gstage[o], 0, coef_bytes(c, o) / 2, c->stream), "memset");
-    if (c->ddstage[o]) HLBM_TRY(c, cudaMemsetAsync(c->ddstage[o], 0, (size_t)N * 4, c->stream), "memset");
+    if (c->gstage[o]) HLBM_TRY(c, cudaMemsetAsync(c->gstage[o], 0, gstage_bytes(c, o), c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->gsum[o], 0, coef_bytes(c, o), c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->ddsum[o], 0, (size_t)N * 8, c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->jblk[o], 0, (size_t)c->nblk * 8, c->stream), "memset");

@@ -36,11 +36,14 @@ struct PrimalArgs {
   // the staged value into the FP64 sum every kStage samples (flush variant),
   // so that the per-step path issues no FP64 instruction; FP64 kernels add to
   // the sums directly and leave these null
+  // The density/momentum(/second-moment) sums and the dissipation terms (its
+  // coefficients, then dJ/dd) are staged packed: float4 planes of
+  // stage_planes4(count) x N, sum k in component k % 4 of plane k / 4.
   float* mstage;
   float* fstage;
   float* tstage;
-  float* gstage[2];
-  float* ddstage[2];
+  float* gstage[2];   // [0]: FFA coefficients, plain planes; [1]: dissipation, packed
+  float* ddstage[2];  // unused by the packed dissipation group
   int obj_mask;
   int ffa[5];         // x, y0, y1, z0, z1 of Gamma_J
   int db[6];          // Omega_J box
@@ -67,6 +70,9 @@ __host__ __device__ inline double coef_basis(int obj_slot, int D, int k, int x, 
   if (D == 2) return 2.0 * x * y;
   return 2.0 * (k == 0 ? x * y : (k == 1 ? x * z : y * z));
 }
+
+// float4 planes holding `count` packed FP32 staging values per cell
+__host__ __device__ constexpr int stage_planes4(int count) { return (count + 3) / 4; }
 
 // averaging variant bits of the primal kernel
 enum { ACC_ON = 1, ACC_FULL = 2, ACC_FLUSH = 4 };

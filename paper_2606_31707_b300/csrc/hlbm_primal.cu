@@ -66,6 +66,59 @@ struct AccSlot {
   }
 };
 
+// A group of G running sums of one cell updated together.  FP64 kernels add to
+// the FP64 sums directly (one AccSlot each).  FP32 kernels keep the staged
+// values packed in float4 planes (one 16-byte load and store per four sums
+// instead of four 4-byte ones) and, in the flush variant, fold them into the
+// FP64 sums.  addr(k) gives the FP64 sum of component k at this cell.
+__device__ __forceinline__ float& comp4(float4& v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+template <class R, int ACC, int G>
+struct SumGroup {
+  static constexpr bool PACKED = sizeof(R) == 4;
+  static constexpr bool FLUSH = (ACC & ACC_FLUSH) != 0;
+  static constexpr int C4 = stage_planes4(G);
+  float4 t[PACKED ? C4 : 1];
+  double s[(!PACKED || FLUSH) ? G : 1];
+  template <class Addr>
+  __device__ __forceinline__ void load(const Addr& addr, const float* stage, long long N,
+                                       long long cell) {
+    if constexpr (PACKED) {
+      const float4* st = reinterpret_cast<const float4*>(stage);
+#pragma unroll
+      for (int j = 0; j < C4; ++j) t[j] = st[(long long)j * N + cell];
+    }
+    if constexpr (!PACKED || FLUSH) {
+#pragma unroll
+      for (int k = 0; k < G; ++k) s[k] = *addr(k);
+    }
+  }
+  template <class Addr>
+  __device__ __forceinline__ void store(const Addr& addr, float* stage, long long N,
+                                        long long cell, const R (&v)[G]) {
+    if constexpr (!PACKED) {
+#pragma unroll
+      for (int k = 0; k < G; ++k) *addr(k) = s[k] + (double)v[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < G; ++k) {
+        float& c = comp4(t[k / 4], k % 4);
+        if constexpr (FLUSH) {
+          *addr(k) = s[k] + (double)(c + v[k]);
+          c = 0.0f;
+        } else {
+          c += v[k];
+        }
+      }
+      float4* st = reinterpret_cast<float4*>(stage);
+#pragma unroll
+      for (int j = 0; j < C4; ++j) st[(long long)j * N + cell] = t[j];
+    }
+  }
+};
+
 // Collide the canonical state of one cell (as deviations g = f - w), store it
 // AA-style, and (ACC > 0) add the cell's samples to the running averages.
 // Returns the velocity.
@@ -144,10 +197,15 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
     constexpr int NCD = 1 + D + D * (D + 1) / 2;  // dissipation coefficients
     // old values of every sum this cell updates, loaded together
     constexpr int NM = 1 + D + (RR ? D * (D + 1) / 2 : 0);  // moment sums
-    AccSlot<R, ACC> sm[NM], sg0[2], sg1[NCD], sdd, st;
+    const auto maddr = [&](int k) { return a.msum + (long long)k * N + cell; };
+    double* const g1 = a.gsum[1];
+    double* const dd1 = a.ddsum[1];
+    const auto daddr = [&](int k) { return k < NCD ? g1 + (long long)k * N + cell : dd1 + cell; };
+    SumGroup<R, ACC, NM> sm;
+    SumGroup<R, ACC, NCD + 1> sdiss;
+    AccSlot<R, ACC> sg0[2], st;
     AccSlot<R, ACC> sf[(ACC & ACC_FULL) != 0 ? Q : 1];
-#pragma unroll
-    for (int k = 0; k < NM; ++k) sm[k].load(a.msum, a.mstage, (long long)k * N + cell);
+    sm.load(maddr, a.mstage, N, cell);
     if constexpr ((ACC & ACC_FULL) != 0) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) sf[i].load(a.fsum, a.fstage, (long long)i * N + cell);
@@ -157,26 +215,29 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
       sg0[0].load(a.gsum[0], a.gstage[0], cell);
       sg0[1].load(a.gsum[0], a.gstage[0], N + cell);
     }
-    if (diss_here) {
-#pragma unroll
-      for (int k = 0; k < NCD; ++k) sg1[k].load(a.gsum[1], a.gstage[1], (long long)k * N + cell);
-      sdd.load(a.ddsum[1], a.ddstage[1], cell);
-    }
+    if (diss_here) sdiss.load(daddr, a.gstage[1], N, cell);
 
-    sm[0].store(a.msum, a.mstage, cell, drho);
-    sm[1].store(a.msum, a.mstage, N + cell, m.x);
-    sm[2].store(a.msum, a.mstage, 2 * N + cell, m.y);
-    if (D == 3) sm[D].store(a.msum, a.mstage, (long long)D * N + cell, m.z);
-    if constexpr (RR) {
-      const R m2[6] = {M2.xx, M2.yy, M2.zz, M2.xy, M2.xz, M2.yz};
-      if constexpr (D == 2) {
-        sm[3].store(a.msum, a.mstage, 3LL * N + cell, m2[0]);
-        sm[4].store(a.msum, a.mstage, 4LL * N + cell, m2[1]);
-        sm[5].store(a.msum, a.mstage, 5LL * N + cell, m2[3]);
-      } else {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) sm[4 + k].store(a.msum, a.mstage, (long long)(4 + k) * N + cell, m2[k]);
+    {
+      R mv[NM];
+      mv[0] = drho;
+      mv[1] = m.x;
+      mv[2] = m.y;
+      if constexpr (D == 3) mv[3] = m.z;
+      if constexpr (RR) {
+        if constexpr (D == 2) {
+          mv[3] = M2.xx;
+          mv[4] = M2.yy;
+          mv[5] = M2.xy;
+        } else {
+          mv[4] = M2.xx;
+          mv[5] = M2.yy;
+          mv[6] = M2.zz;
+          mv[7] = M2.xy;
+          mv[8] = M2.xz;
+          mv[9] = M2.yz;
+        }
       }
+      sm.store(maddr, a.mstage, N, cell, mv);
     }
     if constexpr ((ACC & ACC_FULL) != 0) {
 #pragma unroll
@@ -209,7 +270,7 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
       const R trP = P.xx + P.yy + P.zz;
       const R uPU = dot3(u, PU);
       const R c2 = one_d / tau0 * R(2) / rho;
-      R cf[NCD];
+      R cf[NCD + 1];  // the dJ/df coefficients, then dJ/dd
       cf[0] = fac * (-trP * R(1.0 / 3.0) - uPu + R(2) * d * uPU) - c2 * uu_raw;
       cf[1] = -R(2) * d * fac * PU.x + c2 * u.x;
       cf[2] = -R(2) * d * fac * PU.y + c2 * u.y;
@@ -226,10 +287,9 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
         cf[8] = fac * P.xz;
         cf[9] = fac * P.yz;
       }
-#pragma unroll
-      for (int k = 0; k < NCD; ++k) sg1[k].store(a.gsum[1], a.gstage[1], (long long)k * N + cell, cf[k]);
       const Vec3<R> v{u.x - us.x, u.y - us.y, u.z - us.z};
-      sdd.store(a.ddsum[1], a.ddstage[1], cell, fac * (-R(2) * rho * dot3(v, PU)) - uu_raw / tau0);
+      cf[NCD] = fac * (-R(2) * rho * dot3(v, PU)) - uu_raw / tau0;
+      sdiss.store(daddr, a.gstage[1], N, cell, cf);
       jp[1] += J;
     }
   }

@@ -345,3 +345,42 @@ def test_inflow_profile_steps_match_oracle(q, dims):
     with pytest.raises(H.HlbmError):
         s.configure(P.tau0, 0.0, u_in=P.u_in, regions=R, inflow_profile=np.full((nz, ny), 0.7))
     s.close()
+
+
+@pytest.mark.parametrize("q,dims,Cs,coll", [(9, (300, 24, 1), 0.0, H.COLL_BGK),
+                                           (9, (300, 24, 1), 0.2, H.COLL_BGK),
+                                           (19, (150, 10, 6), 0.15, H.COLL_BGK),
+                                           (9, (300, 24, 1), 0.1, H.COLL_RR)])
+def test_fp32_staged_averages_match_oracle(q, dims, Cs, coll):
+    # FP32 runs stage every sample in float and fold into the FP64 sums every
+    # 64 samples and at the window's end: a 150-step window crosses two folds
+    P, d, R = _case(q, dims, Cs)
+    if coll == H.COLL_RR:
+        P.collision = "rr"
+    f0 = _perturbed_state(P)
+    s = Solver(P.q, P.dims, P.tau0, P.Cs, storage=H.FP32, u_in=P.u_in, regions=R,
+               average_full_f=True, collision=coll)
+    perm = direction_perm(s.xi, P)
+    s.set_porosity(d)
+    s.set_field(H.FIELD_F, to_lib(f0, perm))
+    s.run_primal(160, 150)
+    # the oracle averages the same window from the library's (FP32) state at its start
+    s2 = Solver(P.q, P.dims, P.tau0, P.Cs, storage=H.FP32, u_in=P.u_in, regions=R, collision=coll)
+    s2.set_porosity(d)
+    s2.set_field(H.FIELD_F, to_lib(f0, perm))
+    s2.run_primal(10, 0)
+    f_start = s2.field(H.FIELD_F)[np.argsort(perm)]
+    s2.close()
+    out = omf.run_primal(f_start, d, P, 150, 150, R, 3)
+    assert rel_l2(s.field(H.FIELD_FBAR), to_lib(out["fbar"], perm)) <= 1e-5
+    for o, gf, df in ((oobj.FFA, H.FIELD_GBAR_FFA, H.FIELD_DJDD_FFA),
+                      (oobj.DISS, H.FIELD_GBAR_DISS, H.FIELD_DJDD_DISS)):
+        assert rel_l2(s.field(gf), to_lib(out[("gbar", o)], perm)) <= 1e-4
+        if o == oobj.DISS:
+            assert rel_l2(s.field(df), out[("dJdd_bar", o)]) <= 1e-4
+        # J_FFA is a small difference of O(u0^2) plane sums (a cancellation of
+        # about two digits), so its FP32 bound is looser than the fields'
+        assert abs(s.objective(o) - out[("Jbar", o)]) <= 5e-4 * abs(out[("Jbar", o)])
+    if Cs > 0:
+        assert rel_l2(s.field(H.FIELD_TAU_T), out["tau_t_bar"]) <= 1e-4
+    s.close()
