@@ -50,11 +50,11 @@ MEASURED_DRAM = {
     # ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the two AA parities
     # (profiles/k_primal_karman2d_re100.md, k_adjoint_karman2d_re100.md,
     # k_primal_rr_les3d_re3900.md)
-    ("becd37e4ddd7147d", "karman2d_re100", "fp32", "bgk", "primal_step_accumulate"): 31_859_456,
-    ("becd37e4ddd7147d", "karman2d_re100", "fp32", "bgk", "primal_step_plain"): 18_052_608,
-    ("becd37e4ddd7147d", "karman2d_re100", "fp32", "bgk", "adjoint_step_ffa"): 30_269_696,
-    ("becd37e4ddd7147d", "les3d_re3900", "fp32", "rr", "primal_step_accumulate"): 6_411_626_000,
-    ("becd37e4ddd7147d", "les3d_re3900", "fp32", "rr", "primal_step_plain"): 3_137_791_500,
+    ("31489d5ea0988b20", "karman2d_re100", "fp32", "bgk", "primal_step_accumulate"): 34_510_000,
+    ("31489d5ea0988b20", "karman2d_re100", "fp32", "bgk", "primal_step_plain"): 18_050_000,
+    ("31489d5ea0988b20", "karman2d_re100", "fp32", "bgk", "adjoint_step_ffa"): 30_270_000,
+    ("31489d5ea0988b20", "les3d_re3900", "fp32", "rr", "primal_step_accumulate"): 6_872_420_000,
+    ("31489d5ea0988b20", "les3d_re3900", "fp32", "rr", "primal_step_plain"): 3_138_120_000,
 }
 
 

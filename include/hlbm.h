@@ -6,20 +6,24 @@
  * Unsteady Flow Around Porous Cylinders Using a Homogenized Lattice
  * Boltzmann Method"):
  *   1. the primal homogenized LBM (Sec. 2.1, Eq. hlbm with the porous
- *      equilibrium; Smagorinsky tau_eff of Sec. 2.2) with on-device
- *      tracking averages (Sec. 3.3, Eq. averageObjective);
+ *      equilibrium; BGK or the recursive regularised collision of Sec. 2.2,
+ *      Smagorinsky tau_eff) with on-device tracking averages (Sec. 3.3,
+ *      Eq. averageObjective);
  *   2. the steady / mean-flow adjoint LBM (Eq. adjoint_steady,
- *      Eq. adjoint_unsteady), exact or frozen-turbulence (Sec. 5.4);
+ *      Eq. adjoint_unsteady), exact or frozen-turbulence (Sec. 5.4), by its
+ *      fixed-point iteration or by restarted GMRES on the same fixed point;
  *   3. the gradient contraction dJ/dd (Eq. gradients_steady,
  *      Eq. gradients_unsteady)
- * for the far-field drag J_FFA (Sec. 4.2) and the dissipation J_DISS
- * (Sec. 4.3).
+ * for the far-field drag J_FFA (Sec. 4.2), the dissipation J_DISS
+ * (Sec. 4.3) and the momentum-exchange drag J_MEA (Sec. 4.1); plus the
+ * tangent-linear primal step of the exact transient sensitivities (App. C).
  *
  * Conventions (all entry points):
  *  - Lattice units (dx = dt = 1).  Grids are (nx, ny, nz), nz = 1 for D2Q9;
  *    cell index = x + nx*(y + ny*z) ("canonical order").  x = 0 is an
- *    equilibrium inflow node, x = nx-1 an outflow node; y and z are
- *    periodic.  nx >= 4, ny >= 1, nz >= 1.
+ *    equilibrium inflow node (uniform u_in, or the profile inflow_ux),
+ *    x = nx-1 an outflow node; y and z are periodic.  nx >= 4, ny >= 1,
+ *    nz >= 1.
  *  - Multi-component fields are component-major: component c of cell k is
  *    at [c*N + k], N = nx*ny*nz.
  *  - Every call returns a status: HLBM_OK (0), HLBM_NOT_CONVERGED (1, a
