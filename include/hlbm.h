@@ -182,9 +182,12 @@ int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau,
 /* Change the physical parameters of an existing context without
  * reallocating it: relaxation time tau, Smagorinsky constant Cs and, from
  * opt (may be NULL), u_in, u_solid, tau_adj, objectives, the regions,
- * accum_stride, check_every and average_full_f (storage, stream, allocator
- * and block_x keep their creation values).  Clears the averages and the
- * adjoint; the state and the porosity are kept.  Lets a server reuse a
+ * accum_stride, check_every, average_full_f, the adjoint solver settings and
+ * the inflow profile (NULL restores the uniform inflow); storage, stream,
+ * allocator, block_x and collision keep their creation values (a different
+ * collision is HLBM_EINVAL).  Clears the averages and the adjoint; the state
+ * and the porosity are kept.  Arguments are checked before anything changes,
+ * so an HLBM_EINVAL leaves the context as it was.  Lets a server reuse a
  * context (and its captured graphs) for a new request of the same grid. */
 int hlbm_configure(hlbm_ctx* ctx, double tau, double Cs, const hlbm_options* opt);
 

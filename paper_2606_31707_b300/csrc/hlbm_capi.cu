@@ -369,6 +369,14 @@ int hlbm_velocity_set(int lattice, int* xi, double* w) {
 
 // Copy a caller's inflow profile (u_x on the inflow column, ny * nz values,
 // y fastest) to the device; null restores the uniform inflow u_in.
+static int check_inflow(hlbm_ctx* c, const double* host) {
+  const long long n = (long long)c->g.ny * c->g.nz;
+  for (long long k = 0; k < n; ++k)
+    if (!std::isfinite(host[k]) || std::fabs(host[k]) >= 0.5)
+      return set_err(c, HLBM_EINVAL, "inflow profile: |u_x| < 0.5 and finite");
+  return HLBM_OK;
+}
+
 static int set_inflow(hlbm_ctx* c, const double* host) {
   if (!host) {
     if (c->inflow) dfree(c, c->inflow);
@@ -376,9 +384,8 @@ static int set_inflow(hlbm_ctx* c, const double* host) {
     return HLBM_OK;
   }
   const long long n = (long long)c->g.ny * c->g.nz;
-  for (long long k = 0; k < n; ++k)
-    if (!std::isfinite(host[k]) || std::fabs(host[k]) >= 0.5)
-      return set_err(c, HLBM_EINVAL, "inflow profile: |u_x| < 0.5 and finite");
+  int rc = check_inflow(c, host);
+  if (rc) return rc;
   if (!c->inflow && !(c->inflow = (double*)dalloc(c, (size_t)n * 8)))
     return set_err(c, HLBM_ENOMEM, "inflow profile");
   HLBM_TRY(c, cudaMemcpyAsync(c->inflow, host, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream), "copy");
@@ -547,6 +554,12 @@ int hlbm_configure(hlbm_ctx* c, double tau, double Cs, const hlbm_options* opt) 
     int ffa[6] = {opt->ffa_x, opt->ffa_x + 1, opt->ffa_y0, opt->ffa_y1, opt->ffa_z0, opt->ffa_z1};
     if (!check_box(c, ffa) || !check_box(c, opt->diss_box) || !check_box(c, opt->design_box))
       return set_err(c, HLBM_EINVAL, "region outside the grid");
+    // everything is checked before anything changes: a rejected call leaves the
+    // context as it was
+    if (opt->inflow_ux) {
+      int rc = check_inflow(c, opt->inflow_ux);
+      if (rc) return rc;
+    }
     c->opt.u_in = opt->u_in;
     for (int k = 0; k < 3; ++k) c->opt.u_solid[k] = opt->u_solid[k];
     c->opt.tau_adj = opt->tau_adj;

@@ -344,6 +344,10 @@ def test_inflow_profile_steps_match_oracle(q, dims):
     assert rel_l2(s.field(H.FIELD_F), to_lib(f, perm)) <= 1e-13
     with pytest.raises(H.HlbmError):
         s.configure(P.tau0, 0.0, u_in=P.u_in, regions=R, inflow_profile=np.full((nz, ny), 0.7))
+    # a rejected configure changes nothing: the next step is still the uniform-inflow one
+    s.run_primal(1, 0)
+    f = ohlbm.step(f, d, P)
+    assert rel_l2(s.field(H.FIELD_F), to_lib(f, perm)) <= 1e-13
     s.close()
 
 
