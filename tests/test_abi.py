@@ -58,3 +58,31 @@ def test_header_cites_the_paper_and_states_errors():
     for key in ("Eq. adjoint_unsteady", "Eq. gradients_unsteady", "Sec. 4.2", "Sec. 4.3",
                 "HLBM_EINVAL", "HLBM_ESTATE", "HLBM_ENONFINITE"):
         assert key in src
+
+
+def test_option_and_stats_structs_match_the_header_layout(tmp_path):
+    # the ctypes mirrors of hlbm_options / hlbm_stats against the C compiler's
+    # layout of include/hlbm.h (sizes and every field offset)
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2606_31707_b300 import hlbm as H
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hlbm.h"', "int main(void) {"]
+    for cname, cls in (("hlbm_options", H.hlbm_options), ("hlbm_stats", H.hlbm_stats)):
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in (("hlbm_options", H.hlbm_options), ("hlbm_stats", H.hlbm_stats)):
+        assert got[(cname, "size")] == ctypes.sizeof(cls)
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
