@@ -207,3 +207,17 @@ def partials(f, d, P: Params, objective, regions):
         dtau_dd = tau_derivative(s, P, L["dPi_dd"], P.tau0)
         dJdd = k * (dPP_dd / tau ** 2 - 2.0 * PP * dtau_dd / tau ** 3) - (u * u).sum(axis=0) / P.tau0
     return np.where(mask[None], dJdf, 0.0), np.where(mask, dJdd, 0.0)
+
+
+def porous_drag_force(f, d, P: Params, body):
+    """x-force of the fluid on a porous body (Sec. 5.1, the F_x of
+    c_D = 2 F_x / (rho u^2 D)).  Reading: the force is the momentum the
+    collision removes from the fluid in the body's cells per step,
+    F_x = -sum_{x in body} sum_i xi_ix (C(f)_i - f_i), which for the porous
+    equilibrium is the Brinkman force density (1 - d) rho (u_x - u_s,x) / tau_eff
+    summed over the body (Sec. 2.1; the collision invariant pinned in the
+    tests).  ``body`` is a boolean mask of shape (nz, ny, nx)."""
+    from .hlbm import collide
+    fs, _ = collide(f, d, P)
+    dm = np.tensordot(P.xif[:, 0], fs - f, axes=(0, 0))     # (nz, ny, nx)
+    return -float(dm[body].sum())
