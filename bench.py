@@ -1,21 +1,31 @@
 """Benchmark of the HLBM mean-flow adjoint hot path on B300.
 
-One step = the whole hot path over one synthetic case (default: the D2Q9
-unsteady Karman case, 1100x410, Re 100, FP32 populations): porosity upload,
-primal warm-up, primal averaging window with the tracking averages of f,
-J, dJ/df and dJ/dd, then for the drag (J_FFA) and the dissipation (J_DISS)
-objectives: linearisation, mean-flow adjoint to tolerance and gradient.
+Workload (default): the LES cylinder case, D3Q19 640x320x100 (20.48 M cells),
+BGK with the Smagorinsky relaxation time (C_S = 0.1), Re 3900, u0 0.05,
+FP32 populations -- the largest single-GPU configuration.  Its whole job
+(32 000 warm-up steps, 32 000 averaged steps, adjoints to convergence) takes
+minutes, so one benchmark step is a fixed slice of Algorithm 1 on the full
+grid, continuing the flow from the previous step:
 
-Prints one JSON line (see the contract in the repository documentation):
-value = whole-job lattice updates per second (primal steps + adjoint
-iterations, x cells) in MLUPS, measured with CUDA events on the device with
-inputs resident; e2e = the same metric through the C ABI with host buffers
-and the host<->device copies inside the timed region; roofline of the
-dominant kernel against the measured HBM copy bandwidth; cpu_baseline = the
-FP64 oracle on a bounded sample of the same workload.
+  porosity upload, P plain primal steps, a tracking window of W averaged
+  steps (f, J, dJ/df, dJ/dd, tau_eff - tau0), then for the drag (J_FFA) and
+  the dissipation (J_DISS) objectives: the linearisation at the window's
+  mean, M adjoint sweeps of the fixed-point iteration from zero (tolerance 0:
+  a fixed sweep count, so the status is NOT_CONVERGED by construction and is
+  reported with the residual) and the gradient.
 
-``--impl reference`` times the oracle itself (the only reference there is),
-on the host cores, on the same workload and metric.
+value = lattice updates of the slice (N x (P + W + 2 M)) per second on the
+device, inputs resident; e2e = the same through the C ABI with host buffers
+(porosity uploaded, both gradients downloaded every step).  After the timed
+regions, untimed: the gradient of the last slice against a GMRES solve of
+the same fixed point (the accuracy the slice's sweep count gives), and the
+sweeps and time GMRES needs to reach its tolerance.  roofline: the dominant
+kernel against the measured HBM copy bandwidth.  cpu_baseline: the FP64
+oracle on a bounded sub-box of the same workload, one thread and all host
+cores (one process per core).
+
+``--impl reference`` times the oracle itself (the only reference there is)
+on the host cores, for the same workload, slice and metric.
 """
 from __future__ import annotations
 
@@ -78,38 +88,48 @@ def tau_of(wl):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="karman2d_re100")
-    ap.add_argument("--primal-steps", type=int, default=None,
-                    help="override the workload's primal step count (testing only)")
-    ap.add_argument("--avg-window", type=int, default=None)
-    ap.add_argument("--adjoint-tol", type=float, default=1e-6)
+    ap.add_argument("--workload", default="les3d_re3900")
+    ap.add_argument("--setup-steps", type=int, default=4096,
+                    help="untimed plain steps that develop the flow before the first step")
+    ap.add_argument("--slice-plain", type=int, default=64, help="plain primal steps per step (P)")
+    ap.add_argument("--slice-avg", type=int, default=64, help="averaged primal steps per step (W)")
+    ap.add_argument("--slice-sweeps", type=int, default=64,
+                    help="adjoint sweeps per objective and step (M)")
     ap.add_argument("--adjoint-mode", default="exact", choices=["exact", "fta"])
-    ap.add_argument("--adjoint-solver", default="fixed-point", choices=["fixed-point", "gmres"],
-                    help="the paper's iteration, or restarted GMRES on the same fixed point")
-    ap.add_argument("--tau-adj", type=float, default=0.0,
-                    help="adjoint relaxation time (0: tau0), the regularisation of Sec. 5.4")
-    ap.add_argument("--adjoint-max-iter", type=int, default=20000)
+    ap.add_argument("--tau-adj", type=float, default=None,
+                    help="adjoint relaxation time, the regularisation of Sec. 5.4 "
+                         "(default: 0.6, the paper's LES setting, when C_S > 0, else tau0)")
     ap.add_argument("--collision", default=None, choices=["bgk", "rr"],
                     help="BGK (Sec. 2.1) or the recursive regularised collision (Sec. 2.2); "
-                         "default: the workload's (rr for the LES cases, else bgk)")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+                         "default: the workload's (BGK)")
     ap.add_argument("--storage", default=None, choices=["fp64", "fp32", "fp16dev", "bf16dev"],
                     help="population storage (default: the workload's)")
+    ap.add_argument("--reference-tol", type=float, default=1e-4,
+                    help="GMRES tolerance of the untimed accuracy reference")
+    ap.add_argument("--reference-max-sweeps", type=int, default=20000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-procs", type=int, default=None,
+                    help="oracle processes of the all-core CPU figures (default: host cores, "
+                         "at most 32)")
     return ap.parse_args()
+
+
+def resolve(args, wl):
+    """Fill the workload-dependent defaults into args."""
+    if args.collision is None:
+        args.collision = wl.collision
+    if args.tau_adj is None:
+        args.tau_adj = 0.6 if wl.Cs > 0 else 0.0
+    return args
 
 
 def storage_code(H, wl):
     return {"fp64": H.FP64, "fp32": H.FP32, "fp16dev": H.FP16DEV, "bf16dev": H.BF16DEV}[wl.storage]
-
-
-def job_shape(wl, args):
-    steps = args.primal_steps or wl.steps
-    W = args.avg_window if args.avg_window is not None else min(wl.avg_window, steps)
-    return steps, W
 
 
 # ---------------------------------------------------------------------------
@@ -224,7 +244,15 @@ def job_mlups(lups_per_rank: int, ms_max: float, world: int) -> float:
     return world * lups_per_rank / (ms_max * 1e-3) / 1e6
 
 
+
+
+METRIC = "primal/adjoint MLUPS and % HBM roofline"
+STATUS = {0: "OK", 1: "NOT_CONVERGED", -5: "ENONFINITE", -6: "EDIVERGED"}
+
+
 def run_ours(args, rank, world):
+    import dataclasses
+
     import torch
 
     from paper_2606_31707_b300 import Solver
@@ -233,71 +261,68 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     wl = make_workload(args.workload, seed=rank)
-    if args.collision is None:
-        args.collision = wl.collision
     if args.storage:
-        import dataclasses
         wl = dataclasses.replace(wl, storage=args.storage)
-    steps, W = job_shape(wl, args)
-    n_warm = steps - W
+    resolve(args, wl)
+    Pn, Wn, M = args.slice_plain, args.slice_avg, args.slice_sweeps
     stream = torch.cuda.Stream(device=dev)
+    coll = H.COLL_RR if args.collision == "rr" else H.COLL_BGK
     s = Solver(wl.q, wl.dims, tau_of(wl), wl.Cs, storage=storage_code(H, wl), u_in=wl.u0,
-               regions=wl.regions, stream=stream, tau_adj=args.tau_adj,
-               adjoint_solver=1 if args.adjoint_solver == "gmres" else 0,
-               collision=H.COLL_RR if args.collision == "rr" else H.COLL_BGK)
+               regions=wl.regions, stream=stream, tau_adj=args.tau_adj, collision=coll)
     mode = H.ADJ_EXACT if args.adjoint_mode == "exact" else H.ADJ_FTA
     N = wl.cells
     D = 2 if wl.q == 9 else 3
-    d_dev = torch.from_numpy(np.ascontiguousarray(wl.porosity.ravel())).to(dev)
+    d_host = torch.from_numpy(np.ascontiguousarray(wl.porosity.ravel())).pin_memory()
+    d_dev = d_host.to(dev)
     up = wl.u_perturb if wl.u_perturb is not None else np.zeros((3,) + wl.porosity.shape)
     u0 = up.copy()
     u0[0] += wl.u0
-    u_host = np.ascontiguousarray(u0[:D].reshape(D, -1))
-    u_dev = torch.from_numpy(u_host).to(dev)
+    u_dev = torch.from_numpy(np.ascontiguousarray(u0[:D].reshape(D, -1))).to(dev)
+    # untimed: the flow develops from the perturbed inflow state
+    s.set_porosity(d_dev)
+    H.hlbm_init_equilibrium(s.ctx, None, u_dev)
+    del u_dev
+    if args.setup_steps > 0:
+        s.run_primal(args.setup_steps + args.setup_steps % 2, 0)
     b = wl.regions.design_box
     gvol = (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
     g_dev = torch.empty((2, gvol), dtype=torch.float64, device=dev)
-    g_host = np.empty((2, gvol))
+    g_host = torch.empty((2, gvol), dtype=torch.float64).pin_memory()
     flush = torch.empty(int(2 * L2_BYTES // 4), dtype=torch.float32, device=dev)
     objectives = (H.OBJ_DRAG_FFA, H.OBJ_DISSIPATION)
+    last = [None, None]
 
-    phase = dict(plain_ms=0.0, plain_launch=0, acc_ms=0.0, acc_launch=0, adj_ms=[0.0, 0.0],
-                 adj_launch=[0, 0], adj_iters=[0, 0])
+    def zero_phase():
+        return dict(plain_ms=0.0, plain_launch=0, acc_ms=0.0, acc_launch=0, adj_ms=[0.0, 0.0],
+                    adj_launch=[0, 0], adj_iters=[0, 0])
+
+    phase = zero_phase()
 
     def one_step(host: bool, record: bool):
-        if host:
-            s.set_porosity(wl.porosity.ravel())
-            H.hlbm_init_equilibrium(s.ctx, None, u_host)
-        else:
-            s.set_porosity(d_dev)
-            H.hlbm_init_equilibrium(s.ctx, None, u_dev)
-        lups = 0
-        if n_warm > 0:
-            s.run_primal(n_warm, 0)
-            st = s.stats()
-            if record:
-                phase["plain_ms"] += st.primal_ms
-                phase["plain_launch"] += st.primal_launches
-        s.run_primal(W, W)
+        s.set_porosity(d_host if host else d_dev)
+        s.run_primal(Pn, 0)
+        st = s.stats()
+        if record:
+            phase["plain_ms"] += st.primal_ms
+            phase["plain_launch"] += st.primal_launches
+        s.run_primal(Wn, Wn)
         st = s.stats()
         if record:
             phase["acc_ms"] += st.primal_ms
             phase["acc_launch"] += st.primal_launches
-        lups += steps * N
+        lups = (Pn + Wn) * N
         Js = []
         for k, o in enumerate(objectives):
             Js.append(s.objective(o))
-            _, it, res = s.solve_adjoint(o, mode, args.adjoint_tol, args.adjoint_max_iter)
+            status, it, res = s.solve_adjoint(o, mode, 0.0, M)
+            last[k] = (status, it, res)
             st = s.stats()
             if record:
                 phase["adj_ms"][k] += st.adjoint_ms
                 phase["adj_launch"][k] += st.adjoint_launches
                 phase["adj_iters"][k] += it
             lups += it * N
-            if host:
-                H.hlbm_gradient(s.ctx, g_host[k])
-            else:
-                H.hlbm_gradient(s.ctx, g_dev[k])
+            H.hlbm_gradient(s.ctx, g_host[k] if host else g_dev[k])
         return lups, Js
 
     def barrier():
@@ -307,10 +332,10 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
 
     def timed(host: bool):
+        nonlocal phase
         for _ in range(args.warmup):
             one_step(host, False)
-        phase.update(plain_ms=0.0, plain_launch=0, acc_ms=0.0, acc_launch=0,
-                     adj_ms=[0.0, 0.0], adj_launch=[0, 0], adj_iters=[0, 0])
+        phase = zero_phase()
         k0 = s.stats().kernels_total
         total_lups = 0
         ms = 0.0
@@ -326,18 +351,17 @@ def run_ours(args, rank, world):
             e1.record(stream)
             e1.synchronize()
             wall = (time.perf_counter() - t0) * 1e3
-            gpu = e0.elapsed_time(e1)
-            ms += wall if host else gpu
+            ms += wall if host else e0.elapsed_time(e1)
             total_lups += lups
         barrier()
-        launches = s.stats().kernels_total - k0
-        return total_lups, ms, launches, Js
+        return total_lups, ms, s.stats().kernels_total - k0, Js
 
     sampler = ClockSampler(dev.index or 0)
     sampler.start()
     lups, ms, launches, Js = timed(False)
     clocks = sampler.stop()
     phase_dev = {k: (list(v) if isinstance(v, list) else v) for k, v in phase.items()}
+    adj_state = [dict(status=STATUS.get(st, st), sweeps=it, residual=res) for st, it, res in last]
     ms = max_over_ranks(ms, world, dev)
     value = job_mlups(lups, ms, world)
     e2e = None
@@ -345,17 +369,58 @@ def run_ours(args, rank, world):
         lups_h, ms_h, _, _ = timed(True)
         ms_h = max_over_ranks(ms_h, world, dev)
         e2e = {"value": job_mlups(lups_h, ms_h, world), "unit": "MLUPS",
-               "h2d_bytes_per_step": int(N * 8 + D * N * 8),
-               "d2h_bytes_per_step": int(2 * gvol * 8 + 2 * 8)}
+               "h2d_bytes_per_step": int(d_host.numel() * 8),
+               "d2h_bytes_per_step": int(g_host.numel() * 8)}
+    acc = None
+    if not args.no_accuracy and rank == 0:
+        acc = gradient_accuracy(args, wl, s, H, Solver, mode, coll, stream, d_dev, torch, dev)
     s.close()
-    return dict(wl=wl, steps=steps, W=W, value=value, ms=ms, lups=lups, e2e=e2e,
-                launches=launches, phase=phase_dev, clocks=clocks, Js=Js)
+    return dict(wl=wl, value=value, ms=ms, lups=lups, e2e=e2e, launches=launches,
+                phase=phase_dev, clocks=clocks, Js=Js, adjoint=adj_state, accuracy=acc)
 
 
-def roofline_of(res, args, H_storage_bytes, real_bytes):
+def gradient_accuracy(args, wl, s, H, Solver, mode, coll, stream, d_dev, torch, dev):
+    """Untimed: the drag gradient of one slice (M fixed-point sweeps from zero)
+    against a GMRES solve of the same fixed point, on a second context fed the
+    same averaged state through the ABI."""
+    N, q = wl.cells, wl.q
+    status, it, res = s.solve_adjoint(H.OBJ_DRAG_FFA, mode, 0.0, args.slice_sweeps)
+    b = wl.regions.design_box
+    gvol = (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
+    G_slice = torch.empty(gvol, dtype=torch.float64, device=dev)
+    H.hlbm_gradient(s.ctx, G_slice)
+    r = Solver(q, wl.dims, tau_of(wl), wl.Cs, storage=storage_code(H, wl), u_in=wl.u0,
+               regions=wl.regions, stream=stream, tau_adj=args.tau_adj, collision=coll,
+               adjoint_solver=1, gmres_restart=30, gmres_inner=100)
+    r.set_porosity(d_dev)
+    buf = torch.empty(q * N, dtype=torch.float64, device=dev)
+    for fld, n in ((H.FIELD_FBAR, q * N), (H.FIELD_GBAR_FFA, q * N), (H.FIELD_DJDD_FFA, N),
+                   (H.FIELD_TAU_T, N)):
+        H.hlbm_get_field(s.ctx, fld, buf[:n])
+        H.hlbm_set_field(r.ctx, fld, buf[:n])
+    del buf
+    t0 = time.perf_counter()
+    rst, rit, rres = r.solve_adjoint(H.OBJ_DRAG_FFA, mode, args.reference_tol,
+                                     args.reference_max_sweeps)
+    wall = time.perf_counter() - t0
+    ref_ms = r.stats().adjoint_ms
+    G_ref = torch.empty(gvol, dtype=torch.float64, device=dev)
+    H.hlbm_gradient(r.ctx, G_ref)
+    r.close()
+    err = float(torch.linalg.vector_norm(G_slice - G_ref) / torch.linalg.vector_norm(G_ref))
+    return {"objective": "drag_ffa", "slice": {"solver": "fixed-point", "sweeps": it,
+                                               "status": STATUS.get(status, status),
+                                               "residual": res},
+            "reference": {"solver": "gmres(30), 100 sweep pairs per operator", "tol": args.reference_tol,
+                          "sweeps": rit, "status": STATUS.get(rst, rst), "residual": rres,
+                          "gpu_s": round(ref_ms * 1e-3, 2), "wall_s": round(wall, 2)},
+            "slice_gradient_rel_l2_vs_reference": err}
+
+
+def roofline_of(res, args, storage_bytes, real_bytes):
     wl = res["wl"]
     N = wl.cells
-    bm = bytes_model(wl, H_storage_bytes, real_bytes,
+    bm = bytes_model(wl, storage_bytes, real_bytes,
                      exact_rec=(wl.Cs > 0 and args.adjoint_mode == "exact"),
                      rr=args.collision == "rr")
     ph = res["phase"]
@@ -387,85 +452,181 @@ def roofline_of(res, args, H_storage_bytes, real_bytes):
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "bytes_per_lup": round(bpl, 2), "launch_us": round(per_launch_s * 1e6, 3),
             "time_share": {k: round(v / tot, 4) for k, v in share.items()},
-            "phase_mlups": {c[0]: round(N * c[2] / (c[1] * 1e-3) / 1e6, 1) for c in cand}}
+            "phase_mlups": {c[0]: round(N * c[2] / (c[1] * 1e-3) / 1e6, 1) for c in cand},
+            "phase_gbs": {c[0]: round(N * c[2] * c[3] / (c[1] * 1e-3) / 1e9, 1) for c in cand}}
 
 
 # ---------------------------------------------------------------------------
 # the oracle on a bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(wl, steps, W, adj_iters, n_plain=10, n_acc=2, n_adj=20, collision="bgk"):
-    """Time the oracle on a bounded sample of the workload and extrapolate the
-    whole job's LUP mix; returns (MLUPS, seconds spent, description)."""
-    import contextlib
+def sample_box(wl):
+    """A sub-box of the workload around the front of its body: (x0, x1, y0, y1, z0, z1)."""
+    nx, ny, nz = wl.dims
+    if wl.q == 19:
+        w, h, t = 48, 24, 16
+    else:
+        w, h, t = 96, 48, 1
+    w, h, t = min(w, nx), min(h, ny), min(t, nz)
+    x0 = max(0, min(nx - w, int(wl.regions.ffa_x) - w - 40)) if nx > w else 0
+    y0 = max(0, (ny - h) // 2)
+    return (x0, x0 + w, y0, y0 + h, 0, t)
 
-    try:
-        from threadpoolctl import threadpool_limits
-    except ImportError:  # BLAS is already pinned to one thread by the environment
-        def threadpool_limits(_n):
-            return contextlib.nullcontext()
 
+def sample_inputs(wl):
+    """The sub-box's porosity and initial velocity perturbation (small arrays)."""
+    x0, x1, y0, y1, z0, z1 = sample_box(wl)
+    d = np.ascontiguousarray(wl.porosity[z0:z1, y0:y1, x0:x1])
+    up = None if wl.u_perturb is None else np.ascontiguousarray(wl.u_perturb[:, z0:z1, y0:y1, x0:x1])
+    return d, up
+
+
+def oracle_sample(q, u0, L, Re, Cs, d, up, collision, mode, tau_adj, Pn, Wn, M,
+                  n_plain=2, n_acc=1, n_adj=2):
+    """Time the FP64 oracle, as it stands, on a sub-box of a workload (its own
+    periodic problem with inflow and outflow at the box's x faces) and return
+    (MLUPS of the slice's update mix, seconds spent).  Runs in one process."""
     from oracle import adjoint as oadj
     from oracle import hlbm as ohlbm
     from oracle import meanflow as omf
+    from workloads import Regions
 
     t_start = time.perf_counter()
-    with threadpool_limits(1):
-        P = ohlbm.Params(wl.q, wl.dims, tau0=ohlbm.tau_from_reynolds(wl.u0, wl.L, wl.Re),
-                         Cs=wl.Cs, u_in=wl.u0, collision=collision)
-        f = ohlbm.initial_state(P, wl.u_perturb)
-        d = wl.porosity
+    dims = (d.shape[2], d.shape[1], d.shape[0])
+    P = ohlbm.Params(q, dims, tau0=ohlbm.tau_from_reynolds(u0, L, Re), Cs=Cs, u_in=u0,
+                     collision=collision)
+    R = Regions(ffa_x=dims[0] - 3, ffa_y=(0, dims[1]), ffa_z=(0, dims[2]),
+                diss_box=(0, dims[0], 0, dims[1], 0, dims[2]),
+                design_box=(0, dims[0], 0, dims[1], 0, dims[2]))
+    f = ohlbm.initial_state(P, up)
+    t = time.perf_counter()
+    for _ in range(n_plain):
+        f = ohlbm.step(f, d, P)
+    t_plain = (time.perf_counter() - t) / n_plain
+    t = time.perf_counter()
+    out = omf.run_primal(f, d, P, n_acc, n_acc, R, 3)
+    t_acc = (time.perf_counter() - t) / n_acc
+    t = time.perf_counter()
+    lin = oadj.Linearisation(out["fbar"], d, P, oadj.EXACT if mode == "exact" else oadj.FTA,
+                             tau_adj or None, out["tau_t_bar"])
+    t_lin = time.perf_counter() - t
+    t = time.perf_counter()
+    lam, _, _ = oadj.solve_adjoint(lin, out[("gbar", 1)], tol=0.0, max_iter=n_adj)
+    t_adj = (time.perf_counter() - t) / n_adj
+    t = time.perf_counter()
+    oadj.gradient(lin, lam, out[("dJdd_bar", 1)])
+    t_grad = time.perf_counter() - t
+    n = dims[0] * dims[1] * dims[2]
+    slice_s = Pn * t_plain + Wn * t_acc + 2 * (t_lin + M * t_adj + t_grad)
+    return n * (Pn + Wn + 2 * M) / slice_s / 1e6, time.perf_counter() - t_start
+
+
+def _sample_worker(a):
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    return oracle_sample(*a)
+
+
+class OraclePool:
+    """One oracle process per host core (at most ``cap``), started with spawn."""
+
+    def __init__(self, procs):
+        import multiprocessing as mp
+        self.procs = procs
+        self.pool = mp.get_context("spawn").Pool(procs)
+
+    def round(self, a):
+        """Every process times one sample at once; returns (summed MLUPS, wall s)."""
         t = time.perf_counter()
-        for _ in range(n_plain):
-            f = ohlbm.step(f, d, P)
-        t_plain = (time.perf_counter() - t) / n_plain
-        t = time.perf_counter()
-        out = omf.run_primal(f, d, P, n_acc, n_acc, wl.regions, 3)
-        t_acc = (time.perf_counter() - t) / n_acc
-        t = time.perf_counter()
-        lin = oadj.Linearisation(out["fbar"], d, P, oadj.EXACT, None, out["tau_t_bar"])
-        t_lin = time.perf_counter() - t
-        g = out[("gbar", 2)]
-        t = time.perf_counter()
-        oadj.solve_adjoint(lin, g, tol=0.0, max_iter=n_adj)
-        t_adj = (time.perf_counter() - t) / n_adj
-    spent = time.perf_counter() - t_start
-    N = wl.cells
-    job_s = (steps - W) * t_plain + W * t_acc + 2 * t_lin + sum(adj_iters) * t_adj
-    lups = N * (steps + sum(adj_iters))
-    desc = (f"full {wl.dims[0]}x{wl.dims[1]}x{wl.dims[2]} grid: {n_plain} plain steps "
-            f"({t_plain:.3f} s each), {n_acc} averaging steps ({t_acc:.3f} s), one "
-            f"linearisation ({t_lin:.2f} s), {n_adj} adjoint iterations ({t_adj:.3f} s); "
-            f"extrapolated to {steps} primal steps ({W} averaging) + {sum(adj_iters)} adjoint "
-            f"iterations + 2 linearisations")
-    return lups / job_s / 1e6, spent, desc
+        res = self.pool.map(_sample_worker, [a] * self.procs)
+        return sum(v for v, _ in res), time.perf_counter() - t
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def host_procs(args):
+    return max(1, min(args.cpu_procs or (os.cpu_count() or 1), 32))
+
+
+def sample_desc(wl, args, procs):
+    b = sample_box(wl)
+    return (f"FP64 oracle (numpy/scipy, as it stands) on a {b[1]-b[0]}x{b[3]-b[2]}x{b[5]-b[4]} "
+            f"sub-box of the {wl.dims[0]}x{wl.dims[1]}x{wl.dims[2]} grid (its own problem: inflow "
+            f"and outflow at the box faces, dissipation over the whole box): 2 plain steps, 1 "
+            f"averaging step, one linearisation ({args.adjoint_mode}, tau_adj {args.tau_adj or 'tau0'}), "
+            f"2 adjoint sweeps and a gradient timed, extrapolated to the slice's mix of "
+            f"{args.slice_plain} plain + {args.slice_avg} averaging steps + 2 x ({args.slice_sweeps} "
+            f"sweeps + linearisation + gradient); {procs} process(es) at once, one thread each")
+
+
+def sample_args(wl, args):
+    d, up = sample_inputs(wl)
+    return (wl.q, wl.u0, wl.L, wl.Re, wl.Cs, d, up, args.collision, args.adjoint_mode,
+            args.tau_adj, args.slice_plain, args.slice_avg, args.slice_sweeps)
+
+
+def cpu_baseline(args, wl):
+    a = sample_args(wl, args)
+    v1, sec1 = oracle_sample(*a)
+    procs = host_procs(args)
+    pool = OraclePool(procs)
+    try:
+        vall, wall = pool.round(a)
+    finally:
+        pool.close()
+    return {"value": vall, "unit": "MLUPS", "cores": procs, "kind": "oracle",
+            "sample": sample_desc(wl, args, procs),
+            "one_thread": {"value": v1, "unit": "MLUPS", "cores": 1, "seconds": round(sec1, 1)},
+            "host_cores": os.cpu_count(), "seconds": round(sec1 + wall, 1)}
 
 
 def run_reference(args):
     wl = make_workload(args.workload)
-    steps, W = job_shape(wl, args)
-    adj = [args.adjoint_max_iter, args.adjoint_max_iter]
+    if args.storage:
+        import dataclasses
+        wl = dataclasses.replace(wl, storage=args.storage)
+    resolve(args, wl)
+    a = sample_args(wl, args)
+    procs = host_procs(args)
+    pool = OraclePool(procs)
     vals = []
-    for k in range(args.warmup + args.steps):
-        v, spent, desc = oracle_sample(wl, steps, W, adj, n_plain=4, n_acc=1, n_adj=8,
-                                       collision=args.collision or wl.collision)
-        if k >= args.warmup:
-            vals.append((v, spent))
+    try:
+        for k in range(args.warmup + args.steps):
+            v, wall = pool.round(a)
+            if k >= args.warmup:
+                vals.append((v, wall))
+    finally:
+        pool.close()
     value = statistics.median(v for v, _ in vals)
-    ms = statistics.median(sp for _, sp in vals) * 1e3
-    line = {"impl": "reference", "metric": "primal/adjoint MLUPS (whole job)", "value": value,
+    ms = statistics.median(w for _, w in vals) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "MLUPS", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "grid": list(wl.dims), "lattice": f"D{2 if wl.q == 9 else 3}Q{wl.q}",
-                       "collision": args.collision or wl.collision,
-                       "primal_steps": steps, "avg_window": W,
-                       "adjoint_iters_assumed": adj},
-            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": desc},
+            "config": config_of(wl, args),
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": procs, "kind": "oracle",
+                             "sample": sample_desc(wl, args, procs)},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def config_of(wl, args):
+    return {"workload": wl.name, "grid": list(wl.dims), "cells": wl.cells,
+            "lattice": f"D{2 if wl.q == 9 else 3}Q{wl.q}", "storage": wl.storage,
+            "collision": args.collision, "Cs": wl.Cs, "Re": wl.Re, "u0": wl.u0,
+            "tau0": tau_of(wl),
+            "slice": {"plain_steps": args.slice_plain, "averaged_steps": args.slice_avg,
+                      "adjoint_sweeps_per_objective": args.slice_sweeps,
+                      "objectives": ["drag_ffa", "dissipation"]},
+            "setup_steps_untimed": args.setup_steps,
+            "adjoint": {"mode": args.adjoint_mode, "tau_adj": args.tau_adj or None,
+                        "solver": "fixed-point", "tol": 0.0},
+            "l2": (f"flushed between timed steps (252 MB write); populations alone "
+                   f"{wl.q * wl.cells * {'fp64': 8, 'fp32': 4}.get(wl.storage, 2) / 1e9:.2f} GB"),
+            "parallelism": f"replicas{args.gpus}"}
 
 
 def main():
@@ -488,34 +649,19 @@ def main():
     sb = {"fp64": 8, "fp32": 4, "fp16dev": 2, "bf16dev": 2}[wl.storage]
     rb = 8 if wl.storage == "fp64" else 4
     roof = roofline_of(res, args, sb, rb)
-    ph = res["phase"]
-    it_per_step = [ph["adj_iters"][k] / max(1, args.steps) for k in range(2)]
-    cpu = None
-    if not args.no_cpu_baseline:
-        v, spent, desc = oracle_sample(wl, res["steps"], res["W"], it_per_step,
-                                       collision=args.collision)
-        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": round(spent, 1)}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(args, wl)
+    cfg = config_of(wl, args)
+    cfg["adjoint"]["last_step"] = {"drag_ffa": res["adjoint"][0], "dissipation": res["adjoint"][1]}
     line = {
-        "metric": "primal/adjoint MLUPS (whole job) and % HBM roofline",
+        "metric": METRIC,
         "value": res["value"], "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if rb == 4 else "f64",
         "data": "synthetic",
-        "config": {"workload": wl.name, "grid": list(wl.dims),
-                   "lattice": f"D{2 if wl.q == 9 else 3}Q{wl.q}", "storage": wl.storage,
-                   "collision": args.collision, "Re": wl.Re, "u0": wl.u0, "primal_steps": res["steps"],
-                   "avg_window": res["W"], "objectives": ["drag_ffa", "dissipation"],
-                   "adjoint": {"mode": args.adjoint_mode, "tau_adj": args.tau_adj or None,
-                               "solver": args.adjoint_solver,
-                               "tol": args.adjoint_tol,
-                               "max_iter": args.adjoint_max_iter,
-                               "iters_per_step": it_per_step},
-                   "l2": "flushed between timed steps (252 MB write)",
-                   "parallelism": f"replicas{args.gpus}"},
+        "config": cfg,
         "roofline": roof, "cpu_baseline": cpu, "e2e": res["e2e"],
         "gpu_launches": res["launches"], "clocks": res["clocks"],
-        "gradients_per_s": 2 * args.steps / (res["ms"] * 1e-3),
+        "gradient_accuracy": res["accuracy"],
         "J": {"drag_ffa": res["Js"][0], "dissipation": res["Js"][1]},
     }
     print(json.dumps(line))

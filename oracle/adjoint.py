@@ -189,16 +189,23 @@ class Linearisation:
     """Step Jacobian A = B_f S C_f and dPhi/dd at the state ``fbar``."""
 
     def __init__(self, fbar, d, P: Params, mode=EXACT, tau_adj=None, tau_t_bar=None,
-                 outlet="canonical"):
+                 outlet="canonical", assemble=True):
         """``outlet`` selects the state at which the outflow node is
         linearised: "canonical" uses the velocity of ``fbar`` at x = nx-2
         (the reading used for the mean-flow adjoint and by the CUDA path),
         "streamed" uses S(C(fbar)) there, i.e. the exact derivative of
-        ``hlbm.step`` at an arbitrary state.  At a fixed point both agree."""
+        ``hlbm.step`` at an arbitrary state.  At a fixed point both agree.
+
+        ``assemble`` = False keeps the collision Jacobian as its per-cell
+        q x q blocks and applies A = (B S) C_f factor by factor instead of
+        forming the product matrix: the same linear maps for grids where the
+        assembled q^2 N-entry matrices would not fit (the direct solve then
+        is not available)."""
         from .hlbm import collide, stream
         self.P = P
         nz, ny, nx = P.shape
         self.N = nx * ny * nz
+        self.shape = (P.q,) + P.shape
         JC, Cd = collision_jacobians(fbar, d, P, mode, tau_adj, tau_t_bar)
         if outlet == "streamed":
             fs, _ = collide(fbar, d, P)
@@ -207,6 +214,11 @@ class Linearisation:
             Bm = boundary_matrix(fbar, P)
         Sm = streaming_matrix(P)
         self.BS = (Bm @ Sm).tocsr()
+        self.BST = self.BS.T.tocsr()
+        self.assembled = assemble
+        if not assemble:
+            self.JC, self.Cd = JC, Cd
+            return
         self.A = (self.BS @ block_diag_matrix(JC, P)).tocsr()
         N = self.N
         cells = np.arange(N)
@@ -219,15 +231,27 @@ class Linearisation:
 
     def jvp(self, v):
         """A v (tangent of one step), v shaped like f."""
+        if not self.assembled:
+            cv = np.einsum("ij...,j...->i...", self.JC, v.reshape(self.shape))
+            return (self.BS @ cv.ravel()).reshape(v.shape)
         return (self.A @ v.ravel()).reshape(v.shape)
 
     def vjp(self, lam):
         """A^T lam, shaped like f."""
+        if not self.assembled:
+            m = (self.BST @ lam.ravel()).reshape(self.shape)
+            return np.einsum("ij...,i...->j...", self.JC, m).reshape(lam.shape)
         return (self.AT @ lam.ravel()).reshape(lam.shape)
 
     def mu(self, lam):
         """mu = S^T B_f^T lam: the adjoint pulled back through stream and boundary."""
-        return (self.BS.T @ lam.ravel()).reshape(lam.shape)
+        return (self.BST @ lam.ravel()).reshape(lam.shape)
+
+    def dd_vjp(self, lam):
+        """(dPhi/dd)^T lam, one value per cell, shape (nz, ny, nx)."""
+        if not self.assembled:
+            return (self.mu(lam.reshape(self.shape)) * self.Cd).sum(axis=0)
+        return (self.DT @ lam.ravel()).reshape(self.P.shape)
 
 
 def solve_adjoint(lin: Linearisation, gbar, tol=1e-10, max_iter=100000, lam0=None):
@@ -239,7 +263,7 @@ def solve_adjoint(lin: Linearisation, gbar, tol=1e-10, max_iter=100000, lam0=Non
     lam = np.zeros_like(g) if lam0 is None else lam0.ravel().copy()
     r = np.inf
     for k in range(1, max_iter + 1):
-        new = lin.AT @ lam + g
+        new = lin.vjp(lam) + g
         diff = new - lam
         r = float(np.sqrt(np.dot(diff, diff))) / (gn if gn > 0 else 1.0)
         lam = new
@@ -258,7 +282,7 @@ def solve_adjoint_direct(lin: Linearisation, gbar):
 
 def gradient(lin: Linearisation, lam, dJdd_bar):
     """dJ/dd per cell = dJ/dd_bar + (dPhi/dd)^T lambda, shape (nz, ny, nx)."""
-    return dJdd_bar + (lin.DT @ lam.ravel()).reshape(dJdd_bar.shape)
+    return dJdd_bar + lin.dd_vjp(lam).reshape(dJdd_bar.shape)
 
 
 def newton_steady(f, d, P: Params, iters=8, tol=1e-14):

@@ -26,6 +26,7 @@ class PrimalSpec:
     tol: float = 1e-8
     max_iter: int = 200000
     warm_start: bool = False    # continue from the last state instead of f^eq(1, u_in)
+    allow_unconverged: bool = False  # True: return the last iterate at max_iter instead of raising
 
 
 class HLBMObjective(torch.autograd.Function):
@@ -43,6 +44,8 @@ class HLBMObjective(torch.autograd.Function):
             H.hlbm_init_equilibrium(solver.ctx)
         H.hlbm_run_primal(solver.ctx, spec.steps, spec.avg_window)
         J = H.hlbm_objective(solver.ctx, spec.objective)
+        solver.generation += 1
+        ctx.generation = solver.generation
         ctx.solver = solver
         ctx.spec = spec
         ctx.shape = d.shape
@@ -53,8 +56,17 @@ class HLBMObjective(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gJ: torch.Tensor):
         s, spec = ctx.solver, ctx.spec
+        if s.generation != ctx.generation:
+            # the context's averaged state belongs to a later forward (or was
+            # changed through the solver): its adjoint is not this J's gradient
+            raise H.HlbmError(H.ESTATE, "the solver ran another primal after this forward; "
+                              "call backward before reusing the solver")
         st, it, res = H.hlbm_solve_adjoint(s.ctx, spec.objective, spec.mode, spec.tol, spec.max_iter)
-        ctx.adjoint_status = (st, it, res)
+        s.last_adjoint = (st, it, res)
+        if st == H.NOT_CONVERGED and not spec.allow_unconverged:
+            raise H.HlbmError(H.NOT_CONVERGED, f"adjoint not converged after {it} iterations "
+                              f"(residual {res:.3e} > tol {spec.tol:.1e}); raise max_iter or set "
+                              "allow_unconverged")
         G = torch.empty(s.design_shape, dtype=torch.float64,
                         device=ctx.device if ctx.device.type == "cuda" else "cpu")
         if G.is_cuda:

@@ -336,18 +336,17 @@ __device__ __forceinline__ void residual_io(const AdjointArgs& a, long long cell
                                             double& rp) {
   if (RES == 0) return;
   R* sn = static_cast<R*>(a.snap);
-  R acc = 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     R* p = sn + (long long)i * a.g.pitch + cell;
     if (RES == 1) {
       *p = v[i];
     } else {
-      const R dlt = v[i] - *p;
-      acc += dlt * dlt;
+      // squared update in FP64 (only the comparing sweep, once per check interval)
+      const double dlt = (double)v[i] - (double)*p;
+      rp += dlt * dlt;
     }
   }
-  if (RES == 2) rp += (double)acc;
 }
 
 template <int Q, class R, bool ODD, bool EXACT, int RES, bool RR>

@@ -377,6 +377,16 @@ static int check_inflow(hlbm_ctx* c, const double* host) {
   return HLBM_OK;
 }
 
+// u_in (the inflow and J_FFA reference velocity) and tau_adj (0: tau0, else
+// the adjoint relaxation time, which like tau must exceed 1/2)
+static bool options_valid(const hlbm_options* o) {
+  if (!std::isfinite(o->u_in) || std::fabs(o->u_in) >= 0.5) return false;
+  if (!std::isfinite(o->tau_adj) || !(o->tau_adj == 0.0 || o->tau_adj > 0.5)) return false;
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(o->u_solid[k]) || std::fabs(o->u_solid[k]) >= 0.5) return false;
+  return true;
+}
+
 static int set_inflow(hlbm_ctx* c, const double* host) {
   if (!host) {
     if (c->inflow) dfree(c, c->inflow);
@@ -425,6 +435,7 @@ int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau, doub
   if (opt) c->opt = *opt;
   else hlbm_default_options(&c->opt, dims);
   if (c->opt.storage < HLBM_FP64 || c->opt.storage > HLBM_BF16DEV) { delete c; return HLBM_EINVAL; }
+  if (!options_valid(&c->opt)) { delete c; return HLBM_EINVAL; }
   if (c->opt.accum_stride < 1) c->opt.accum_stride = 1;
   if (c->opt.check_every < 2) c->opt.check_every = 100;
   if (c->opt.check_every & 1) c->opt.check_every += 1;
@@ -554,29 +565,35 @@ int hlbm_configure(hlbm_ctx* c, double tau, double Cs, const hlbm_options* opt) 
     int ffa[6] = {opt->ffa_x, opt->ffa_x + 1, opt->ffa_y0, opt->ffa_y1, opt->ffa_z0, opt->ffa_z1};
     if (!check_box(c, ffa) || !check_box(c, opt->diss_box) || !check_box(c, opt->design_box))
       return set_err(c, HLBM_EINVAL, "region outside the grid");
-    // everything is checked before anything changes: a rejected call leaves the
-    // context as it was
+    if (!options_valid(opt))
+      return set_err(c, HLBM_EINVAL, "need |u_in|, |u_solid| < 0.5 and tau_adj = 0 or > 0.5");
+    // everything is checked, and the inflow profile's buffer allocated and
+    // filled, before any option changes: a rejected call (HLBM_EINVAL,
+    // HLBM_ENOMEM or HLBM_ECUDA from the profile) leaves the options as they were
     if (opt->inflow_ux) {
       int rc = check_inflow(c, opt->inflow_ux);
       if (rc) return rc;
     }
-    c->opt.u_in = opt->u_in;
-    for (int k = 0; k < 3; ++k) c->opt.u_solid[k] = opt->u_solid[k];
-    c->opt.tau_adj = opt->tau_adj;
-    c->opt.objectives = opt->objectives;
-    c->opt.ffa_x = opt->ffa_x;
-    c->opt.ffa_y0 = opt->ffa_y0; c->opt.ffa_y1 = opt->ffa_y1;
-    c->opt.ffa_z0 = opt->ffa_z0; c->opt.ffa_z1 = opt->ffa_z1;
-    std::memcpy(c->opt.diss_box, opt->diss_box, sizeof c->opt.diss_box);
-    std::memcpy(c->opt.design_box, opt->design_box, sizeof c->opt.design_box);
-    c->opt.accum_stride = opt->accum_stride < 1 ? 1 : opt->accum_stride;
-    c->opt.check_every = opt->check_every < 2 ? 100 : opt->check_every + (opt->check_every & 1);
-    c->opt.average_full_f = opt->average_full_f;
-    c->opt.adjoint_solver = opt->adjoint_solver;
-    c->opt.gmres_restart = opt->gmres_restart;
-    c->opt.gmres_inner = opt->gmres_inner;
     int rc = set_inflow(c, opt->inflow_ux);
     if (rc) return rc;
+    hlbm_options n = c->opt;
+    n.u_in = opt->u_in;
+    for (int k = 0; k < 3; ++k) n.u_solid[k] = opt->u_solid[k];
+    n.tau_adj = opt->tau_adj;
+    n.objectives = opt->objectives;
+    n.ffa_x = opt->ffa_x;
+    n.ffa_y0 = opt->ffa_y0; n.ffa_y1 = opt->ffa_y1;
+    n.ffa_z0 = opt->ffa_z0; n.ffa_z1 = opt->ffa_z1;
+    std::memcpy(n.diss_box, opt->diss_box, sizeof n.diss_box);
+    std::memcpy(n.design_box, opt->design_box, sizeof n.design_box);
+    n.accum_stride = opt->accum_stride < 1 ? 1 : opt->accum_stride;
+    n.check_every = opt->check_every < 2 ? 100 : opt->check_every + (opt->check_every & 1);
+    n.average_full_f = opt->average_full_f;
+    n.adjoint_solver = opt->adjoint_solver;
+    n.gmres_restart = opt->gmres_restart;
+    n.gmres_inner = opt->gmres_inner;
+    n.inflow_ux = nullptr;  // the context keeps its own device copy
+    c->opt = n;
   }
   c->tau0 = tau;
   c->Cs = Cs;

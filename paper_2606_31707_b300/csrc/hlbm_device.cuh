@@ -361,23 +361,6 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// block sum in the arithmetic type (valid in thread 0)
-template <class R, int NT>
-__device__ __forceinline__ R block_sum_r(R v, R* sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  R r = 0;
-  if (threadIdx.x == 0) {
-    const int nw = (int)(blockDim.x >> 5);
-    for (int k = 0; k < nw; ++k) r += sh[k];
-  }
-  __syncthreads();
-  return r;
-}
-
 __device__ __forceinline__ long long block_linear() {
   return (long long)blockIdx.x + (long long)gridDim.x * ((long long)blockIdx.y + (long long)gridDim.y * blockIdx.z);
 }

@@ -147,7 +147,7 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
     const PrimalArgs& a, typename Store<S>::mem* A, const Rows& rows, int x, int y, int z,
     long long cell,
     typename Store<S>::real (&g)[Q], typename Store<S>::real d,
-    typename Store<S>::real (&jp)[2]) {
+    double (&jp)[2]) {
   using R = typename Store<S>::real;
   using L = Lat<Q>;
   constexpr int D = L::D;
@@ -250,7 +250,7 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
       const R u0 = par<R>(a.u_in, a.u_in_f);
       sg0[0].store(a.gsum[0], a.gstage[0], cell, u.x * u.x - R(1.0 / 3.0));
       sg0[1].store(a.gsum[0], a.gstage[0], N + cell, u0 - R(2) * u.x);
-      jp[0] += m.x * (u0 - u.x) - R(1.0 / 3.0) * drho;
+      jp[0] += (double)(m.x * (u0 - u.x) - R(1.0 / 3.0) * drho);
     }
     // dissipation J_DISS on Omega_J (Sec. 4.3): 2 nu S:S + (1-d)/tau0 u.u,
     // S = -3 Pi / (2 tau):  J = (9 nu / 2) |Pi|^2 / tau^2 + (1-d)/tau0 |u|^2.
@@ -290,7 +290,7 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
       const Vec3<R> v{u.x - us.x, u.y - us.y, u.z - us.z};
       cf[NCD] = fac * (-R(2) * rho * dot3(v, PU)) - uu_raw / tau0;
       sdiss.store(daddr, a.gstage[1], N, cell, cf);
-      jp[1] += J;
+      jp[1] += (double)J;
     }
   }
 
@@ -367,7 +367,7 @@ __device__ __forceinline__ void primal_body(const PrimalArgs& a) {
   const int y = blockIdx.y, z = blockIdx.z;
   auto* A = static_cast<typename St::mem*>(a.f);
   const R* dp = static_cast<const R*>(a.d);
-  R jp[2] = {R(0), R(0)};
+  double jp[2] = {0.0, 0.0};  // this thread's J terms, summed in FP64
   if (x < gr.nx - 1) {
     const long long cell = cell_of(gr, x, y, z);
     const Rows rows = make_rows<Lat<Q>::D>(gr, y, z);
@@ -387,14 +387,15 @@ __device__ __forceinline__ void primal_body(const PrimalArgs& a) {
     }
   }
   if constexpr (ACC > 0) {
-    // J of this step summed over the block in the arithmetic type, then added
-    // to the block's FP64 running sum (one FP64 add per block and step)
-    __shared__ R sh[NT / 32];
+    // J of this step: each cell's term (computed in the arithmetic type) is
+    // added in FP64, summed over the block in FP64 and added to the block's
+    // FP64 running sum, so the reduction carries no FP32 rounding
+    __shared__ double sh[NT / 32];
 #pragma unroll
     for (int o = 0; o < 2; ++o) {
       if (!(a.obj_mask & (1 << o))) continue;
-      const R sm = block_sum_r<R, NT>(jp[o], sh);
-      if (threadIdx.x == 0) a.jblk[o][block_linear()] += (double)sm;
+      const double sm = block_sum<NT>(jp[o], sh);
+      if (threadIdx.x == 0) a.jblk[o][block_linear()] += sm;
     }
   }
 }

@@ -301,10 +301,42 @@ def hlbm_destroy(ctx):
 
 def hlbm_objective_noalloc(lattice: int, dims: Sequence[int], tau: float, Cs: float, u_in: float,
                            objective: int, region: Sequence[int], f, d, J, dJdf=None, dJdd=None,
-                           stream: int = 0, u_solid=(0.0, 0.0, 0.0)) -> int:
+                           stream: Optional[int] = None, u_solid=(0.0, 0.0, 0.0)) -> int:
     """Objective of a device-resident state without any allocation in the
-    library (see include/hlbm.h).  f, d, J, dJdf, dJdd are CUDA float64
-    tensors; returns the status (negative on error) without raising."""
+    library (see include/hlbm.h).  f (q*N), d (N), J (1), dJdf (q*N) and dJdd
+    (N) are contiguous float64 CUDA tensors on the current device; the C side
+    cannot check their sizes, so they are checked here and a mismatch raises
+    ValueError before anything is launched.  ``stream`` defaults to torch's
+    current stream.  Returns the status (negative on error) without raising."""
+    import torch
+
+    q = int(lattice)
+    if q not in (9, 19) or len(dims) != 3 or len(region) != 6:
+        raise ValueError("lattice must be 9 or 19, dims 3 values, region 6 values")
+    N = int(dims[0]) * int(dims[1]) * int(dims[2])
+    dev = None
+    sizes = {"f": q * N, "d": N, "J": 1, "dJdf": q * N, "dJdd": N}
+    tensors = {"f": f, "d": d, "J": J, "dJdf": dJdf, "dJdd": dJdd}
+    for name in ("f", "d", "J"):
+        if tensors[name] is None:
+            raise ValueError(f"{name} is required")
+    for name, t in tensors.items():
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if dev is None:
+            dev = torch.cuda.current_device()
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+        if t.numel() != sizes[name]:
+            raise ValueError(f"{name} needs {sizes[name]} elements, got {t.numel()}")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
     ptr = [C.c_void_p(t.data_ptr()) if t is not None else None for t in (f, d, J, dJdf, dJdd)]
     return _lib.hlbm_objective_noalloc(lattice, (C.c_int * 3)(*dims), tau, Cs, u_in,
                                        (C.c_double * 3)(*u_solid), objective,

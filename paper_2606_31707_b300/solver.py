@@ -42,6 +42,10 @@ class Solver:
         if stream is not None:
             opt.stream = stream if isinstance(stream, int) else int(stream.cuda_stream)
         self.opt = opt
+        # bumped by every call that changes the state or the averages, so that a
+        # pending autograd backward can tell its forward's state was replaced
+        self.generation = 0
+        self.last_adjoint = None
         self.ctx = H.hlbm_create(lattice, self.dims, tau, Cs, opt)
         opt.inflow_ux = None  # copied by the library
         self.xi, self.w = H.hlbm_velocity_set(lattice)
@@ -91,6 +95,7 @@ class Solver:
                 raise ValueError("inflow_profile needs ny * nz values")
             opt.inflow_ux = prof.ctypes.data
         H.hlbm_configure(self.ctx, tau, Cs, opt)
+        self.generation += 1
         opt.inflow_ux = None
         self._design(opt)
 
@@ -101,6 +106,7 @@ class Solver:
         return (nz, ny, nx)
 
     def set_porosity(self, d):
+        self.generation += 1
         H.hlbm_set_porosity(self.ctx, np.ascontiguousarray(d, dtype=np.float64).ravel()
                             if isinstance(d, np.ndarray) else d)
 
@@ -109,9 +115,11 @@ class Solver:
             u = np.ascontiguousarray(u[: self.dim], dtype=np.float64)
         if rho is not None and isinstance(rho, np.ndarray):
             rho = np.ascontiguousarray(rho, dtype=np.float64)
+        self.generation += 1
         H.hlbm_init_equilibrium(self.ctx, rho, u)
 
     def run_primal(self, steps: int, avg_window: int = 0):
+        self.generation += 1
         return H.hlbm_run_primal(self.ctx, steps, avg_window)
 
     def objective(self, obj: int) -> float:
@@ -147,6 +155,7 @@ class Solver:
         return out
 
     def set_field(self, which: int, data):
+        self.generation += 1
         H.hlbm_set_field(self.ctx, which, np.ascontiguousarray(data, dtype=np.float64)
                          if isinstance(data, np.ndarray) else data)
 
@@ -157,6 +166,7 @@ class Solver:
         H.hlbm_save(self.ctx, path)
 
     def load(self, path):
+        self.generation += 1
         H.hlbm_load(self.ctx, path)
 
     def close(self):

@@ -51,3 +51,27 @@ def oracle_pipeline(P, d, regions, f0, steps, W, objective, mode=oadj.EXACT, tau
         lam, _, _ = oadj.solve_adjoint(lin, g, tol=tol, max_iter=1_000_000)
     G = oadj.gradient(lin, lam, out[("dJdd_bar", objective)])
     return dict(out=out, lin=lin, lam=lam, G=G, mu=lin.mu(lam))
+
+
+def oracle_grf_gradients():
+    """The Gaussian-random-field design case (D2Q9 400x160, Re 40) in the
+    oracle: steady state by Newton steps with the exact step Jacobian, the
+    steady adjoint by a sparse direct solve, and the gradient and J of both
+    objectives (Eq. gradients_steady).  Returns {"newton_residual": r,
+    1: (G, J) of J_FFA, 2: (G, J) of J_DISS}.  Picklable for a spawned worker."""
+    from workloads import make_workload
+
+    wl = make_workload("grf2d_re40")
+    P = Params(9, wl.dims, tau0=ohlbm.tau_from_reynolds(wl.u0, wl.L, wl.Re), u_in=wl.u0)
+    d = wl.porosity
+    f = ohlbm.initial_state(P)
+    for _ in range(1000):
+        f = ohlbm.step(f, d, P)
+    f, res = oadj.newton_steady(f, d, P, iters=20, tol=1e-12)
+    lin = oadj.Linearisation(f, d, P, oadj.EXACT)
+    out = {"newton_residual": res}
+    for o in (oobj.FFA, oobj.DISS):
+        g, gd = oobj.partials(f, d, P, o, wl.regions)
+        lam = oadj.solve_adjoint_direct(lin, g)
+        out[o] = (oadj.gradient(lin, lam, gd), oobj.value(f, d, P, o, wl.regions))
+    return out

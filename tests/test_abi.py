@@ -51,6 +51,14 @@ def test_default_options_and_argument_checks_without_gpu():
         with pytest.raises(H.HlbmError) as e:
             H.hlbm_create(lattice, dims, tau, 0.0)
         assert e.value.status == H.EINVAL
+    # options: |u_in| < 0.5, tau_adj 0 or above 1/2, all finite
+    for field, value in (("u_in", 0.7), ("u_in", float("nan")), ("tau_adj", 0.4),
+                         ("tau_adj", -1.0), ("tau_adj", float("inf"))):
+        o = H.hlbm_default_options((10, 4, 1))
+        setattr(o, field, value)
+        with pytest.raises(H.HlbmError) as e:
+            H.hlbm_create(9, (10, 4, 1), 0.6, 0.0, o)
+        assert e.value.status == H.EINVAL, (field, value)
 
 
 def test_header_cites_the_paper_and_states_errors():
@@ -86,3 +94,20 @@ def test_option_and_stats_structs_match_the_header_layout(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls)
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_noalloc_wrapper_rejects_bad_buffers_before_any_launch():
+    # the C side cannot check buffer sizes; the binding checks dtype, device,
+    # contiguity and element counts and raises before calling it
+    import torch
+    from paper_2606_31707_b300 import hlbm as H
+    dims = (8, 4, 1)
+    f = torch.zeros(9 * 32, dtype=torch.float64)
+    d = torch.zeros(32, dtype=torch.float64)
+    J = torch.zeros(1, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA"):
+        H.hlbm_objective_noalloc(9, dims, 0.7, 0.0, 0.05, H.OBJ_DISSIPATION, (0, 8, 0, 4, 0, 1),
+                                 f, d, J)
+    with pytest.raises(ValueError, match="required"):
+        H.hlbm_objective_noalloc(9, dims, 0.7, 0.0, 0.05, H.OBJ_DISSIPATION, (0, 8, 0, 4, 0, 1),
+                                 f, None, J)

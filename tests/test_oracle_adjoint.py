@@ -271,3 +271,31 @@ def test_mea_steady_gradient_vs_central_fd():
     fd = (Jp - Jm) / (2 * h)
     an = float((G * v).sum())
     assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-6)
+
+
+@pytest.mark.parametrize("q,Cs,mode,collision", [(9, 0.0, adj.EXACT, "bgk"), (9, 0.2, adj.EXACT, "bgk"),
+                                                 (19, 0.15, adj.EXACT, "bgk"), (19, 0.15, adj.FTA, "bgk"),
+                                                 (19, 0.1, adj.EXACT, "rr")])
+def test_matrix_free_linearisation_is_the_assembled_one(q, Cs, mode, collision):
+    # the factor-by-factor form (per-cell blocks, B S sparse) applies the same
+    # maps as the assembled matrices that the central-difference pins check
+    P = Params(q, (10, 6, 4) if q == 19 else (12, 7, 1), tau0=0.58, Cs=Cs, u_in=0.05,
+               collision=collision)
+    f, d = _state(P, 31, amp=0.05)
+    f = hlbm.apply_boundary(f, P)
+    tt = np.full(P.shape, 0.021)
+    A = adj.Linearisation(f, d, P, mode, tau_adj=0.63, tau_t_bar=tt)
+    M = adj.Linearisation(f, d, P, mode, tau_adj=0.63, tau_t_bar=tt, assemble=False)
+    rng = np.random.default_rng(2)
+    v = rng.standard_normal(f.shape)
+    w = rng.standard_normal(f.shape)
+    for a, b in ((A.jvp(v), M.jvp(v)), (A.vjp(w), M.vjp(w)), (A.dd_vjp(w), M.dd_vjp(w))):
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+    g = rng.standard_normal(f.shape)
+    la, ka, ra = adj.solve_adjoint(A, g, tol=0.0, max_iter=7)
+    lm, km, rm = adj.solve_adjoint(M, g, tol=0.0, max_iter=7)
+    assert ka == km == 7 and abs(ra - rm) <= 1e-12 * ra
+    assert np.abs(la - lm).max() <= 1e-12 * np.abs(la).max()
+    gd = rng.standard_normal(d.shape)
+    Ga, Gm = adj.gradient(A, la, gd), adj.gradient(M, lm, gd)
+    assert np.abs(Ga - Gm).max() <= 1e-12 * np.abs(Ga).max()

@@ -61,9 +61,10 @@ class Workload:
     the length ``L`` (the cylinder diameter unless stated), ``Cs`` the
     Smagorinsky constant (0 = plain BGK).  ``steps``/``avg_window`` are the
     primal step count and the number of final steps that are averaged.
-    ``collision`` is the collision the case is run with by default: the
-    turbulent cases use the recursive regularised collision of the paper's
-    turbulent model, the laminar ones BGK.
+    ``collision`` is the collision the case is run with by default: BGK
+    (with the Smagorinsky relaxation time when ``Cs`` > 0) for every case;
+    the recursive regularised collision of the paper's turbulent model is the
+    alternative for the LES cases.
     """
 
     name: str
@@ -195,16 +196,19 @@ def make_workload(name: str, seed: int = 0, **over) -> Workload:
         up = velocity_perturbation(dims, 1e-3 * 0.04, seed)
         wl = Workload(name, 9, dims, 0.04, 100.0, D, 0.0, 225_000, 150_000,
                       _regions_cyl(dims, xc, D), d, up, "fp32")
-    elif name in ("les3d_re3900", "les3d_re3900_quarter"):
+    elif name in ("les3d_re3900", "les3d_re3900_quarter", "les3d_re3900_slab"):
+        # the LES case (640x320x100, D = 32); its quarter-scale copy (D = 8);
+        # and a 24-cell-deep slab of the full-resolution case (4.9 M cells, a
+        # few GB on the device: the size for kernel profiles)
         quarter = name.endswith("quarter")
         D = 8.0 if quarter else 32.0
-        dims = (160, 80, 25) if quarter else (640, 320, 100)
+        dims = (160, 80, 25) if quarter else ((640, 320, 24) if name.endswith("slab") else (640, 320, 100))
         xc, yc = 5 * D, 5 * D
         d = cylinder_porosity(dims, xc, yc, D / 2, 2.0, jitter=0.01, seed=seed)
         cu = int(D / 0.05)  # steps per convective unit D/u0
         up = velocity_perturbation(dims, 1e-3 * 0.05, seed)
         wl = Workload(name, 19, dims, 0.05, 3900.0, D, 0.1, 100 * cu, 50 * cu,
-                      _regions_cyl(dims, xc, D), d, up, "fp32", "rr")
+                      _regions_cyl(dims, xc, D), d, up, "fp32", "bgk")
     elif name == "grf2d_re40":
         # differentiation case: D2Q9 400x160, GRF in a 60x60 box at (100, 80)
         dims = (400, 160, 1)
@@ -244,6 +248,7 @@ def make_workload(name: str, seed: int = 0, **over) -> Workload:
 
 
 WORKLOADS = ("cyl2d_re20", "karman2d_re100", "karman2d_4096", "les3d_re3900", "les3d_re3900_quarter",
+             "les3d_re3900_slab",
              "grf2d_re40", "tiny2d", "tiny3d")
 
 
