@@ -23,7 +23,7 @@
  *    cell index = x + nx*(y + ny*z) ("canonical order").  x = 0 is an
  *    equilibrium inflow node (uniform u_in, or the profile inflow_ux),
  *    x = nx-1 an outflow node; y and z are periodic.  nx >= 4, ny >= 1,
- *    nz >= 1.
+ *    nz >= 1, ny and nz <= 65535, nx * ny * nz < 2^31 - 64.
  *  - Multi-component fields are component-major: component c of cell k is
  *    at [c*N + k], N = nx*ny*nz.
  *  - Every call returns a status: HLBM_OK (0), HLBM_NOT_CONVERGED (1, a
@@ -276,6 +276,50 @@ const char* hlbm_last_error(const hlbm_ctx* ctx);
 
 /* Release all device memory and the own stream.  NULL is a no-op. */
 void hlbm_destroy(hlbm_ctx* ctx);
+
+/* ---------------------------------------------------------------------
+ * Batched stepping (the serving form of the path).  Several contexts, each
+ * with its own grid, porosity, parameters and device state, advance together:
+ * every primal step (adjoint sweep) of all of them is one kernel launch over a
+ * device work list of (context, x-block, y, z) tiles, each block reading its
+ * context's arguments from a device table.  Small grids that cannot fill the
+ * GPU alone then share launches, and a launch's fixed cost is paid once per
+ * step for the whole batch.  Per context, the arithmetic, the order of every
+ * reduction and the block decomposition are those of the single-context
+ * calls, so a context's results are bitwise the same whether it is stepped
+ * alone (hlbm_run_primal / hlbm_solve_adjoint) or in any batch.
+ *
+ * A batch holds contexts created on the batch's stream with the batch's
+ * lattice, FP32 storage, BGK collision with Cs = 0, block_x = 128,
+ * accum_stride 1, the fixed-point adjoint solver, no J_MEA and averages of
+ * the moments only (average_full_f = 0), all at the same AA phase (every
+ * context that has run the same parity of steps; an even number of steps
+ * keeps it); others give HLBM_EINVAL.  The batch owns only its tables and work
+ * list (device memory it allocates as it grows); the contexts keep their
+ * state.
+ *
+ * hlbm_batch_create: lattice HLBM_D2Q9 or HLBM_D3Q19, stream (cudaStream_t,
+ *   not NULL) that the member contexts were created on.
+ * hlbm_batch_run_primal: hlbm_run_primal(ctx, steps, avg_window) for each of
+ *   ctxs[0..n), in one launch per step.  Returns HLBM_ENONFINITE if any
+ *   state became non-finite (that context's last error says so).
+ * hlbm_batch_solve_adjoint: hlbm_solve_adjoint(ctxs[k], objectives[k], mode,
+ *   tol, max_iter) for each k, in one launch per sweep over the contexts still
+ *   iterating (a context leaves the work list when it converges, diverges or
+ *   becomes non-finite; the residual is checked every check_every sweeps of
+ *   ctxs[0]).  iters_out, residual_out, status_out (n entries each, may be
+ *   NULL) receive each context's results; the return value is the worst
+ *   status (a negative one, else HLBM_NOT_CONVERGED if any, else HLBM_OK).
+ *   hlbm_gradient then reads each context's gradient.
+ * --------------------------------------------------------------------- */
+typedef struct hlbm_batch hlbm_batch;
+int hlbm_batch_create(hlbm_batch** out, int lattice, void* stream);
+int hlbm_batch_run_primal(hlbm_batch* batch, hlbm_ctx* const* ctxs, int n, long steps,
+                          long avg_window);
+int hlbm_batch_solve_adjoint(hlbm_batch* batch, hlbm_ctx* const* ctxs, int n,
+                             const int* objectives, int mode, double tol, long max_iter,
+                             long* iters_out, double* residual_out, int* status_out);
+void hlbm_batch_destroy(hlbm_batch* batch);
 
 /* ---------------------------------------------------------------------
  * Objective evaluation without allocation.  The paper has no counterpart

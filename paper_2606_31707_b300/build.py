@@ -40,8 +40,25 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps if os.path.exists(p))
 
 
+def _headers():
+    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    hs.append(os.path.join(os.path.dirname(HERE), "include", "hlbm.h"))
+    return hs
+
+
+def _obj_current(src: str, obj: str) -> bool:
+    """The object exists and is newer than its source, every header and this script."""
+    if not os.path.exists(obj):
+        return False
+    t = os.path.getmtime(obj)
+    deps = [os.path.join(CSRC, src), os.path.abspath(__file__), *_headers()]
+    return all(os.path.getmtime(p) <= t for p in deps if os.path.exists(p))
+
+
 def _compile(src: str, log: bool) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+    if _obj_current(src, obj):
+        return obj
     cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -57,6 +74,11 @@ def build(force: bool = False, log: bool = True) -> str:
     if not force and not _stale():
         return OUT
     os.makedirs(BUILD, exist_ok=True)
+    if force:
+        for src in SOURCES:
+            obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+            if os.path.exists(obj):
+                os.remove(obj)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, log), SOURCES))
     tmp = OUT + ".tmp"

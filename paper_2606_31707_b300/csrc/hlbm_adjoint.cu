@@ -349,12 +349,14 @@ __device__ __forceinline__ void residual_io(const AdjointArgs& a, long long cell
   }
 }
 
+// One block of an adjoint sweep: x-block bxi of row (y, z); blin is the
+// block's slot in the residual partial sums.
 template <int Q, class R, bool ODD, bool EXACT, int RES, bool RR>
-__device__ __forceinline__ void adjoint_body(const AdjointArgs& a) {
+__device__ __forceinline__ void adjoint_body(const AdjointArgs& a, int bxi, int y, int z,
+                                             long long blin) {
   constexpr int S = RealStore<R>::S;
   const Grid& g = a.g;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int x = bxi * blockDim.x + threadIdx.x;
   R* A = static_cast<R*>(a.lam);
   const R* dp = static_cast<const R*>(a.d);
   double rp = 0.0;
@@ -390,7 +392,7 @@ __device__ __forceinline__ void adjoint_body(const AdjointArgs& a) {
   if (RES == 2) {
     __shared__ double sh[NT / 32];
     const double s = block_sum<NT>(rp, sh);
-    if (threadIdx.x == 0) a.red[block_linear()] = s;
+    if (threadIdx.x == 0) a.red[blin] = s;
   }
 }
 
@@ -421,12 +423,43 @@ constexpr int adjoint_min_blocks() {
 
 template <int Q, class R, bool ODD, bool EXACT, int RES, bool RR>
 __global__ void __launch_bounds__(NT) k_adjoint(AdjointArgs a) {
-  adjoint_body<Q, R, ODD, EXACT, RES, RR>(a);
+  adjoint_body<Q, R, ODD, EXACT, RES, RR>(a, blockIdx.x, blockIdx.y, blockIdx.z, block_linear());
 }
 
 template <int Q, class R, bool ODD, bool EXACT, int RES, bool RR, int MB>
 __global__ void __launch_bounds__(NT, MB) k_adjoint_mb(AdjointArgs a) {
-  adjoint_body<Q, R, ODD, EXACT, RES, RR>(a);
+  adjoint_body<Q, R, ODD, EXACT, RES, RR>(a, blockIdx.x, blockIdx.y, blockIdx.z, block_linear());
+}
+
+// Batched sweep over a work list (see k_primal_batch): block b processes tile
+// tiles[b] = (context k, x-block, y, z) with the arguments tab[k].
+template <int Q, bool ODD, int RES>
+__global__ void __launch_bounds__(NT) k_adjoint_batch(const AdjointArgs* __restrict__ tab,
+                                                      const int4* __restrict__ tiles) {
+  const int4 t = tiles[blockIdx.x];
+  const AdjointArgs& a = tab[t.x];
+  const long long gx = (a.g.nx + NT - 1) / NT;
+  adjoint_body<Q, float, ODD, false, RES, false>(
+      a, t.y, t.z, t.w, t.y + gx * ((long long)t.z + (long long)a.g.ny * t.w));
+}
+
+template <int Q, bool ODD>
+static cudaError_t launch_adj_batch_q(const AdjointArgs* tab, const int4* tiles, int ntiles,
+                                      int res, cudaStream_t s) {
+  if (res == 0) k_adjoint_batch<Q, ODD, 0><<<ntiles, NT, 0, s>>>(tab, tiles);
+  else if (res == 1) k_adjoint_batch<Q, ODD, 1><<<ntiles, NT, 0, s>>>(tab, tiles);
+  else k_adjoint_batch<Q, ODD, 2><<<ntiles, NT, 0, s>>>(tab, tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_batch(const AdjointArgs* tab, const int4* tiles, int ntiles, int q,
+                                 bool odd, int res, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (q == 9) return odd ? launch_adj_batch_q<9, true>(tab, tiles, ntiles, res, s)
+                         : launch_adj_batch_q<9, false>(tab, tiles, ntiles, res, s);
+  if (q == 19) return odd ? launch_adj_batch_q<19, true>(tab, tiles, ntiles, res, s)
+                          : launch_adj_batch_q<19, false>(tab, tiles, ntiles, res, s);
+  return cudaErrorInvalidValue;
 }
 
 template <int Q, class R, bool ODD, bool EXACT, int RES, bool RR>

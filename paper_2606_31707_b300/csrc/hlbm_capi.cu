@@ -49,7 +49,6 @@ struct hlbm_ctx {
   double* jblk[2] = {nullptr, nullptr};
   float* mstage = nullptr;  // FP32 staging of the sums (FP32 / 16-bit storage only)
   float* fstage = nullptr;
-  float* tstage = nullptr;
   float* gstage[2] = {nullptr, nullptr};
   float* ddstage[2] = {nullptr, nullptr};
   long long nblk = 0;
@@ -238,12 +237,14 @@ int obj_slot(int obj) {
 
 size_t coef_bytes(const hlbm_ctx* c, int o) { return (size_t)ncoef(o, c->D) * c->g.N * 8; }
 
-// FP32 staging: the moment sums packed in float4 planes; the drag coefficients
-// in plain planes; the dissipation coefficients and dJ/dd packed together
-size_t mstage_bytes(const hlbm_ctx* c) { return (size_t)stage_planes4(c->mplanes) * c->g.N * 16; }
+// FP32 staging, one float per sum and cell, each group laid out as float4
+// planes then float planes: the moment sums and tau_eff - tau0 (compact
+// averages), or the q sums of f - w and tau_eff - tau0 (full averages); the
+// drag coefficients; the dissipation coefficients and dJ/dd
+size_t mstage_bytes(const hlbm_ctx* c) { return (size_t)(c->mplanes + 1) * c->g.N * 4; }
+size_t fstage_bytes(const hlbm_ctx* c) { return (size_t)(c->q + 1) * c->g.N * 4; }
 size_t gstage_bytes(const hlbm_ctx* c, int o) {
-  return o == 0 ? (size_t)ncoef(0, c->D) * c->g.N * 4
-                : (size_t)stage_planes4(ncoef(1, c->D) + 1) * c->g.N * 16;
+  return (size_t)(o == 0 ? ncoef(0, c->D) : ncoef(1, c->D) + 1) * c->g.N * 4;
 }
 
 int ensure_averages(hlbm_ctx* c, int mask) {
@@ -255,9 +256,10 @@ int ensure_averages(hlbm_ctx* c, int mask) {
   if (!c->tsum && !(c->tsum = (double*)dalloc(c, (size_t)N * 8))) return set_err(c, HLBM_ENOMEM, "tsum");
   const bool stage = !real_is_double(c);
   if (stage) {
-    if (!c->mstage && !(c->mstage = (float*)dalloc(c, mstage_bytes(c)))) return set_err(c, HLBM_ENOMEM, "mstage");
-    if (c->full_f && !c->fstage && !(c->fstage = (float*)dalloc(c, (size_t)c->q * N * 4))) return set_err(c, HLBM_ENOMEM, "fstage");
-    if (!c->tstage && !(c->tstage = (float*)dalloc(c, (size_t)N * 4))) return set_err(c, HLBM_ENOMEM, "tstage");
+    if (!c->full_f && !c->mstage && !(c->mstage = (float*)dalloc(c, mstage_bytes(c))))
+      return set_err(c, HLBM_ENOMEM, "mstage");
+    if (c->full_f && !c->fstage && !(c->fstage = (float*)dalloc(c, fstage_bytes(c))))
+      return set_err(c, HLBM_ENOMEM, "fstage");
   }
   for (int o = 0; o < 2; ++o) {
     if (!(mask & (1 << o))) continue;
@@ -277,8 +279,7 @@ int reset_averages(hlbm_ctx* c, int mask) {
   if (c->fsum) HLBM_TRY(c, cudaMemsetAsync(c->fsum, 0, (size_t)c->q * N * 8, c->stream), "memset");
   HLBM_TRY(c, cudaMemsetAsync(c->tsum, 0, (size_t)N * 8, c->stream), "memset");
   if (c->mstage) HLBM_TRY(c, cudaMemsetAsync(c->mstage, 0, mstage_bytes(c), c->stream), "memset");
-  if (c->fstage) HLBM_TRY(c, cudaMemsetAsync(c->fstage, 0, (size_t)c->q * N * 4, c->stream), "memset");
-  if (c->tstage) HLBM_TRY(c, cudaMemsetAsync(c->tstage, 0, (size_t)N * 4, c->stream), "memset");
+  if (c->fstage) HLBM_TRY(c, cudaMemsetAsync(c->fstage, 0, fstage_bytes(c), c->stream), "memset");
   for (int o = 0; o < 2; ++o) {
     if (!(mask & (1 << o))) continue;
     if (c->gstage[o]) HLBM_TRY(c, cudaMemsetAsync(c->gstage[o], 0, gstage_bytes(c, o), c->stream), "memset");
@@ -328,7 +329,6 @@ PrimalArgs primal_args(hlbm_ctx* c) {
   }
   a.mstage = c->mstage;
   a.fstage = c->fstage;
-  a.tstage = c->tstage;
   a.obj_mask = c->acc_mask;
   a.ffa[0] = c->opt.ffa_x;
   a.ffa[1] = c->opt.ffa_y0;
@@ -430,6 +430,8 @@ int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau, doub
   if (dims[0] < 4 || dims[1] < 1 || dims[2] < 1) return HLBM_EINVAL;
   if (lattice == 9 && dims[2] != 1) return HLBM_EINVAL;
   if (dims[1] > 65535 || dims[2] > 65535) return HLBM_EINVAL;
+  // cell indices (and the padded plane pitch) are held in 32 bits in the kernels
+  if ((long long)dims[0] * dims[1] * dims[2] + 64 > 2147483647LL) return HLBM_EINVAL;
   if (!(tau > 0.5) || !(Cs >= 0.0) || !std::isfinite(tau) || !std::isfinite(Cs)) return HLBM_EINVAL;
   hlbm_ctx* c = new hlbm_ctx();
   if (opt) c->opt = *opt;
@@ -785,6 +787,10 @@ int hlbm_run_primal(hlbm_ctx* c, long steps, long W) {
     c->nsamples = samples;
     c->generation++;
     c->have_adjoint = false;
+    // a window that averaged f itself derives the moment sums from it
+    if (c->full_f)
+      HLBM_TRY(c, CNT(c, launch_moments_of_sums)(c->fsum, c->q, c->g.N, c->msum, c->rr, c->stream),
+               "moments of the averages");
   }
   if (err & 1u) return set_err(c, HLBM_ENONFINITE, "primal state became non-finite");
   return HLBM_OK;
@@ -1098,12 +1104,21 @@ static int adjoint_gmres(hlbm_ctx* c, const AdjointArgs& a, bool dbl, bool exact
   return HLBM_OK;
 }
 
-int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter, long* iters_out,
-                       double* res_out) {
-  if (!c) return HLBM_EINVAL;
+// Everything an adjoint solve does before its sweeps: the argument checks of
+// the objective and mode, the buffers, the linearisation record at the
+// averaged state, the source g_bar and its norm, lambda = 0; ev0 is recorded
+// before the source.
+struct AdjSetup {
+  AdjointArgs a;
+  bool exact;
+  long long nb_adj;
+  double gnorm;
+};
+
+static int adjoint_setup(hlbm_ctx* c, int obj, int mode, AdjSetup* out) {
   const int o = obj_slot(obj);
-  if (o < 0 || (mode != HLBM_ADJ_EXACT && mode != HLBM_ADJ_FTA) || !(tol >= 0) || max_iter < 2)
-    return set_err(c, HLBM_EINVAL, "bad objective, mode, tol or max_iter");
+  if (o < 0 || (mode != HLBM_ADJ_EXACT && mode != HLBM_ADJ_FTA))
+    return set_err(c, HLBM_EINVAL, "bad objective or mode");
   if (c->nsamples < 1 || !(c->acc_mask & obj)) return set_err(c, HLBM_ESTATE, "run the primal with this objective averaged first");
   const bool dbl = real_is_double(c);
   const size_t lam_bytes = (size_t)c->q * c->g.pitch * real_bytes(c);
@@ -1164,7 +1179,50 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
   double gnorm = std::sqrt(c->scal_host[0]);
   if (!(gnorm > 0.0)) gnorm = 1.0;
 
-  AdjointArgs a = adjoint_args(c, mode, sb);
+  out->a = adjoint_args(c, mode, sb);
+  out->exact = exact;
+  out->nb_adj = nb_adj;
+  out->gnorm = gnorm;
+  return HLBM_OK;
+}
+
+// Everything an adjoint solve does after its sweeps (ev1, statistics, the
+// state flags, the message of the status); returns the status.
+static int adjoint_finish(hlbm_ctx* c, int obj, int mode, int status, long k, long launches,
+                          bool exact) {
+  HLBM_TRY(c, cudaEventRecord(c->ev1, c->stream), "event");
+  HLBM_TRY(c, cudaEventSynchronize(c->ev1), "sync");
+  float ms = 0;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  c->stats.adjoint_ms = ms;
+  c->stats.adjoint_iters = k;
+  c->stats.adjoint_launches = launches;
+  {
+    const int recp = exact ? c->q : c->D + 2;
+    const double rb = (double)real_bytes(c);
+    c->stats.adjoint_bytes_per_lup = (2.0 * c->q + recp + 1) * rb;
+  }
+  c->last_obj = obj;
+  c->last_mode = mode;
+  c->have_adjoint = (status == HLBM_OK || status == HLBM_NOT_CONVERGED);
+  if (status == HLBM_ENONFINITE) return set_err(c, status, "adjoint became non-finite");
+  if (status == HLBM_EDIVERGED) return set_err(c, status, "adjoint residual diverged");
+  if (status == HLBM_NOT_CONVERGED) set_err(c, status, "adjoint reached max_iter");
+  return status;
+}
+
+int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter, long* iters_out,
+                       double* res_out) {
+  if (!c) return HLBM_EINVAL;
+  if (!(tol >= 0) || max_iter < 2) return set_err(c, HLBM_EINVAL, "bad tol or max_iter");
+  AdjSetup su{};
+  int rc = adjoint_setup(c, obj, mode, &su);
+  if (rc) return rc;
+  const bool dbl = real_is_double(c);
+  const bool exact = su.exact;
+  const long long nb_adj = su.nb_adj;
+  const double gnorm = su.gnorm;
+  AdjointArgs a = su.a;
   const long m = c->opt.check_every;
   long k = 0, launches = 0;
   double r = INFINITY, rmin = INFINITY;
@@ -1234,27 +1292,9 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
     if (r > 1e6 * rmin && rmin > 0) { status = HLBM_EDIVERGED; break; }
     if (c->opt.adjoint_solver == 1) break;
   }
-  HLBM_TRY(c, cudaEventRecord(c->ev1, c->stream), "event");
-  HLBM_TRY(c, cudaEventSynchronize(c->ev1), "sync");
-  float ms = 0;
-  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-  c->stats.adjoint_ms = ms;
-  c->stats.adjoint_iters = k;
-  c->stats.adjoint_launches = launches;
-  {
-    const int recp = exact ? c->q : c->D + 2;
-    const double rb = (double)real_bytes(c);
-    c->stats.adjoint_bytes_per_lup = (2.0 * c->q + recp + 1) * rb;
-  }
   if (iters_out) *iters_out = k;
   if (res_out) *res_out = r;
-  c->last_obj = obj;
-  c->last_mode = mode;
-  c->have_adjoint = (status == HLBM_OK || status == HLBM_NOT_CONVERGED);
-  if (status == HLBM_ENONFINITE) return set_err(c, status, "adjoint became non-finite");
-  if (status == HLBM_EDIVERGED) return set_err(c, status, "adjoint residual diverged");
-  if (status == HLBM_NOT_CONVERGED) set_err(c, status, "adjoint reached max_iter");
-  return status;
+  return adjoint_finish(c, obj, mode, status, k, launches, exact);
 }
 
 static int run_gradient(hlbm_ctx* c, const int box[6], double* out, double* mu_out) {
@@ -1573,7 +1613,6 @@ void hlbm_destroy(hlbm_ctx* c) {
   dfree(c, c->fsum);
   dfree(c, c->mstage);
   dfree(c, c->fstage);
-  dfree(c, c->tstage);
   for (int o = 0; o < 2; ++o) {
     dfree(c, c->gstage[o]);
     dfree(c, c->ddstage[o]);
@@ -1609,6 +1648,344 @@ void hlbm_destroy(hlbm_ctx* c) {
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
+}
+
+// ---------------------------------------------------------------------------
+// Batched stepping (the serving form)
+// ---------------------------------------------------------------------------
+
+struct hlbm_batch {
+  int q = 9;
+  cudaStream_t stream = nullptr;
+  PrimalArgs* ptab = nullptr;   // device: one PrimalArgs per context
+  AdjointArgs* atab = nullptr;  // device: one AdjointArgs per context
+  int tab_n = 0;
+  int4* tiles = nullptr;        // device work list: (context, x-block, y, z)
+  long long tiles_n = 0;
+  int4* tiles_host = nullptr;   // pinned copy
+  long long tiles_host_n = 0;
+  // captured graph of kGraphSteps batched primal steps, per (averaging pattern, phase)
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int ntiles = 0;
+  } pg[2][2];
+  bool graphs_ok = true;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double last_ms = 0.0;
+};
+
+namespace {
+
+void batch_drop_graphs(hlbm_batch* b) {
+  // the captured graphs hold the pointers of the tables and the work list
+  for (auto& row : b->pg)
+    for (auto& g : row)
+      if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+}
+
+int batch_tables(hlbm_batch* b, int n, long long ntiles) {
+  if (b->tab_n < n) {
+    batch_drop_graphs(b);
+    if (b->ptab) cudaFree(b->ptab);
+    if (b->atab) cudaFree(b->atab);
+    b->ptab = nullptr;
+    b->atab = nullptr;
+    b->tab_n = 0;
+    if (cudaMalloc(&b->ptab, sizeof(PrimalArgs) * n) != cudaSuccess ||
+        cudaMalloc(&b->atab, sizeof(AdjointArgs) * n) != cudaSuccess) {
+      cudaGetLastError();
+      return HLBM_ENOMEM;
+    }
+    b->tab_n = n;
+  }
+  if (b->tiles_n < ntiles) {
+    batch_drop_graphs(b);
+    if (b->tiles) cudaFree(b->tiles);
+    b->tiles = nullptr;
+    b->tiles_n = 0;
+    if (cudaMalloc(&b->tiles, sizeof(int4) * ntiles) != cudaSuccess) {
+      cudaGetLastError();
+      return HLBM_ENOMEM;
+    }
+    b->tiles_n = ntiles;
+  }
+  if (b->tiles_host_n < ntiles) {
+    if (b->tiles_host) cudaFreeHost(b->tiles_host);
+    b->tiles_host = nullptr;
+    b->tiles_host_n = 0;
+    if (cudaMallocHost(&b->tiles_host, sizeof(int4) * ntiles) != cudaSuccess) {
+      cudaGetLastError();
+      return HLBM_ENOMEM;
+    }
+    b->tiles_host_n = ntiles;
+  }
+  return HLBM_OK;
+}
+
+// the work list of contexts ctxs[idx[0..m)]: every NT-wide block of each
+long long batch_tiles(hlbm_batch* b, hlbm_ctx* const* ctxs, const int* idx, int m) {
+  long long t = 0;
+  for (int j = 0; j < m; ++j) {
+    const hlbm_ctx* c = ctxs[idx[j]];
+    const int gx = (c->g.nx + NT - 1) / NT;
+    for (int z = 0; z < c->g.nz; ++z)
+      for (int y = 0; y < c->g.ny; ++y)
+        for (int xb = 0; xb < gx; ++xb) b->tiles_host[t++] = make_int4(j, xb, y, z);
+  }
+  return t;
+}
+
+long long batch_count(hlbm_ctx* const* ctxs, int n) {
+  long long t = 0;
+  for (int k = 0; k < n; ++k) t += (long long)((ctxs[k]->g.nx + NT - 1) / NT) * ctxs[k]->g.ny * ctxs[k]->g.nz;
+  return t;
+}
+
+// what a batch may hold: contexts of its lattice and stream, FP32 storage, BGK
+// without the Smagorinsky model, NT-wide blocks, the same AA phase
+int batch_check(hlbm_batch* b, hlbm_ctx* const* ctxs, int n) {
+  if (!b || !ctxs || n < 1) return HLBM_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    hlbm_ctx* c = ctxs[k];
+    if (!c) return HLBM_EINVAL;
+    if (c->q != b->q || c->stream != b->stream || c->storage != HLBM_FP32 || c->rr ||
+        c->Cs != 0.0 || c->full_f || c->g.bx != NT || c->phase != ctxs[0]->phase ||
+        c->opt.accum_stride != 1 || c->opt.adjoint_solver != 0)
+      return set_err(c, HLBM_EINVAL,
+                     "batched stepping needs contexts of the batch's lattice and stream, FP32 "
+                     "storage, BGK with Cs = 0, compact averages, block_x 128, stride 1, the "
+                     "fixed-point adjoint and the same AA phase");
+  }
+  return HLBM_OK;
+}
+
+}  // namespace
+
+int hlbm_batch_create(hlbm_batch** out, int lattice, void* stream) {
+  if (!out) return HLBM_EINVAL;
+  *out = nullptr;
+  if ((lattice != 9 && lattice != 19) || !stream) return HLBM_EINVAL;
+  hlbm_batch* b = new hlbm_batch();
+  b->q = lattice;
+  b->stream = static_cast<cudaStream_t>(stream);
+  if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    hlbm_batch_destroy(b);
+    return HLBM_ECUDA;
+  }
+  *out = b;
+  return HLBM_OK;
+}
+
+int hlbm_batch_run_primal(hlbm_batch* b, hlbm_ctx* const* ctxs, int n, long steps, long W) {
+  int rc = batch_check(b, ctxs, n);
+  if (rc) return rc;
+  if (steps < 0 || W < 0 || W > steps) return set_err(ctxs[0], HLBM_EINVAL, "need 0 <= avg_window <= steps");
+  const long long ntiles = batch_count(ctxs, n);
+  if (ntiles > 0x7fffffffLL) return set_err(ctxs[0], HLBM_EINVAL, "batch too large");
+  rc = batch_tables(b, n, ntiles);
+  if (rc) return set_err(ctxs[0], rc, "batch tables");
+  for (int k = 0; k < n; ++k) {
+    if (W > 0) {
+      rc = reset_averages(ctxs[k], ctxs[k]->opt.objectives & 7);
+      if (rc) return rc;
+    }
+  }
+  std::vector<PrimalArgs> tab(n);
+  std::vector<int> idx(n);
+  for (int k = 0; k < n; ++k) {
+    tab[k] = primal_args(ctxs[k]);
+    idx[k] = k;
+  }
+  batch_tiles(b, ctxs, idx.data(), n);
+  cudaStream_t s = b->stream;
+  hlbm_ctx* c0 = ctxs[0];
+  HLBM_TRY(c0, cudaMemcpyAsync(b->ptab, tab.data(), sizeof(PrimalArgs) * n, cudaMemcpyHostToDevice, s), "table");
+  HLBM_TRY(c0, cudaMemcpyAsync(b->tiles, b->tiles_host, sizeof(int4) * ntiles, cudaMemcpyHostToDevice, s), "tiles");
+  HLBM_TRY(c0, cudaEventRecord(b->ev0, s), "event");
+  int phase = c0->phase;
+  long launches = 0;
+  const long first = steps - W;
+  // a stretch of `count` steps of one pattern (plain, or averaging samples 0..count-1)
+  auto stretch = [&](int acc_base, long count) -> int {
+    long done = 0;
+    auto& g = b->pg[acc_base ? 1 : 0][phase];
+    if (b->graphs_ok && count >= kGraphSteps) {
+      if (g.exec && g.ntiles != (int)ntiles) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+      }
+      if (!g.exec) {
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        int ph = phase;
+        for (long k = 0; ok && k < kGraphSteps; ++k) {
+          ok = launch_primal_batch(b->ptab, b->tiles, (int)ntiles, b->q, ph == 1,
+                                   step_variant(acc_base, k, kGraphSteps + 1), s) == cudaSuccess;
+          ph ^= 1;
+        }
+        if (cudaStreamEndCapture(s, &graph) != cudaSuccess) ok = false;
+        if (ok && cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+          ok = false;
+          g.exec = nullptr;
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+          cudaGetLastError();
+          b->graphs_ok = false;
+        } else {
+          g.ntiles = (int)ntiles;
+        }
+      }
+      if (g.exec) {
+        for (; done + kGraphSteps <= count; done += kGraphSteps) {
+          if (cudaGraphLaunch(g.exec, s) != cudaSuccess) return HLBM_ECUDA;
+          launches += kGraphSteps;
+        }
+      }
+    }
+    for (; done < count; ++done) {
+      if (launch_primal_batch(b->ptab, b->tiles, (int)ntiles, b->q, phase == 1,
+                              step_variant(acc_base, done, count), s) != cudaSuccess)
+        return HLBM_ECUDA;
+      phase ^= 1;
+      ++launches;
+    }
+    return HLBM_OK;
+  };
+  rc = stretch(0, first);
+  if (rc == HLBM_OK && W > 0) rc = stretch(ACC_ON, W);
+  if (rc) {
+    cudaGetLastError();
+    return set_err(c0, HLBM_ECUDA, "batched primal launch");
+  }
+  HLBM_TRY(c0, cudaEventRecord(b->ev1, s), "event");
+  HLBM_TRY(c0, cudaEventSynchronize(b->ev1), "sync");
+  float ms = 0;
+  cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+  b->last_ms = ms;
+  int status = HLBM_OK;
+  for (int k = 0; k < n; ++k) {
+    hlbm_ctx* c = ctxs[k];
+    c->phase = phase;
+    c->stats.primal_ms = ms;
+    c->stats.primal_launches = launches;
+    c->stats.primal_steps += steps;
+    c->stats.kernels_total += launches;
+    c->steps_done += steps;
+    if (W > 0) {
+      c->nsamples = W;
+      c->generation++;
+      c->have_adjoint = false;
+    }
+    unsigned err = 0;
+    rc = read_err(c, &err);
+    if (rc) return rc;
+    if (err & 1u) status = set_err(c, HLBM_ENONFINITE, "primal state became non-finite");
+  }
+  return status;
+}
+
+int hlbm_batch_solve_adjoint(hlbm_batch* b, hlbm_ctx* const* ctxs, int n, const int* objectives,
+                             int mode, double tol, long max_iter, long* iters_out,
+                             double* residual_out, int* status_out) {
+  int rc = batch_check(b, ctxs, n);
+  if (rc) return rc;
+  if (!objectives || !(tol >= 0) || max_iter < 2) return set_err(ctxs[0], HLBM_EINVAL, "bad tol, max_iter or objectives");
+  const long long ntiles_all = batch_count(ctxs, n);
+  if (ntiles_all > 0x7fffffffLL) return set_err(ctxs[0], HLBM_EINVAL, "batch too large");
+  rc = batch_tables(b, n, ntiles_all);
+  if (rc) return set_err(ctxs[0], rc, "batch tables");
+  std::vector<AdjSetup> su(n);
+  for (int k = 0; k < n; ++k) {
+    hlbm_ctx* c = ctxs[k];
+    if (c->nsamples < 1 || !(c->acc_mask & objectives[k]) || objectives[k] == HLBM_OBJ_DRAG_MEA)
+      return set_err(c, HLBM_ESTATE, "run the primal with this objective averaged first (J_FFA or J_DISS)");
+    rc = adjoint_setup(c, objectives[k], mode, &su[k]);
+    if (rc) return rc;
+    if (su[k].exact) return set_err(c, HLBM_EINVAL, "batched sweeps use the compact record");
+  }
+  std::vector<AdjointArgs> tab(n);
+  for (int k = 0; k < n; ++k) tab[k] = su[k].a;
+  cudaStream_t s = b->stream;
+  hlbm_ctx* c0 = ctxs[0];
+  HLBM_TRY(c0, cudaMemcpyAsync(b->atab, tab.data(), sizeof(AdjointArgs) * n, cudaMemcpyHostToDevice, s), "table");
+  std::vector<int> active(n), status(n, HLBM_NOT_CONVERGED);
+  std::vector<long> iters(n, 0);
+  std::vector<double> r(n, INFINITY), rmin(n, INFINITY);
+  for (int k = 0; k < n; ++k) active[k] = k;
+  const long m = c0->opt.check_every;
+  long k_done = 0, launches = 0;
+  while (!active.empty() && k_done < max_iter) {
+    // the work list of the contexts still iterating (table entries keep their index)
+    long long t = 0;
+    for (int k : active) {
+      const hlbm_ctx* c = ctxs[k];
+      const int gx = (c->g.nx + NT - 1) / NT;
+      for (int z = 0; z < c->g.nz; ++z)
+        for (int y = 0; y < c->g.ny; ++y)
+          for (int xb = 0; xb < gx; ++xb) b->tiles_host[t++] = make_int4(k, xb, y, z);
+    }
+    HLBM_TRY(c0, cudaMemcpyAsync(b->tiles, b->tiles_host, sizeof(int4) * t, cudaMemcpyHostToDevice, s), "tiles");
+    long chunk = max_iter - k_done < m ? max_iter - k_done : m;
+    if (chunk & 1) chunk += 1;
+    if (chunk < 2) chunk = 2;
+    for (long j = 0; j < chunk; ++j) {
+      const int res = j == chunk - 2 ? 1 : (j == chunk - 1 ? 2 : 0);
+      if (launch_adjoint_batch(b->atab, b->tiles, (int)t, b->q, (j & 1) != 0, res, s) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c0, HLBM_ECUDA, "batched adjoint launch");
+      }
+    }
+    launches += chunk;
+    k_done += chunk;
+    for (int k : active) {
+      hlbm_ctx* c = ctxs[k];
+      HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, su[k].nb_adj, c->scal_dev, s), "reduce");
+      HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, s), "copy");
+    }
+    HLBM_TRY(c0, cudaStreamSynchronize(s), "sync");
+    std::vector<int> still;
+    for (int k : active) {
+      iters[k] = k_done;
+      const double rk = std::sqrt(ctxs[k]->scal_host[0]) / su[k].gnorm;
+      r[k] = rk;
+      if (!std::isfinite(rk)) { status[k] = HLBM_ENONFINITE; continue; }
+      if (rk < rmin[k]) rmin[k] = rk;
+      if (rk <= tol) { status[k] = HLBM_OK; continue; }
+      if (rk > 1e6 * rmin[k] && rmin[k] > 0) { status[k] = HLBM_EDIVERGED; continue; }
+      still.push_back(k);
+    }
+    active.swap(still);
+  }
+  int worst = HLBM_OK;
+  for (int k = 0; k < n; ++k) {
+    hlbm_ctx* c = ctxs[k];
+    c->stats.kernels_total += iters[k];
+    const int st = adjoint_finish(c, objectives[k], mode, status[k], iters[k], iters[k], su[k].exact);
+    if (iters_out) iters_out[k] = iters[k];
+    if (residual_out) residual_out[k] = r[k];
+    if (status_out) status_out[k] = st;
+    if (st < 0 && worst >= 0) worst = st;
+    else if (st == HLBM_NOT_CONVERGED && worst == HLBM_OK) worst = st;
+  }
+  (void)launches;
+  return worst;
+}
+
+void hlbm_batch_destroy(hlbm_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->ptab) cudaFree(b->ptab);
+  if (b->atab) cudaFree(b->atab);
+  if (b->tiles) cudaFree(b->tiles);
+  if (b->tiles_host) cudaFreeHost(b->tiles_host);
+  for (auto& row : b->pg)
+    for (auto& g : row)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  delete b;
 }
 
 }  // extern "C"

@@ -135,9 +135,11 @@ __device__ __forceinline__ long long cell_of(const Grid& g, int x, int y, int z)
 
 // Row bases (y + ny z) * nx of the 3 x 3 neighbouring rows of (y, z), with the
 // periodic wrap resolved once per cell; the cell index of (x + dx, y + dy,
-// z + dz) is row[dy + 1][dz + 1] + x + dx.
+// z + dz) is row[dy + 1][dz + 1] + x + dx.  32-bit: grids have fewer than
+// 2^31 cells (hlbm_create checks), which keeps the nine bases in nine
+// registers instead of eighteen.
 struct Rows {
-  long long r[3][3];
+  int r[3][3];
 };
 
 template <int D>
@@ -148,7 +150,7 @@ __device__ __forceinline__ Rows make_rows(const Grid& g, int y, int z) {
   const int yy[3] = {ym, y, yp};
   if (D == 2) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) R.r[a][1] = (long long)yy[a] * g.nx;
+    for (int a = 0; a < 3; ++a) R.r[a][1] = yy[a] * g.nx;
   } else {
     const int zm = z == 0 ? g.nz - 1 : z - 1;
     const int zp = z == g.nz - 1 ? 0 : z + 1;
@@ -157,7 +159,7 @@ __device__ __forceinline__ Rows make_rows(const Grid& g, int y, int z) {
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b)
-        R.r[a][b] = ((long long)yy[a] + (long long)g.ny * zz[b]) * g.nx;
+        R.r[a][b] = (yy[a] + g.ny * zz[b]) * g.nx;
   }
   return R;
 }
@@ -360,6 +362,80 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   __syncthreads();
   return r;
 }
+
+// ----------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async): the data in flight holds no
+// registers; a thread that reads back only its own slots needs no barrier
+// after cp.async.wait_all.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// ----------------------------------------------------------------------------
+// Double-float sums for the FP32 kernels.  B300's FP64 pipe runs at a small
+// fraction of its FP32 rate, so the FP32 kernels add their per-cell objective
+// terms as an unevaluated pair hi + lo of floats with Knuth's error-free
+// TwoSum (s + e == a + b exactly in round-to-nearest), which carries about
+// twice the float precision, and convert to FP64 once per warp.
+// ----------------------------------------------------------------------------
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// x += v (double-float)
+__device__ __forceinline__ void jadd(F2& x, float v) {
+  float s, e;
+  two_sum(x.hi, v, s, e);
+  x.hi = s;
+  x.lo += e;
+}
+__device__ __forceinline__ void jadd(double& x, double v) { x += v; }
+
+// block sum of per-thread double-float values, in FP64 across warps (valid in thread 0)
+template <int NT>
+__device__ __forceinline__ double block_sum(F2 v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    const float l = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    float s, e;
+    two_sum(v.hi, h, s, e);
+    v.hi = s;
+    v.lo = v.lo + l + e;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = (double)v.hi + (double)v.lo;
+  __syncthreads();
+  double r = 0;
+  if (threadIdx.x == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    for (int k = 0; k < nw; ++k) r += sh[k];
+  }
+  __syncthreads();
+  return r;
+}
+
+// the objective accumulator of an arithmetic type: FP64 itself, or a double-float pair
+template <class R> struct JAcc { using T = F2; };
+template <> struct JAcc<double> { using T = double; };
 
 __device__ __forceinline__ long long block_linear() {
   return (long long)blockIdx.x + (long long)gridDim.x * ((long long)blockIdx.y + (long long)gridDim.y * blockIdx.z);

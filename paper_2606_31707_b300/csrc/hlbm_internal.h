@@ -26,7 +26,8 @@ struct PrimalArgs {
   // averaging (only read when the ACC variant runs)
   double* msum;       // (1 + D) x N running sums of rho - 1 and rho u (moments of f);
                       // RR adds D(D+1)/2 planes of sum xi xi (f - w): xx, yy[, zz], xy[, xz, yz]
-  double* fsum;       // q x N running sum of f - w (only with the full-f variant)
+  double* fsum;       // q x N running sum of f - w (only with the full-f variant, which
+                      // then leaves msum alone)
   double* tsum;       // N running sum of tau_eff - tau0 (LES only)
   double* gsum[2];    // ncoef(obj) x N running sums of the coefficients of dJ/df
                       // in the basis of coef_basis() (FFA, DISS); may be null
@@ -35,15 +36,17 @@ struct PrimalArgs {
   // FP32 kernels add each sample to a float staging copy of every sum and fold
   // the staged value into the FP64 sum every kStage samples (flush variant),
   // so that the per-step path issues no FP64 instruction; FP64 kernels add to
-  // the sums directly and leave these null
-  // The density/momentum(/second-moment) sums and the dissipation terms (its
-  // coefficients, then dJ/dd) are staged packed: float4 planes of
-  // stage_planes4(count) x N, sum k in component k % 4 of plane k / 4.
+  // the sums directly and leave these null.
+  // A group of G staged sums is laid out as G / 4 float4 planes (sum k in
+  // component k % 4 of plane k / 4) followed by G % 4 float planes, N cells
+  // each.  Groups: the moment sums then tau_eff - tau0 (mstage, compact
+  // averages) or the q sums of f - w then tau_eff - tau0 (fstage, full
+  // averages: the moment sums are derived from them after the window); the
+  // dissipation coefficients then dJ/dd (gstage[1]).
   float* mstage;
   float* fstage;
-  float* tstage;
-  float* gstage[2];   // [0]: FFA coefficients, plain planes; [1]: dissipation, packed
-  float* ddstage[2];  // unused by the packed dissipation group
+  float* gstage[2];   // [0]: FFA coefficients, plain planes; [1]: dissipation group
+  float* ddstage[2];  // unused by the dissipation group
   int obj_mask;
   int ffa[5];         // x, y0, y1, z0, z1 of Gamma_J
   int db[6];          // Omega_J box
@@ -71,9 +74,6 @@ __host__ __device__ inline double coef_basis(int obj_slot, int D, int k, int x, 
   return 2.0 * (k == 0 ? x * y : (k == 1 ? x * z : y * z));
 }
 
-// float4 planes holding `count` packed FP32 staging values per cell
-__host__ __device__ constexpr int stage_planes4(int count) { return (count + 3) / 4; }
-
 // averaging variant bits of the primal kernel
 enum { ACC_ON = 1, ACC_FULL = 2, ACC_FLUSH = 4 };
 // 64 measured fastest of 16 / 32 / 64 (averaging step: Karman 16.4 / 16.1 / 16.0 us,
@@ -88,6 +88,11 @@ constexpr int kStage = HLBM_KSTAGE;  // samples staged in FP32 before folding in
 // optional ACC_FLUSH (fold the FP32 staging into the FP64 sums)
 cudaError_t launch_primal(const PrimalArgs& a, int q, int storage, bool odd, bool les, int acc,
                           bool rr, cudaStream_t s);
+// one step of several contexts in one launch (the serving form): tab holds each
+// context's arguments on the device, tiles the (context, x-block, y, z) of every
+// NT-wide block; FP32 storage, BGK without LES, acc 0, ACC_ON or ACC_ON | ACC_FLUSH
+cudaError_t launch_primal_batch(const PrimalArgs* tab, const int4* tiles, int ntiles, int q,
+                                bool odd, int acc, cudaStream_t s);
 // out[k] (k < q, per cell) = scale * sum_c coef[c] b_c(xi_k): expand coefficient sums
 cudaError_t launch_expand_coef(const double* coef, int obj_slot, int q, long long N, double scale,
                                double* out, cudaStream_t s);
@@ -97,6 +102,9 @@ cudaError_t launch_project_coef(const double* g, const double* Pmat, int obj_slo
 // fsum = f - w and msum = (rho - 1, rho u) of the q x N field f (a set f_bar)
 cudaError_t launch_set_fbar(const double* f, int q, long long N, double* fsum, double* msum,
                             bool rr, cudaStream_t s);
+// msum = the moments (rho - 1, rho u[, xi xi (f - w) with rr]) of the q x N sums fsum
+cudaError_t launch_moments_of_sums(const double* fsum, int q, long long N, double* msum, bool rr,
+                                   cudaStream_t s);
 // out = fsum * scale + w (readout of f_bar)
 cudaError_t launch_fbar_out(const double* fsum, int q, long long N, double scale, double* out,
                             cudaStream_t s);
@@ -172,6 +180,10 @@ struct AdjointArgs {
 cudaError_t launch_adjoint(const AdjointArgs& a, int q, bool dbl, bool odd, bool exact, int res,
                            bool rr, cudaStream_t s);
 int adjoint_blocks(const Grid& g);
+// one sweep of several contexts in one launch (see launch_primal_batch): FP32,
+// compact linearisation record (BGK / frozen turbulence), res as launch_adjoint
+cudaError_t launch_adjoint_batch(const AdjointArgs* tab, const int4* tiles, int ntiles, int q,
+                                 bool odd, int res, cudaStream_t s);
 
 // momentum-exchange drag: J(f_bar) per-block partials and surface-node counts
 cudaError_t launch_mea_eval(const double* fsum, double inv_n, const void* d, const Grid& g, int q,

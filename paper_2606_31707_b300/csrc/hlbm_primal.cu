@@ -24,21 +24,6 @@ __device__ __forceinline__ void equilibrium_dev(R (&g)[Q], R drho, const Vec3<R>
   for (int i = 0; i < Q; ++i) g[i] = geq_i<Q>(i, drho, rho, u, uu);
 }
 
-// Add one sample v to a running FP64 sum.  FP64 kernels add directly; FP32
-// kernels add to the float staging value and, in the flush variant, move the
-// staged total into the FP64 sum and clear the staging value.
-template <class R, int ACC>
-__device__ __forceinline__ void acc_add(double* sum, float* stage, long long k, R v) {
-  if constexpr (sizeof(R) == 8) {
-    sum[k] += (double)v;
-  } else if constexpr ((ACC & ACC_FLUSH) == 0) {
-    stage[k] += v;
-  } else {
-    sum[k] += (double)(stage[k] + v);
-    stage[k] = 0.0f;
-  }
-}
-
 // The same update split in two: the old values are loaded right after the
 // populations (so that all loads of a cell are in flight together, before any
 // store), the new values are written at the end.
@@ -67,21 +52,60 @@ struct AccSlot {
 };
 
 // A group of G running sums of one cell updated together.  FP64 kernels add to
-// the FP64 sums directly (one AccSlot each).  FP32 kernels keep the staged
-// values packed in float4 planes (one 16-byte load and store per four sums
-// instead of four 4-byte ones) and, in the flush variant, fold them into the
-// FP64 sums.  addr(k) gives the FP64 sum of component k at this cell.
+// the FP64 sums directly.  FP32 kernels keep the staged values of the group in
+// G / 4 float4 planes followed by G % 4 float planes (no unused lanes: one
+// 16-byte access per four sums, one 4-byte access per remaining sum) and, in
+// the flush variant, fold them into the FP64 sums.  addr(k) gives the FP64 sum
+// of component k at this cell.
 __device__ __forceinline__ float& comp4(float4& v, int c) {
   return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
+
+// Shared-memory slots of one thread's staged sums: float4 slot j of the thread
+// at s4[j * NT + tid], float slot j at sr[j * NT + tid].
+struct Slots {
+  float4* s4;
+  float* sr;
+};
 
 template <class R, int ACC, int G>
 struct SumGroup {
   static constexpr bool PACKED = sizeof(R) == 4;
   static constexpr bool FLUSH = (ACC & ACC_FLUSH) != 0;
-  static constexpr int C4 = stage_planes4(G);
-  float4 t[PACKED ? C4 : 1];
+  static constexpr int C4 = G / 4, CR = G % 4;
+  float4 t[PACKED && C4 > 0 ? C4 : 1];
+  float r[PACKED && CR > 0 ? CR : 1];
   double s[(!PACKED || FLUSH) ? G : 1];
+  __device__ __forceinline__ float& staged(int k) {
+    return k < 4 * C4 ? comp4(t[k / 4], k % 4) : r[k - 4 * C4];
+  }
+  // FP32: start copying this cell's staged values into the thread's shared slots
+  __device__ __forceinline__ static void prefetch(const float* stage, long long N, long long cell,
+                                                  const Slots& sl) {
+    const float4* st = reinterpret_cast<const float4*>(stage);
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < C4; ++j) cp_async16(sl.s4 + j * NT + tid, st + (long long)j * N + cell);
+    const float* sr = stage + 4LL * C4 * N;
+#pragma unroll
+    for (int j = 0; j < CR; ++j) cp_async4(sl.sr + j * NT + tid, sr + (long long)j * N + cell);
+  }
+  // FP32: the prefetched values (after cp_async_wait_all)
+  __device__ __forceinline__ void take(const Slots& sl) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < C4; ++j) t[j] = sl.s4[j * NT + tid];
+#pragma unroll
+    for (int j = 0; j < CR; ++j) r[j] = sl.sr[j * NT + tid];
+  }
+  // the FP64 sums read by this variant (FP64 kernels, and the fold of FP32 ones)
+  template <class Addr>
+  __device__ __forceinline__ void load_sums(const Addr& addr) {
+    if constexpr (!PACKED || FLUSH) {
+#pragma unroll
+      for (int k = 0; k < G; ++k) s[k] = *addr(k);
+    }
+  }
   template <class Addr>
   __device__ __forceinline__ void load(const Addr& addr, const float* stage, long long N,
                                        long long cell) {
@@ -89,11 +113,11 @@ struct SumGroup {
       const float4* st = reinterpret_cast<const float4*>(stage);
 #pragma unroll
       for (int j = 0; j < C4; ++j) t[j] = st[(long long)j * N + cell];
-    }
-    if constexpr (!PACKED || FLUSH) {
+      const float* sr = stage + 4LL * C4 * N;
 #pragma unroll
-      for (int k = 0; k < G; ++k) s[k] = *addr(k);
+      for (int j = 0; j < CR; ++j) r[j] = sr[(long long)j * N + cell];
     }
+    load_sums(addr);
   }
   template <class Addr>
   __device__ __forceinline__ void store(const Addr& addr, float* stage, long long N,
@@ -104,7 +128,7 @@ struct SumGroup {
     } else {
 #pragma unroll
       for (int k = 0; k < G; ++k) {
-        float& c = comp4(t[k / 4], k % 4);
+        float& c = staged(k);
         if constexpr (FLUSH) {
           *addr(k) = s[k] + (double)(c + v[k]);
           c = 0.0f;
@@ -115,8 +139,26 @@ struct SumGroup {
       float4* st = reinterpret_cast<float4*>(stage);
 #pragma unroll
       for (int j = 0; j < C4; ++j) st[(long long)j * N + cell] = t[j];
+      float* sr = stage + 4LL * C4 * N;
+#pragma unroll
+      for (int j = 0; j < CR; ++j) sr[(long long)j * N + cell] = r[j];
     }
   }
+};
+
+// group sizes of the averaging variant ACC (see cell_update)
+template <int Q, bool LES, int ACC, bool RR>
+struct AccGroups {
+  static constexpr int D = Lat<Q>::D;
+  static constexpr bool FULL = (ACC & ACC_FULL) != 0;
+  static constexpr int NM = 1 + D + (RR ? D * (D + 1) / 2 : 0);  // moment sums
+  static constexpr int NTT = LES ? 1 : 0;                        // tau_eff - tau0
+  static constexpr int NCD = 1 + D + D * (D + 1) / 2;             // dissipation coefficients
+  static constexpr int GM = FULL ? 1 : NM + NTT;
+  static constexpr int GF = FULL ? Q + NTT : 1;
+  static constexpr int GA = FULL ? GF : GM;                       // the state group in use
+  static constexpr int GD = NCD + 1;                              // dissipation group
+  static constexpr int S4 = GA / 4 + GD / 4, SR = GA % 4 + GD % 4;  // shared slots per thread
 };
 
 // Collide the canonical state of one cell (as deviations g = f - w), store it
@@ -142,12 +184,15 @@ struct SumGroup {
 // third-order coefficient a1^(3) = u~ (x) Pi (symmetrised) contracted with
 // the third Hermite polynomial (the xxx and xyz entries vanish on D2Q9 and
 // D3Q19).
-template <int Q, int S, bool ODD, bool LES, int ACC, bool RR>
+//
+// PF: the staged (FP32) values of this cell's sums were prefetched into the
+// thread's shared-memory slots sla (state group) and sld (dissipation group).
+template <int Q, int S, bool ODD, bool LES, int ACC, bool RR, bool PF>
 __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
     const PrimalArgs& a, typename Store<S>::mem* A, const Rows& rows, int x, int y, int z,
     long long cell,
     typename Store<S>::real (&g)[Q], typename Store<S>::real d,
-    double (&jp)[2]) {
+    typename JAcc<typename Store<S>::real>::T (&jp)[2], const Slots& sla, const Slots& sld) {
   using R = typename Store<S>::real;
   using L = Lat<Q>;
   constexpr int D = L::D;
@@ -194,31 +239,63 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
     const long long N = gr.N;
     const bool ffa_here = (a.obj_mask & 1) && x == a.ffa[0] && y >= a.ffa[1] && y < a.ffa[2] &&
                           z >= a.ffa[3] && z < a.ffa[4];
-    constexpr int NCD = 1 + D + D * (D + 1) / 2;  // dissipation coefficients
+    using AG = AccGroups<Q, LES, ACC, RR>;
+    constexpr int NCD = AG::NCD;  // dissipation coefficients
+    constexpr bool FULL = AG::FULL;
+    // The averaged state is kept either as its moments (compact: rho - 1,
+    // rho u[, xi xi (f - w)], which is all the BGK / frozen-turbulence / RR
+    // linearisation reads) or, when f_bar itself is needed, as all q sums of
+    // f - w (the moments are then derived from them once per window).  The
+    // turbulent relaxation time rides in the same group.
+    constexpr int NM = AG::NM;  // moment sums
+    constexpr int GM = AG::GM;
+    constexpr int GF = AG::GF;
     // old values of every sum this cell updates, loaded together
-    constexpr int NM = 1 + D + (RR ? D * (D + 1) / 2 : 0);  // moment sums
-    const auto maddr = [&](int k) { return a.msum + (long long)k * N + cell; };
+    const auto maddr = [&](int k) {
+      return k < NM ? a.msum + (long long)k * N + cell : a.tsum + cell;
+    };
+    const auto faddr = [&](int k) {
+      return k < Q ? a.fsum + (long long)k * N + cell : a.tsum + cell;
+    };
     double* const g1 = a.gsum[1];
     double* const dd1 = a.ddsum[1];
     const auto daddr = [&](int k) { return k < NCD ? g1 + (long long)k * N + cell : dd1 + cell; };
-    SumGroup<R, ACC, NM> sm;
+    SumGroup<R, ACC, GM> sm;
+    SumGroup<R, ACC, GF> sf;
     SumGroup<R, ACC, NCD + 1> sdiss;
-    AccSlot<R, ACC> sg0[2], st;
-    AccSlot<R, ACC> sf[(ACC & ACC_FULL) != 0 ? Q : 1];
-    sm.load(maddr, a.mstage, N, cell);
-    if constexpr ((ACC & ACC_FULL) != 0) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) sf[i].load(a.fsum, a.fstage, (long long)i * N + cell);
+    AccSlot<R, ACC> sg0[2];
+    if constexpr (PF) {
+      // the staged values are on their way to shared memory; a fold reads the FP64 sums
+      if constexpr (FULL) sf.load_sums(faddr);
+      else sm.load_sums(maddr);
+      if (diss_here) sdiss.load_sums(daddr);
+    } else {
+      if constexpr (FULL) sf.load(faddr, a.fstage, N, cell);
+      else sm.load(maddr, a.mstage, N, cell);
+      if (diss_here) sdiss.load(daddr, a.gstage[1], N, cell);
     }
-    if (LES) st.load(a.tsum, a.tstage, cell);
     if (ffa_here) {
       sg0[0].load(a.gsum[0], a.gstage[0], cell);
       sg0[1].load(a.gsum[0], a.gstage[0], N + cell);
     }
-    if (diss_here) sdiss.load(daddr, a.gstage[1], N, cell);
 
-    {
-      R mv[NM];
+    // tau_eff - tau0 = kles |Pi| / tau_eff (the quadratic tau (tau - tau0) =
+    // kles |Pi|), free of the cancellation of the difference in FP32
+    const R tturb = LES ? kles * nP / tau : R(0);
+    if constexpr (PF) {
+      cp_async_wait_all();
+      if constexpr (FULL) sf.take(sla);
+      else sm.take(sla);
+      if (diss_here) sdiss.take(sld);
+    }
+    if constexpr (FULL) {
+      R fv[GF];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) fv[i] = g[i];
+      if constexpr (LES) fv[GF - 1] = tturb;
+      sf.store(faddr, a.fstage, N, cell, fv);
+    } else {
+      R mv[GM];
       mv[0] = drho;
       mv[1] = m.x;
       mv[2] = m.y;
@@ -237,20 +314,16 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
           mv[9] = M2.yz;
         }
       }
+      if constexpr (LES) mv[GM - 1] = tturb;
       sm.store(maddr, a.mstage, N, cell, mv);
     }
-    if constexpr ((ACC & ACC_FULL) != 0) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) sf[i].store(a.fsum, a.fstage, (long long)i * N + cell, g[i]);
-    }
-    if (LES) st.store(a.tsum, a.tstage, cell, tau - tau0);
     // far-field drag J_FFA on Gamma_J (Sec. 4.2): rho u_x (u0 - u_x) + c_s^2 (1 - rho);
     // dJ/df_j = (u_x^2 - c_s^2) + (u0 - 2 u_x) xi_jx
     if (ffa_here) {
       const R u0 = par<R>(a.u_in, a.u_in_f);
       sg0[0].store(a.gsum[0], a.gstage[0], cell, u.x * u.x - R(1.0 / 3.0));
       sg0[1].store(a.gsum[0], a.gstage[0], N + cell, u0 - R(2) * u.x);
-      jp[0] += (double)(m.x * (u0 - u.x) - R(1.0 / 3.0) * drho);
+      jadd(jp[0], m.x * (u0 - u.x) - R(1.0 / 3.0) * drho);
     }
     // dissipation J_DISS on Omega_J (Sec. 4.3): 2 nu S:S + (1-d)/tau0 u.u,
     // S = -3 Pi / (2 tau):  J = (9 nu / 2) |Pi|^2 / tau^2 + (1-d)/tau0 |u|^2.
@@ -290,7 +363,7 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
       const Vec3<R> v{u.x - us.x, u.y - us.y, u.z - us.z};
       cf[NCD] = fac * (-R(2) * rho * dot3(v, PU)) - uu_raw / tau0;
       sdiss.store(daddr, a.gstage[1], N, cell, cf);
-      jp[1] += (double)J;
+      jadd(jp[1], J);
     }
   }
 
@@ -358,18 +431,37 @@ constexpr int primal_min_blocks() {
   return 0;
 }
 
+// One block of a primal step: x-block bxi of row (y, z); blin is the block's
+// slot in the per-block objective sums.
 template <int Q, int S, bool ODD, bool LES, int ACC, bool RR>
-__device__ __forceinline__ void primal_body(const PrimalArgs& a) {
+__device__ __forceinline__ void primal_body(const PrimalArgs& a, int bxi, int y, int z,
+                                            long long blin) {
   using St = Store<S>;
   using R = typename St::real;
   const Grid& gr = a.g;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int x = bxi * blockDim.x + threadIdx.x;
   auto* A = static_cast<typename St::mem*>(a.f);
   const R* dp = static_cast<const R*>(a.d);
-  double jp[2] = {0.0, 0.0};  // this thread's J terms, summed in FP64
+  typename JAcc<R>::T jp[2] = {};  // this thread's J terms (FP64, or double-float)
+  // FP32 averaging variants copy the staged values of the cell's sums into
+  // shared memory before the populations are read (cp.async: no registers
+  // held while they are in flight; they are needed only at the end)
+  constexpr bool PF = ACC > 0 && sizeof(R) == 4;
+  using AG = AccGroups<Q, LES, ACC, RR>;
+  __shared__ float4 pf4[PF && AG::S4 > 0 ? AG::S4 * NT : 1];
+  __shared__ float pfr[PF && AG::SR > 0 ? AG::SR * NT : 1];
+  const Slots sla{pf4, pfr};
+  const Slots sld{pf4 + (AG::GA / 4) * NT, pfr + (AG::GA % 4) * NT};
   if (x < gr.nx - 1) {
     const long long cell = cell_of(gr, x, y, z);
+    if constexpr (PF) {
+      const long long N = gr.N;
+      if constexpr (AG::FULL) SumGroup<R, ACC, AG::GF>::prefetch(a.fstage, N, cell, sla);
+      else SumGroup<R, ACC, AG::GM>::prefetch(a.mstage, N, cell, sla);
+      const bool diss_here = (a.obj_mask & 2) && x >= a.db[0] && x < a.db[1] && y >= a.db[2] &&
+                             y < a.db[3] && z >= a.db[4] && z < a.db[5];
+      if (diss_here) SumGroup<R, ACC, AG::GD>::prefetch(a.gstage[1], N, cell, sld);
+    }
     const Rows rows = make_rows<Lat<Q>::D>(gr, y, z);
     R g[Q];
     if (x == 0) {
@@ -378,36 +470,82 @@ __device__ __forceinline__ void primal_body(const PrimalArgs& a) {
     } else {
       aa_load<Q, S, ODD, +1>(A, gr, rows, x, cell, g);
     }
-    const Vec3<R> u = cell_update<Q, S, ODD, LES, ACC, RR>(a, A, rows, x, y, z, cell, g, dp[cell], jp);
+    const Vec3<R> u =
+        cell_update<Q, S, ODD, LES, ACC, RR, PF>(a, A, rows, x, y, z, cell, g, dp[cell], jp, sla, sld);
     if (x == gr.nx - 2) {
       // outflow node: f^eq(1, u(nx-2)), then relaxed and streamed like any cell
+      // (its sums read directly)
       R go[Q];
       equilibrium_dev<Q, R>(go, R(0), u);
-      cell_update<Q, S, ODD, LES, ACC, RR>(a, A, rows, x + 1, y, z, cell + 1, go, dp[cell + 1], jp);
+      cell_update<Q, S, ODD, LES, ACC, RR, false>(a, A, rows, x + 1, y, z, cell + 1, go,
+                                                   dp[cell + 1], jp, sla, sld);
     }
   }
   if constexpr (ACC > 0) {
     // J of this step: each cell's term (computed in the arithmetic type) is
-    // added in FP64, summed over the block in FP64 and added to the block's
-    // FP64 running sum, so the reduction carries no FP32 rounding
+    // summed over the warp in FP64 (FP64 kernels) or as a double-float pair
+    // (FP32 kernels), over the block's warps in FP64, and added to the block's
+    // FP64 running sum: the reduction carries no FP32 rounding
     __shared__ double sh[NT / 32];
 #pragma unroll
     for (int o = 0; o < 2; ++o) {
       if (!(a.obj_mask & (1 << o))) continue;
       const double sm = block_sum<NT>(jp[o], sh);
-      if (threadIdx.x == 0) a.jblk[o][block_linear()] += sm;
+      if (threadIdx.x == 0) a.jblk[o][blin] += sm;
     }
   }
 }
 
 template <int Q, int S, bool ODD, bool LES, int ACC, bool RR>
 __global__ void __launch_bounds__(NT) k_primal(PrimalArgs a) {
-  primal_body<Q, S, ODD, LES, ACC, RR>(a);
+  primal_body<Q, S, ODD, LES, ACC, RR>(a, blockIdx.x, blockIdx.y, blockIdx.z, block_linear());
 }
 
 template <int Q, int S, bool ODD, bool LES, int ACC, bool RR, int MB>
 __global__ void __launch_bounds__(NT, MB) k_primal_mb(PrimalArgs a) {
-  primal_body<Q, S, ODD, LES, ACC, RR>(a);
+  primal_body<Q, S, ODD, LES, ACC, RR>(a, blockIdx.x, blockIdx.y, blockIdx.z, block_linear());
+}
+
+// Batched step over a work list: block b processes tile tiles[b] = (context k,
+// x-block, y, z) of context k, whose arguments are tab[k].  Every context has
+// NT-wide blocks, so a tile is exactly one of the context's own blocks and its
+// objective slot is the one the single-context kernel would use.
+template <int Q, int S, bool ODD, bool LES, int ACC, bool RR>
+__global__ void __launch_bounds__(NT) k_primal_batch(const PrimalArgs* __restrict__ tab,
+                                                     const int4* __restrict__ tiles) {
+  const int4 t = tiles[blockIdx.x];
+  const PrimalArgs& a = tab[t.x];
+  const long long gx = (a.g.nx + NT - 1) / NT;
+  primal_body<Q, S, ODD, LES, ACC, RR>(a, t.y, t.z, t.w,
+                                       t.y + gx * ((long long)t.z + (long long)a.g.ny * t.w));
+}
+
+// Batched steps are built for the serving form: FP32 populations, BGK without
+// the Smagorinsky model, compact averages (ACC 0, ON, ON | FLUSH)
+template <int Q, bool ODD>
+static cudaError_t launch_batch_q(const PrimalArgs* tab, const int4* tiles, int ntiles, int acc,
+                                  cudaStream_t s) {
+  switch (acc) {
+    case 0: k_primal_batch<Q, ST_F32, ODD, false, 0, false><<<ntiles, NT, 0, s>>>(tab, tiles); break;
+    case ACC_ON:
+      k_primal_batch<Q, ST_F32, ODD, false, ACC_ON, false><<<ntiles, NT, 0, s>>>(tab, tiles);
+      break;
+    case ACC_ON | ACC_FLUSH:
+      k_primal_batch<Q, ST_F32, ODD, false, ACC_ON | ACC_FLUSH, false><<<ntiles, NT, 0, s>>>(tab, tiles);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_primal_batch(const PrimalArgs* tab, const int4* tiles, int ntiles, int q,
+                                bool odd, int acc, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (q == 9) return odd ? launch_batch_q<9, true>(tab, tiles, ntiles, acc, s)
+                         : launch_batch_q<9, false>(tab, tiles, ntiles, acc, s);
+  if (q == 19) return odd ? launch_batch_q<19, true>(tab, tiles, ntiles, acc, s)
+                          : launch_batch_q<19, false>(tab, tiles, ntiles, acc, s);
+  return cudaErrorInvalidValue;
 }
 
 template <int Q, int S, bool ODD, bool LES, int ACC, bool RR>
@@ -709,15 +847,21 @@ __global__ void k_project_coef(const double* gin, ProjMat P, int obj_slot, long 
   }
 }
 
-template <int Q>
+// FROM_SUMS = false: fsum = f - w and msum = its moments (a set f_bar);
+// FROM_SUMS = true: msum = the moments of the sums fsum (f is fsum itself)
+template <int Q, bool FROM_SUMS>
 __global__ void k_set_fbar(const double* f, long long N, double* fsum, double* msum, bool rr) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
        c += (long long)gridDim.x * blockDim.x) {
     double gv[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      gv[i] = f[(long long)i * N + c] - Lat<Q>::w(i);
-      fsum[(long long)i * N + c] = gv[i];
+      if constexpr (FROM_SUMS) {
+        gv[i] = f[(long long)i * N + c];
+      } else {
+        gv[i] = f[(long long)i * N + c] - Lat<Q>::w(i);
+        fsum[(long long)i * N + c] = gv[i];
+      }
     }
     double dr, r;
     Vec3<double> m, u;
@@ -776,8 +920,16 @@ cudaError_t launch_project_coef(const double* g, const double* Pmat, int obj_slo
 
 cudaError_t launch_set_fbar(const double* f, int q, long long N, double* fsum, double* msum,
                             bool rr, cudaStream_t s) {
-  if (q == 9) k_set_fbar<9><<<util_blocks(N), 256, 0, s>>>(f, N, fsum, msum, rr);
-  else if (q == 19) k_set_fbar<19><<<util_blocks(N), 256, 0, s>>>(f, N, fsum, msum, rr);
+  if (q == 9) k_set_fbar<9, false><<<util_blocks(N), 256, 0, s>>>(f, N, fsum, msum, rr);
+  else if (q == 19) k_set_fbar<19, false><<<util_blocks(N), 256, 0, s>>>(f, N, fsum, msum, rr);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments_of_sums(const double* fsum, int q, long long N, double* msum, bool rr,
+                                   cudaStream_t s) {
+  if (q == 9) k_set_fbar<9, true><<<util_blocks(N), 256, 0, s>>>(fsum, N, nullptr, msum, rr);
+  else if (q == 19) k_set_fbar<19, true><<<util_blocks(N), 256, 0, s>>>(fsum, N, nullptr, msum, rr);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -61,7 +61,7 @@ __device__ __forceinline__ void tangent_cell(const TangentArgs& a, typename Stor
                                              typename Store<S>::real (&gd)[Q],
                                              typename Store<S>::real d,
                                              typename Store<S>::real dl,
-                                             double& jp,
+                                             typename JAcc<typename Store<S>::real>::T& jp,
                                              Vec3<typename Store<S>::real>& u_out,
                                              Vec3<typename Store<S>::real>& ud_out) {
   using R = typename Store<S>::real;
@@ -116,7 +116,7 @@ __device__ __forceinline__ void tangent_cell(const TangentArgs& a, typename Stor
       z < a.ffa[4]) {
     // J = (rho u_x)(u0 - u_x) - c_s^2 (rho - 1): dJ/df_j = (u_x^2 - c_s^2) + (u0 - 2 u_x) xi_jx
     const R u0 = par<R>(a.u_in, a.u_in_f);
-    jp += (double)((u.x * u.x - R(1.0 / 3.0)) * rhod + (u0 - R(2) * u.x) * md.x);
+    jadd(jp, (u.x * u.x - R(1.0 / 3.0)) * rhod + (u0 - R(2) * u.x) * md.x);
   }
   if (diss_here) {
     // J = (9 nu / 2) |Pi|^2 / tau^2 + (1-d)/tau0 |u|^2 with Pi, tau and u along gd and delta
@@ -124,7 +124,7 @@ __device__ __forceinline__ void tangent_cell(const TangentArgs& a, typename Stor
     const R uu_raw = dot3(u, u);
     R jd = R(4.5) * nu * (R(2) * PPd / (tau * tau) - R(2) * nP * nP * taud / (tau * tau * tau));
     jd += one_d / tau0 * R(2) * dot3(u, ud) - dl / tau0 * uu_raw;
-    jp += (double)jd;
+    jadd(jp, jd);
   }
 
   // collide and store
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(NT) k_tangent(TangentArgs a) {
   auto* T = static_cast<typename Store<SD>::mem*>(a.fd);
   const R* dp = static_cast<const R*>(a.d);
   const R* dlp = static_cast<const R*>(a.delta);
-  double jp = 0.0;  // this thread's dJ/dd . delta terms, summed in FP64
+  typename JAcc<R>::T jp{};  // this thread's dJ/dd . delta terms (FP64, or double-float)
   if (x < gr.nx - 1) {
     const long long cell = cell_of(gr, x, y, z);
     const Rows rows = make_rows<Lat<Q>::D>(gr, y, z);

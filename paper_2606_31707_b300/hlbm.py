@@ -113,6 +113,12 @@ def _load():
         "hlbm_load": (C.c_int, [P, C.c_char_p]),
         "hlbm_last_error": (C.c_char_p, [P]),
         "hlbm_destroy": (None, [P]),
+        "hlbm_batch_create": (C.c_int, [C.POINTER(P), C.c_int, P]),
+        "hlbm_batch_run_primal": (C.c_int, [P, C.POINTER(P), C.c_int, C.c_long, C.c_long]),
+        "hlbm_batch_solve_adjoint": (C.c_int, [P, C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.c_int,
+                                               C.c_double, C.c_long, C.POINTER(C.c_long),
+                                               C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+        "hlbm_batch_destroy": (None, [P]),
         "hlbm_objective_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_double, C.c_double,
                                              C.c_double, C.POINTER(C.c_double), C.c_int,
                                              C.POINTER(C.c_int), P, P, P, P, P, P]),
@@ -129,7 +135,9 @@ EXPORTED = ("hlbm_velocity_set", "hlbm_default_options", "hlbm_create", "hlbm_co
             "hlbm_set_porosity",
             "hlbm_init_equilibrium", "hlbm_run_primal", "hlbm_run_tangent", "hlbm_objective", "hlbm_solve_adjoint",
             "hlbm_gradient", "hlbm_get_field", "hlbm_set_field", "hlbm_get_stats", "hlbm_save",
-            "hlbm_load", "hlbm_last_error", "hlbm_destroy", "hlbm_objective_noalloc")
+            "hlbm_load", "hlbm_last_error", "hlbm_destroy", "hlbm_batch_create",
+            "hlbm_batch_run_primal", "hlbm_batch_solve_adjoint", "hlbm_batch_destroy",
+            "hlbm_objective_noalloc")
 
 
 def lib():
@@ -297,6 +305,55 @@ def hlbm_last_error(ctx) -> str:
 
 def hlbm_destroy(ctx):
     _lib.hlbm_destroy(ctx)
+
+
+def _ctx_array(ctxs):
+    arr = (C.c_void_p * len(ctxs))()
+    for k, c in enumerate(ctxs):
+        arr[k] = c.value if isinstance(c, C.c_void_p) else c
+    return arr
+
+
+def _check_many(ctxs, status):
+    if status < 0:
+        for c in ctxs:
+            m = _lib.hlbm_last_error(c)
+            if m:
+                raise HlbmError(status, m.decode())
+        raise HlbmError(status, "batched call failed")
+    return status
+
+
+def hlbm_batch_create(lattice: int, stream: int):
+    """A batch for contexts of this lattice created on ``stream`` (a cudaStream_t)."""
+    b = C.c_void_p()
+    r = _lib.hlbm_batch_create(C.byref(b), lattice, C.c_void_p(stream))
+    if r < 0:
+        raise HlbmError(r, "hlbm_batch_create failed")
+    return b
+
+
+def hlbm_batch_run_primal(batch, ctxs, steps: int, avg_window: int):
+    return _check_many(ctxs, _lib.hlbm_batch_run_primal(batch, _ctx_array(ctxs), len(ctxs),
+                                                        steps, avg_window))
+
+
+def hlbm_batch_solve_adjoint(batch, ctxs, objectives, mode: int, tol: float, max_iter: int):
+    """Returns (worst status, [(status, iterations, residual)] per context)."""
+    n = len(ctxs)
+    objs = (C.c_int * n)(*objectives)
+    it = (C.c_long * n)()
+    res = (C.c_double * n)()
+    st = (C.c_int * n)()
+    r = _lib.hlbm_batch_solve_adjoint(batch, _ctx_array(ctxs), n, objs, mode, tol, max_iter,
+                                      it, res, st)
+    if r < 0 and all(v >= 0 for v in st):
+        _check_many(ctxs, r)
+    return r, [(st[k], it[k], res[k]) for k in range(n)]
+
+
+def hlbm_batch_destroy(batch):
+    _lib.hlbm_batch_destroy(batch)
 
 
 def hlbm_objective_noalloc(lattice: int, dims: Sequence[int], tau: float, Cs: float, u_in: float,

@@ -47,6 +47,7 @@ class Request:
     tag: object = None
     t_submit: float = 0.0
     adjoint_solver: int = 0              # 0 fixed point, 1 restarted GMRES (same fixed point)
+    block_x: int = 0                     # threads per block along x (0: chosen by grid size)
 
 
 @dataclass
@@ -134,13 +135,38 @@ def _key(req: "Request"):
     return (req.q, tuple(req.dims), req.storage)
 
 
+BATCH_BLOCK_X = 128  # the block width batched contexts share (the library's NT)
+
+
+def batchable(req: "Request", max_cells: int) -> bool:
+    """Requests the batched lane can step together: FP32, BGK without the
+    Smagorinsky model, the fixed-point adjoint, J_FFA or J_DISS, and a grid
+    small enough that it cannot fill the GPU alone."""
+    return (req.storage == H.FP32 and req.Cs == 0.0 and req.adjoint_solver == 0
+            and req.objective in (H.OBJ_DRAG_FFA, H.OBJ_DISSIPATION)
+            and int(np.prod(req.dims)) <= max_cells)
+
+
 class SensitivityServer:
     """Admit requests into at most ``slots`` concurrent solves within
-    ``hbm_budget`` bytes; results are returned through futures."""
+    ``hbm_budget`` bytes; results are returned through futures.
 
-    def __init__(self, slots: int = 8, hbm_budget: int = 200 << 30, reuse_contexts: bool = True):
+    Requests that ``batchable`` accepts (grids of at most ``batch_cells``
+    cells) go to the batched lane instead: one host thread takes every such
+    request waiting, up to ``batch_slots``, as a cohort and steps them together
+    on one stream through the library's batched entry points (one kernel launch
+    per primal step or adjoint sweep for the whole cohort), while the other
+    requests run concurrently on their own contexts and streams.  Requests
+    that arrive while a cohort runs form the next one."""
+
+    def __init__(self, slots: int = 8, hbm_budget: int = 200 << 30, reuse_contexts: bool = True,
+                 batch_cells: int = 400_000, batch_slots: int = 32):
         self.slots = slots
         self.budget = hbm_budget
+        self.batch_cells = batch_cells
+        self.batch_slots = batch_slots
+        self._bpending: List[tuple] = []
+        self.cohorts: List[int] = []
         self._q: "queue.Queue[tuple]" = queue.Queue()
         self._used = 0
         self._active = 0
@@ -152,6 +178,10 @@ class SensitivityServer:
         self.completed: List[Result] = []
         self.pool = ContextPool() if reuse_contexts else None
         self._sched.start()
+        self._batch_thread = None
+        if batch_cells > 0:
+            self._batch_thread = threading.Thread(target=self._batch_loop, daemon=True)
+            self._batch_thread.start()
 
     # ------------------------------------------------------------------
     def submit(self, req: Request) -> Future:
@@ -162,7 +192,10 @@ class SensitivityServer:
             fut.set_exception(H.HlbmError(H.ENOMEM, "request larger than the HBM budget"))
             return fut
         with self._cv:
-            self._pending.append((req, fut, need))
+            if self._batch_thread is not None and batchable(req, self.batch_cells):
+                self._bpending.append((req, fut, need))
+            else:
+                self._pending.append((req, fut, need))
             self._cv.notify_all()
         return fut
 
@@ -171,6 +204,8 @@ class SensitivityServer:
             self._stop = True
             self._cv.notify_all()
         self._sched.join()
+        if self._batch_thread is not None:
+            self._batch_thread.join()
         for t in self._threads:
             t.join()
         if self.pool is not None:
@@ -192,7 +227,12 @@ class SensitivityServer:
                          if self._fits(need))
                 req, fut, need = self._pending.pop(k)
                 solver = self.pool.take(_key(req)) if self.pool is not None else None
-                if solver is None:
+                if solver is not None:
+                    # a reused context keeps every buffer it ever allocated (a
+                    # Krylov basis of an earlier GMRES request, for instance):
+                    # account for the most it has held
+                    need = max(need, getattr(solver, "held_bytes", need))
+                else:
                     while self.pool is not None and self._used + self.pool.idle_bytes + need > self.budget:
                         if not self.pool.evict_one():
                             break
@@ -201,6 +241,98 @@ class SensitivityServer:
             t = threading.Thread(target=self._run, args=(req, fut, need, solver), daemon=True)
             t.start()
             self._threads.append(t)
+
+    # ------------------------------------------------------------------
+    def _batch_loop(self):
+        import torch
+
+        stream = torch.cuda.Stream()
+        sptr = int(stream.cuda_stream)
+        batches = {}
+        idle = {}   # (q, dims) -> idle Solvers of this lane (created on its stream)
+        while True:
+            with self._cv:
+                while not self._stop and not self._batch_admissible():
+                    self._cv.wait(timeout=0.05)
+                if self._stop and not self._bpending:
+                    break
+                cohort = []
+                rest = []
+                for item in self._bpending:
+                    if len(cohort) < self.batch_slots and self._fits(item[2]):
+                        cohort.append(item)
+                        self._used += item[2]
+                    else:
+                        rest.append(item)
+                self._bpending = rest
+            if not cohort:
+                continue
+            self.cohorts.append(len(cohort))
+            groups = {}
+            for item in cohort:
+                r = item[0]
+                groups.setdefault((r.q, r.warm_steps, r.avg_steps, r.mode, r.tol, r.max_iter),
+                                  []).append(item)
+            for key, items in groups.items():
+                q = key[0]
+                if q not in batches:
+                    batches[q] = H.hlbm_batch_create(q, sptr)
+                self._run_cohort(batches[q], items, idle, sptr)
+            with self._cv:
+                for _, _, need in cohort:
+                    self._used -= need
+                self._cv.notify_all()
+        for b in batches.values():
+            H.hlbm_batch_destroy(b)
+        for lst in idle.values():
+            for s_ in lst:
+                s_.close()
+
+    def _run_cohort(self, batch, items, idle, sptr):
+        t0 = time.perf_counter()
+        solvers = []
+        try:
+            for req, _, _ in items:
+                key = (req.q, tuple(req.dims))
+                s_ = idle[key].pop() if idle.get(key) else None
+                if s_ is None:
+                    s_ = Solver(req.q, req.dims, req.tau, req.Cs, storage=H.FP32, u_in=req.u_in,
+                                regions=req.regions, objectives=req.objective, stream=sptr,
+                                block_x=BATCH_BLOCK_X)
+                else:
+                    s_.configure(req.tau, req.Cs, u_in=req.u_in, regions=req.regions,
+                                 objectives=req.objective)
+                solvers.append(s_)
+                s_.set_porosity(req.porosity)
+                H.hlbm_init_equilibrium(s_.ctx)
+            ctxs = [s_.ctx for s_ in solvers]
+            r0 = items[0][0]
+            steps = r0.warm_steps + r0.avg_steps
+            H.hlbm_batch_run_primal(batch, ctxs, steps, r0.avg_steps)
+            Js = [s_.objective(req.objective) for s_, (req, _, _) in zip(solvers, items)]
+            _, per = H.hlbm_batch_solve_adjoint(batch, ctxs, [req.objective for req, _, _ in items],
+                                                r0.mode, r0.tol, r0.max_iter)
+            for s_, (req, fut, _), J, (st, it, res) in zip(solvers, items, Js, per):
+                if st < 0:
+                    fut.set_exception(H.HlbmError(st, H.hlbm_last_error(s_.ctx)))
+                    continue
+                G = s_.gradient()
+                N = int(np.prod(req.dims))
+                out = Result(req.tag, J, G, it, res, st, 0.0, 0.0, N * (steps + it))
+                out.queued_s = t0 - req.t_submit
+                out.latency_s = time.perf_counter() - req.t_submit
+                self.completed.append(out)
+                fut.set_result(out)
+        except Exception as e:  # noqa: BLE001 - forwarded to the callers
+            for _, fut, _ in items:
+                if not fut.done():
+                    fut.set_exception(e)
+        finally:
+            for s_, (req, _, _) in zip(solvers, items):
+                idle.setdefault((req.q, tuple(req.dims)), []).append(s_)
+
+    def _batch_admissible(self) -> bool:
+        return any(self._fits(need) for _, _, need in self._bpending)
 
     def _fits(self, need: int) -> bool:
         # idle pooled contexts can always be evicted to make room
@@ -227,7 +359,8 @@ class SensitivityServer:
                 self._used -= need
                 self._active -= 1
                 if keep is not None:
-                    self.pool.give(_key(req), keep, need)
+                    keep.held_bytes = max(need, getattr(keep, "held_bytes", 0))
+                    self.pool.give(_key(req), keep, keep.held_bytes)
                 self._cv.notify_all()
 
 
@@ -240,7 +373,7 @@ def solve_one(req: Request, solver: Optional[Solver] = None, keep_context: bool 
     if solver is None:
         s = Solver(req.q, req.dims, req.tau, req.Cs, storage=req.storage, u_in=req.u_in,
                    regions=req.regions, objectives=req.objective,
-                   adjoint_solver=req.adjoint_solver)
+                   adjoint_solver=req.adjoint_solver, block_x=req.block_x)
     else:
         s = solver
         s.configure(req.tau, req.Cs, u_in=req.u_in, regions=req.regions, objectives=req.objective,

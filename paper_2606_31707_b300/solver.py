@@ -23,7 +23,7 @@ class Solver:
                  accum_stride: int = 1, check_every: int = 100, stream=None,
                  u_solid=(0.0, 0.0, 0.0), average_full_f: bool = False,
                  adjoint_solver: int = 0, gmres_restart: int = 30, gmres_inner: int = 100,
-                 collision: int = H.COLL_BGK, inflow_profile=None):
+                 collision: int = H.COLL_BGK, inflow_profile=None, block_x: int = 0):
         self.q = lattice
         self.dims = tuple(int(v) for v in dims)
         self.dim = 2 if lattice == 9 else 3
@@ -33,6 +33,7 @@ class Solver:
         opt.gmres_restart = gmres_restart
         opt.gmres_inner = gmres_inner
         opt.collision = collision
+        opt.block_x = block_x
         prof = None
         if inflow_profile is not None:
             prof = np.ascontiguousarray(inflow_profile, dtype=np.float64).ravel()

@@ -5,7 +5,8 @@ d = 1 outside; drag J_FFA on the plane x = 300 and dissipation J_DISS over
 the whole domain).
 
 * The gradient that ``torch.autograd`` returns through ``HLBMObjective``
-  (FP32 populations, steady primal, adjoint to 1e-6) against the FP64
+  (FP32 populations, steady primal, adjoint to 2e-5, the FP32 floor of its
+  update criterion here) against the FP64
   oracle's gradient: the oracle's steady state by Newton steps with its exact
   step Jacobian and its adjoint by a sparse direct solve (Eq. gradients_steady).
   Bound 1e-4 relative L2 over the whole domain.
@@ -31,6 +32,9 @@ from tests.hlbm_cases import oracle_grf_gradients  # noqa: E402
 from workloads import Regions, make_workload  # noqa: E402
 
 TOL_ORACLE = 1e-4
+# the update criterion of the FP32 fixed-point iteration stalls near 1e-5 on
+# this case (the rounding of the FP32 adjoint populations): its tolerance
+TOL_ADJ_FP32 = 2e-5
 H_FD = 1e-4
 N_CELLS = 32
 
@@ -74,12 +78,13 @@ def test_autograd_grf_gradient_against_oracle_and_central_differences(oracle_fut
     tau = _tau0(wl)
     # autograd, FP32 populations
     s32 = Solver(9, wl.dims, tau, 0.0, storage=H.FP32, u_in=wl.u0, regions=R)
-    spec = PrimalSpec(steps=200000, avg_window=1, objective=objective, tol=1e-6, max_iter=400000)
+    spec = PrimalSpec(steps=200000, avg_window=1, objective=objective, tol=TOL_ADJ_FP32,
+                      max_iter=1_000_000)
     dt = torch.from_numpy(wl.porosity.astype(np.float32)).to(dev).requires_grad_(True)
     J32 = HLBMObjective.apply(dt, s32, spec)
     J32.backward()
     st, it, res = s32.last_adjoint
-    assert st == H.OK and res <= 1e-6
+    assert st == H.OK and res <= TOL_ADJ_FP32
     G = dt.grad.detach().double().cpu().numpy()
     s32.close()
     # central differences of J with FP64 populations, warm-started at the steady state

@@ -62,9 +62,12 @@ def test_autograd_fp32_gradient_within_1e4_of_fp64():
     dims, d, R, tau, box = _grf_case()
     dev = torch.device("cuda", 0)
     Gs = []
-    for storage, tol in ((H.FP64, 1e-12), (H.FP32, 1e-6)):
+    # adjoint tolerances: FP64 1e-11; FP32 1e-5, above the floor of the FP32
+    # update criterion
+    for storage, tol in ((H.FP64, 1e-11), (H.FP32, 1e-5)):
         s = Solver(9, dims, tau, 0.0, storage=storage, u_in=0.05, regions=R)
-        spec = PrimalSpec(steps=40000, avg_window=1, objective=H.OBJ_DISSIPATION, tol=tol)
+        spec = PrimalSpec(steps=40000, avg_window=1, objective=H.OBJ_DISSIPATION, tol=tol,
+                          max_iter=1_000_000)
         dt = torch.from_numpy(d.astype(np.float32 if storage == H.FP32 else np.float64)).to(dev)
         dt.requires_grad_(True)
         HLBMObjective.apply(dt, s, spec).backward()
@@ -92,9 +95,10 @@ def _requests():
 
 
 def test_served_results_identical_alone_and_in_the_mix():
+    # the per-request lane (no batching): each request on its own context and stream
     reqs = _requests()
     alone = [solve_one(r) for r in reqs]
-    srv = SensitivityServer(slots=4)
+    srv = SensitivityServer(slots=4, batch_cells=0)
     futs = [srv.submit(r) for r in reqs]
     mixed = [f.result(timeout=600) for f in futs]
     srv.close()
@@ -106,7 +110,7 @@ def test_served_results_identical_alone_and_in_the_mix():
 
 def test_server_rejects_requests_above_the_budget():
     r = _requests()[0]
-    srv = SensitivityServer(slots=2, hbm_budget=1 << 20)
+    srv = SensitivityServer(slots=2, hbm_budget=1 << 20, batch_cells=0)
     fut = srv.submit(r)
     with pytest.raises(H.HlbmError):
         fut.result(timeout=10)
@@ -124,7 +128,7 @@ def test_reused_contexts_give_the_same_results_as_fresh_ones():
                             warm_steps=500, avg_steps=300, objective=H.OBJ_DRAG_FFA, max_iter=800,
                             regions=base.regions, tag=k))
     fresh = [solve_one(r) for r in reqs]
-    srv = SensitivityServer(slots=2)
+    srv = SensitivityServer(slots=2, batch_cells=0)
     got = [f.result(timeout=600) for f in [srv.submit(r) for r in reqs]]
     assert srv.pool.hits >= 1
     srv.close()
