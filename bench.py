@@ -167,8 +167,9 @@ def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False, rr=False):
     acc = plain + sb * (state + (1 if les else 0))
     acc += (ffa_cells * sb * 2 + diss_cells * sb * (1 + D + D * (D + 1) // 2 + 1)) / N
     rec = D + 2 + D * (D + 1) // 2 if rr else (q if exact_rec else D + 2)
-    adj_ffa = (2 * q + rec + 1) * real_bytes + ffa_cells * q * real_bytes / N
-    adj_diss = (2 * q + rec + 1) * real_bytes + diss_cells * q * real_bytes / N
+    # the source: the derivative polynomial's coefficients in the objective's region
+    adj_ffa = (2 * q + rec + 1) * real_bytes + ffa_cells * 2 * real_bytes / N
+    adj_diss = (2 * q + rec + 1) * real_bytes + diss_cells * (1 + D + D * (D + 1) // 2) * real_bytes / N
     return dict(plain=plain, acc=acc, adj_ffa=adj_ffa, adj_diss=adj_diss)
 
 

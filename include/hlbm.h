@@ -347,7 +347,9 @@ void hlbm_batch_destroy(hlbm_batch* batch);
  * returns HLBM_ESCRATCH.  Calls that overlap on the GPU race on the scratch
  * array; order them on one stream.  The first call on a device looks up
  * the scratch address (cudaGetSymbolAddress, that device current); make it
- * before any stream capture.  Errors: HLBM_EINVAL (bad argument),
+ * before any stream capture.  The address is kept for the life of the
+ * process: after a cudaDeviceReset of that device the kept address is stale,
+ * so do not call this entry point on a device that has been reset.  Errors: HLBM_EINVAL (bad argument),
  * HLBM_ESCRATCH, HLBM_ECUDA.
  * --------------------------------------------------------------------- */
 #define HLBM_NOALLOC_MAX_BLOCKS 65536

@@ -293,15 +293,61 @@ __device__ __forceinline__ void transpose_collide(const RRCell<R, EXACT>& c, R (
 template <int Q, class R, bool EXACT, bool RR> struct CellOf { using T = LinCell<Q, R, EXACT>; };
 template <int Q, class R, bool EXACT> struct CellOf<Q, R, EXACT, true> { using T = RRCell<R, EXACT>; };
 
+// lam += g_bar in the source box.  J_FFA and J_DISS store g_bar as the
+// coefficients of their derivative polynomials in xi (2 or 1 + D + D(D+1)/2 per
+// cell instead of q values) and the values are formed here, in the order of
+// coef_basis; J_MEA stores the q values.
 template <int Q, class R>
 __device__ __forceinline__ void add_source(const AdjointArgs& a, int x, int y, int z, R (&v)[Q]) {
   if (x >= a.sb[0] && x < a.sb[1] && y >= a.sb[2] && y < a.sb[3] && z >= a.sb[4] && z < a.sb[5]) {
+    using L = Lat<Q>;
+    constexpr int D = L::D;
     const long long bc = (long long)(x - a.sb[0]) +
                          (long long)(a.sb[1] - a.sb[0]) *
                              ((long long)(y - a.sb[2]) + (long long)(a.sb[3] - a.sb[2]) * (z - a.sb[4]));
     const R* src = static_cast<const R*>(a.src);
+    const long long sp = a.src_pitch;
+    if (a.src_nc == 0) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) v[i] += src[(long long)i * a.src_pitch + bc];
+      for (int i = 0; i < Q; ++i) v[i] += src[(long long)i * sp + bc];
+    } else if (a.src_nc == 2) {
+      // J_FFA: c0 + c1 xi_x
+      const R c0 = src[bc], c1 = src[sp + bc];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        R t = c0;
+        if (L::cx(i)) t += L::cx(i) > 0 ? c1 : -c1;
+        v[i] += t;
+      }
+    } else {
+      // J_DISS: c0 + c . xi + xi . C . xi (squares, then doubled cross terms)
+      constexpr int NC = 1 + D + D * (D + 1) / 2;
+      R c[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) c[k] = src[(long long)k * sp + bc];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const int ex = L::cx(i), ey = L::cy(i), ez = L::cz(i);
+        R t = c[0];
+        if (ex) t += ex > 0 ? c[1] : -c[1];
+        if (ey) t += ey > 0 ? c[2] : -c[2];
+        if constexpr (D == 3) {
+          if (ez) t += ez > 0 ? c[3] : -c[3];
+        }
+        constexpr int S0 = 1 + D;  // first square coefficient
+        if (ex) t += c[S0];
+        if (ey) t += c[S0 + 1];
+        if constexpr (D == 2) {
+          if (ex && ey) t += (ex * ey > 0) ? R(2) * c[4] : -R(2) * c[4];
+        } else {
+          if (ez) t += c[S0 + 2];
+          if (ex && ey) t += (ex * ey > 0) ? R(2) * c[7] : -R(2) * c[7];
+          if (ex && ez) t += (ex * ez > 0) ? R(2) * c[8] : -R(2) * c[8];
+          if (ey && ez) t += (ey * ez > 0) ? R(2) * c[9] : -R(2) * c[9];
+        }
+        v[i] += t;
+      }
+    }
   }
 }
 
@@ -399,14 +445,16 @@ __device__ __forceinline__ void adjoint_body(const AdjointArgs& a, int bxi, int 
 // Resident blocks per SM requested from ptxas for the FP32 D3Q19 sweeps
 // (0 = no request, ptxas chooses); the exact variants otherwise take more than
 // 120 registers.  Chosen by timing sweeps on the LES case (640x320x100):
-//   BGK exact LES: none 1419 us, 4 blocks 1262, 5: 1270
+//   BGK exact LES: none 1419 us, 4 blocks 1262, 5: 1270; again with the
+//     slice of the benchmark (J_FFA / J_DISS sweeps, GLUPS): 3: 16.1 / 12.9,
+//     4: 18.4 / 14.9, 5: 18.9 / 15.4, 6: 17.9 / 14.7
 //   RR exact:      none 1265, 4: 1154, 5: 1091
 //   RR frozen:     none 1167, 5: 1057, 6: 1043
 #ifndef HLBM_AMINB_D3Q19
 #define HLBM_AMINB_D3Q19 0
 #endif
 #ifndef HLBM_AMINB_D3Q19_EXACT
-#define HLBM_AMINB_D3Q19_EXACT 4
+#define HLBM_AMINB_D3Q19_EXACT 5
 #endif
 #ifndef HLBM_AMINB_D3Q19_RR
 #define HLBM_AMINB_D3Q19_RR 6
@@ -569,17 +617,19 @@ __global__ void __launch_bounds__(NT) k_source(SourceArgs a) {
     const long long vol = (long long)bx * by * (a.box[5] - a.box[4]);
     const long long cell = cell_of(a.g, a.box[0] + xl, a.box[2] + yl, a.box[4] + zl);
     const int nc = ncoef(a.obj_slot, D);
-    double cf[10];
-    for (int k = 0; k < nc; ++k) cf[k] = a.gsum[(long long)k * a.g.N + cell] * a.inv_n;
+    R cf[10];
     R* src = static_cast<R*>(a.src);
+    for (int k = 0; k < nc; ++k) {
+      cf[k] = (R)(a.gsum[(long long)k * a.g.N + cell] * a.inv_n);
+      src[(long long)k * vol + bc] = cf[k];
+    }
+    // ||g_bar||^2 of the values the sweep forms from these coefficients
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       double gv = 0.0;
       for (int k = 0; k < nc; ++k)
-        gv += cf[k] * coef_basis(a.obj_slot, D, k, Lat<Q>::cx(i), Lat<Q>::cy(i), Lat<Q>::cz(i));
-      const R v = (R)gv;
-      src[(long long)i * vol + bc] = v;
-      acc += (double)v * (double)v;
+        gv += (double)cf[k] * coef_basis(a.obj_slot, D, k, Lat<Q>::cx(i), Lat<Q>::cy(i), Lat<Q>::cz(i));
+      acc += gv * gv;
     }
   }
   __shared__ double sh[NT / 32];

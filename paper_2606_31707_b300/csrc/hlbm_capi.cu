@@ -52,6 +52,7 @@ struct hlbm_ctx {
   float* gstage[2] = {nullptr, nullptr};
   float* ddstage[2] = {nullptr, nullptr};
   long long nblk = 0;
+  long long njslot = 0;  // per-warp slots of the objective sums (nblk x warps per block)
   long nsamples = 0;
   int acc_mask = 0;
   long generation = 0;  // bumps whenever the averaged state changes
@@ -77,6 +78,7 @@ struct hlbm_ctx {
   double rec_taub = 0;
   long rec_generation = -1;
   int last_obj = 0;
+  int src_obj = 0;  // objective whose g_bar the source buffer holds
   int last_mode = 0;
   bool have_adjoint = false;
   // scalars
@@ -266,7 +268,7 @@ int ensure_averages(hlbm_ctx* c, int mask) {
     if (stage && !c->gstage[o] && !(c->gstage[o] = (float*)dalloc(c, gstage_bytes(c, o)))) return set_err(c, HLBM_ENOMEM, "gstage");
     if (!c->gsum[o] && !(c->gsum[o] = (double*)dalloc(c, coef_bytes(c, o)))) return set_err(c, HLBM_ENOMEM, "gsum");
     if (!c->ddsum[o] && !(c->ddsum[o] = (double*)dalloc(c, (size_t)N * 8))) return set_err(c, HLBM_ENOMEM, "ddsum");
-    if (!c->jblk[o] && !(c->jblk[o] = (double*)dalloc(c, (size_t)c->nblk * 8))) return set_err(c, HLBM_ENOMEM, "jblk");
+    if (!c->jblk[o] && !(c->jblk[o] = (double*)dalloc(c, (size_t)c->njslot * 8))) return set_err(c, HLBM_ENOMEM, "jblk");
   }
   return HLBM_OK;
 }
@@ -285,7 +287,7 @@ int reset_averages(hlbm_ctx* c, int mask) {
     if (c->gstage[o]) HLBM_TRY(c, cudaMemsetAsync(c->gstage[o], 0, gstage_bytes(c, o), c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->gsum[o], 0, coef_bytes(c, o), c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->ddsum[o], 0, (size_t)N * 8, c->stream), "memset");
-    HLBM_TRY(c, cudaMemsetAsync(c->jblk[o], 0, (size_t)c->nblk * 8, c->stream), "memset");
+    HLBM_TRY(c, cudaMemsetAsync(c->jblk[o], 0, (size_t)c->njslot * 8, c->stream), "memset");
   }
   c->nsamples = 0;
   c->acc_mask = mask;
@@ -472,6 +474,7 @@ int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau, doub
     c->g.bx = bx;
   }
   c->nblk = (long long)((dims[0] + c->g.bx - 1) / c->g.bx) * dims[1] * dims[2];
+  c->njslot = c->nblk * (c->g.bx / 32);
   if (c->opt.collision != HLBM_COLL_BGK && c->opt.collision != HLBM_COLL_RR) { delete c; return HLBM_EINVAL; }
   c->rr = c->opt.collision == HLBM_COLL_RR;
   c->mplanes = 1 + c->D + (c->rr ? c->D * (c->D + 1) / 2 : 0);
@@ -886,7 +889,7 @@ int hlbm_objective(hlbm_ctx* c, int obj, double* J) {
     *J = c->scal_host[0] / (c->scal_host[1] > 0 ? c->scal_host[1] : 1.0);
     return HLBM_OK;
   }
-  HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->jblk[o], c->nblk, c->scal_dev, c->stream), "reduce");
+  HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->jblk[o], c->njslot, c->scal_dev, c->stream), "reduce");
   HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
   HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
   *J = c->scal_host[0] / (double)c->nsamples;
@@ -947,6 +950,8 @@ static AdjointArgs adjoint_args(hlbm_ctx* c, int mode, const int sb[6]) {
   a.src = c->src;
   std::memcpy(a.sb, sb, sizeof a.sb);
   a.src_pitch = (long long)(sb[1] - sb[0]) * (sb[3] - sb[2]) * (sb[5] - sb[4]);
+  // J_MEA keeps its q values; the others their derivative-polynomial coefficients
+  a.src_nc = c->src_obj == HLBM_OBJ_DRAG_MEA ? 0 : ncoef(obj_slot(c->src_obj), c->D);
   a.snap = c->snap;
   a.red = c->red;
   (void)mode;
@@ -1179,6 +1184,7 @@ static int adjoint_setup(hlbm_ctx* c, int obj, int mode, AdjSetup* out) {
   double gnorm = std::sqrt(c->scal_host[0]);
   if (!(gnorm > 0.0)) gnorm = 1.0;
 
+  c->src_obj = obj;
   out->a = adjoint_args(c, mode, sb);
   out->exact = exact;
   out->nb_adj = nb_adj;
@@ -1453,7 +1459,7 @@ int hlbm_set_field(hlbm_ctx* c, int which, const void* data, int dtype, int on_d
       if (!(c->acc_mask & (1 << o))) continue;
       CNT(c, launch_scale)(c->gsum[o], (long long)ncoef(o, c->D) * N, s, c->stream);
       CNT(c, launch_scale)(c->ddsum[o], N, s, c->stream);
-      CNT(c, launch_scale)(c->jblk[o], c->nblk, s, c->stream);
+      CNT(c, launch_scale)(c->jblk[o], c->njslot, s, c->stream);
     }
   }
   if (c->nsamples < 1) {
@@ -1465,7 +1471,7 @@ int hlbm_set_field(hlbm_ctx* c, int which, const void* data, int dtype, int on_d
     const int o = need_mask - 1;
     HLBM_TRY(c, cudaMemsetAsync(c->gsum[o], 0, coef_bytes(c, o), c->stream), "memset");
     HLBM_TRY(c, cudaMemsetAsync(c->ddsum[o], 0, (size_t)N * 8, c->stream), "memset");
-    HLBM_TRY(c, cudaMemsetAsync(c->jblk[o], 0, (size_t)c->nblk * 8, c->stream), "memset");
+    HLBM_TRY(c, cudaMemsetAsync(c->jblk[o], 0, (size_t)c->njslot * 8, c->stream), "memset");
     c->acc_mask |= need_mask;
   }
   rc = stage_in(c, data, dtype, on_device, n);
@@ -1510,7 +1516,7 @@ int hlbm_save(hlbm_ctx* c, const char* path) {
   FILE* fp = std::fopen(path, "wb");
   if (!fp) return set_err(c, HLBM_EINVAL, "cannot open %s", path);
   CkptHeader h{};
-  std::memcpy(h.magic, "HLBMCK3", 8);
+  std::memcpy(h.magic, "HLBMCK4", 8);
   h.has_fsum = c->fsum != nullptr;
   h.mplanes = c->mplanes;
   h.q = c->q; h.storage = c->storage; h.nx = c->g.nx; h.ny = c->g.ny; h.nz = c->g.nz;
@@ -1539,7 +1545,7 @@ int hlbm_save(hlbm_ctx* c, const char* path) {
       if (!(h.acc_mask & (1 << o))) continue;
       rc = dump(c->gsum[o], coef_bytes(c, o));
       if (!rc) rc = dump(c->ddsum[o], (size_t)c->g.N * 8);
-      if (!rc) rc = dump(c->jblk[o], (size_t)c->nblk * 8);
+      if (!rc) rc = dump(c->jblk[o], (size_t)c->njslot * 8);
     }
   }
   std::fclose(fp);
@@ -1552,7 +1558,7 @@ int hlbm_load(hlbm_ctx* c, const char* path) {
   FILE* fp = std::fopen(path, "rb");
   if (!fp) return set_err(c, HLBM_EINVAL, "cannot open %s", path);
   CkptHeader h{};
-  if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "HLBMCK3", 8) != 0 ||
+  if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "HLBMCK4", 8) != 0 ||
       h.q != c->q || h.storage != c->storage || h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz ||
       h.mplanes != c->mplanes) {
     std::fclose(fp);
@@ -1584,7 +1590,7 @@ int hlbm_load(hlbm_ctx* c, const char* path) {
       if (!(h.acc_mask & (1 << o))) continue;
       rc = load(c->gsum[o], coef_bytes(c, o));
       if (!rc) rc = load(c->ddsum[o], (size_t)c->g.N * 8);
-      if (!rc) rc = load(c->jblk[o], (size_t)c->nblk * 8);
+      if (!rc) rc = load(c->jblk[o], (size_t)c->njslot * 8);
     }
   }
   std::fclose(fp);

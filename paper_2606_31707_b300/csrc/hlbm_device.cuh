@@ -433,6 +433,21 @@ __device__ __forceinline__ double block_sum(F2 v, double* sh) {
   return r;
 }
 
+// warp sums of the objective accumulators as FP64 (valid in every lane)
+__device__ __forceinline__ double warp_sum_j(double v) { return warp_sum(v); }
+__device__ __forceinline__ double warp_sum_j(F2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    const float l = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    float s, e;
+    two_sum(v.hi, h, s, e);
+    v.hi = s;
+    v.lo = v.lo + l + e;
+  }
+  return (double)v.hi + (double)v.lo;
+}
+
 // the objective accumulator of an arithmetic type: FP64 itself, or a double-float pair
 template <class R> struct JAcc { using T = F2; };
 template <> struct JAcc<double> { using T = double; };

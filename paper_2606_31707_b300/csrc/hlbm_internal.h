@@ -32,7 +32,7 @@ struct PrimalArgs {
   double* gsum[2];    // ncoef(obj) x N running sums of the coefficients of dJ/df
                       // in the basis of coef_basis() (FFA, DISS); may be null
   double* ddsum[2];   // N running sums of dJ/dd
-  double* jblk[2];    // per-block running sums of J
+  double* jblk[2];    // per-warp running sums of J (block linear index x warps per block + warp)
   // FP32 kernels add each sample to a float staging copy of every sum and fold
   // the staged value into the FP64 sum every kStage samples (flush variant),
   // so that the per-step path issues no FP64 instruction; FP64 kernels add to
@@ -154,7 +154,7 @@ struct SourceArgs {
   const double* gsum;  // ncoef x N coefficient sums
   int obj_slot;        // 0 FFA, 1 DISS
   double inv_n;
-  void* src;           // real, q planes of box volume
+  void* src;           // real, ncoef planes of box volume: the averaged coefficients
   int box[6];
   Grid g;
   double* red;         // per-block partial sums of src^2
@@ -170,9 +170,12 @@ struct AdjointArgs {
   double tau_b, kles;
   double us[3];
   float tau_b_f, kles_f, us_f[3];
-  const void* src;     // g_bar restricted to the source box (real)
+  const void* src;     // g_bar restricted to the source box (real): src_nc = 0: q planes of
+                       // its values; src_nc > 0: the src_nc planes of its coefficients in the
+                       // basis of coef_basis (the objective's derivative polynomial in xi)
   int sb[6];
   long long src_pitch;
+  int src_nc;
   void* snap;          // residual snapshot (real, q planes of g.pitch)
   double* red;         // per-block partial of the residual
 };

@@ -402,14 +402,16 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
 // each variant (CUDA events, 3 repeats) on the Karman case (D2Q9 1100x410)
 // and the LES case (D3Q19 640x320x100), FP32:
 //   D2Q9 BGK averaging:   none 18.5 us, 8 blocks 16.4 us (64 registers)
-//   D3Q19 BGK averaging:  none 2204 us, 3: 2230, 4: 2296, 5: 2564
+//   D3Q19 BGK averaging with the shared-memory prefetch of the staged sums and
+//   no barrier (the exact-LES window, full f): none 1621 us (108 / 134
+//   registers even / odd), 4: 1452, 5: 1447, 6: 1582 (spills)
 //   D3Q19 RR averaging:   none 1800 us, 4: 1880, 5: 1687
 //   D3Q19 RR plain:       none 712 us, 4: 796
 #ifndef HLBM_MINB_ACC_D2Q9
 #define HLBM_MINB_ACC_D2Q9 8
 #endif
 #ifndef HLBM_MINB_ACC_D3Q19
-#define HLBM_MINB_ACC_D3Q19 0
+#define HLBM_MINB_ACC_D3Q19 4
 #endif
 #ifndef HLBM_MINB_ACC_RR_D2Q9
 #define HLBM_MINB_ACC_RR_D2Q9 0
@@ -432,7 +434,7 @@ constexpr int primal_min_blocks() {
 }
 
 // One block of a primal step: x-block bxi of row (y, z); blin is the block's
-// slot in the per-block objective sums.
+// linear index (its warps' objective slots follow from it).
 template <int Q, int S, bool ODD, bool LES, int ACC, bool RR>
 __device__ __forceinline__ void primal_body(const PrimalArgs& a, int bxi, int y, int z,
                                             long long blin) {
@@ -484,14 +486,15 @@ __device__ __forceinline__ void primal_body(const PrimalArgs& a, int bxi, int y,
   if constexpr (ACC > 0) {
     // J of this step: each cell's term (computed in the arithmetic type) is
     // summed over the warp in FP64 (FP64 kernels) or as a double-float pair
-    // (FP32 kernels), over the block's warps in FP64, and added to the block's
-    // FP64 running sum: the reduction carries no FP32 rounding
-    __shared__ double sh[NT / 32];
+    // (FP32 kernels) and added by the warp's first lane to the warp's own FP64
+    // running slot (blocks x warps per block slots): no FP32 rounding in the
+    // reduction, no barrier, and a fixed summation order
+    const long long slot = blin * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
 #pragma unroll
     for (int o = 0; o < 2; ++o) {
       if (!(a.obj_mask & (1 << o))) continue;
-      const double sm = block_sum<NT>(jp[o], sh);
-      if (threadIdx.x == 0) a.jblk[o][blin] += sm;
+      const double w = warp_sum_j(jp[o]);
+      if ((threadIdx.x & 31) == 0) a.jblk[o][slot] += w;
     }
   }
 }

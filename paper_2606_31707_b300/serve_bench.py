@@ -1,25 +1,28 @@
-"""Served batched form vs the plain one-solve-at-a-time path.
+"""Served form vs the plain one-solve-at-a-time path on a Poisson stream.
 
-``python -m paper_2606_31707_b300.serve_bench [--requests N] [--rate R] [--slots S]``
+``python -m paper_2606_31707_b300.serve_bench [--requests N] [--slots S]``
 
-Requests arrive as a Poisson stream (seeded) with grid sizes drawn from the
-D2Q9 grids {200x80, 800x320, 2000x800} and the D3Q19 grids {128^3,
-256x128x64}, a seeded porous cylinder each and Re in [20, 200].  Every
-request is one mean-flow sensitivity solve with a fixed budget (2000 warm-up
-+ 2000 averaging steps, adjoint to 1e-6 or 4000 iterations) in FP32.
+Requests are drawn (seeded) with grid sizes from the D2Q9 grids {200x80,
+800x320, 2000x800} and the D3Q19 grids {128^3, 256x128x64}, a seeded porous
+cylinder each and Re in [20, 200].  Every request is one mean-flow
+sensitivity solve with a fixed budget (2000 warm-up + 2000 averaging steps,
+adjoint to 1e-6 or 4000 iterations) in FP32.
 
-* plain: one solve after the other, in arrival order (a request waits for
-  the previous one to finish);
-* served: the continuous-batching server, requests submitted at their
-  arrival times, up to ``slots`` solves running concurrently.
+* plain: one solve after the other on its own context (each kernel launch
+  covers one request); its service times give the plain capacity C in
+  gradients/s;
+* served: the continuous-batching server (requests of at most 400 000 cells
+  stepped together in cohorts through the batched entry points, the others
+  on their own contexts and streams concurrently), requests submitted at
+  their arrival times scaled to rates of 0.5, 0.9 and 1.5 C and to the
+  nominal 200 requests/s.
 
-Prints one JSON line with gradients/s and p50/p99 latency of both, and the
-largest relative gradient difference between them (the served results are
-expected to be identical when both use the same adjoint solver).  With
-``--served-solver gmres`` the served form solves the same adjoint fixed point
-by restarted GMRES; ``--accuracy`` then also solves every request untimed to a
-tighter tolerance and reports each form's largest relative gradient error
-against that reference, the accuracy at which the two are compared.
+Prints one JSON line: gradients/s and p50/p99 latency of the plain path and
+of the served form at every rate, and the largest relative gradient
+difference between served and plain results (the same FP32 arithmetic in
+other kernel instances: rounding only).  With ``--accuracy`` every request is
+also solved untimed by GMRES to a tighter tolerance, the reference each
+form's gradient error is stated against.
 """
 from __future__ import annotations
 
@@ -65,88 +68,98 @@ def pct(v, p):
     return float(np.percentile(np.asarray(v), p)) if v else None
 
 
-def run(args):
-    reqs = build_requests(args.requests, args.rate, args.seed, args.warm, args.avg, args.max_iter)
-    # warm-up: one small solve to load kernels
-    solve_one(build_requests(1, args.rate, 99, 50, 50, 20)[0][1])
-
-    # plain path: sequential in arrival order
-    t0 = time.perf_counter()
-    plain = []
-    lat_plain = []
-    clock = 0.0
-    per_size = {}
-    for t_arr, r in reqs:
-        start = max(clock, t_arr)
-        t = time.perf_counter()
-        res = solve_one(r)
-        dt = time.perf_counter() - t
-        clock = start + dt
-        lat_plain.append(clock - t_arr)
-        plain.append(res)
-        per_size.setdefault("x".join(map(str, r.dims)), []).append(round(dt, 4))
-    wall_plain = time.perf_counter() - t0
-    span_plain = clock - reqs[0][0]
-
-    # served path: submit at arrival times, in the chosen storage and solver form
-    import dataclasses
-    st_code = {"fp32": H.FP32, "fp16dev": H.FP16DEV, "bf16dev": H.BF16DEV}[args.served_storage]
-    solver_code = 1 if args.served_solver == "gmres" else 0
-    srv = SensitivityServer(slots=args.slots, hbm_budget=args.budget_gb << 30)
+def _served(reqs, rate_scale, args):
+    """Submit the requests at their arrival times divided by rate_scale."""
+    srv = SensitivityServer(slots=args.slots, hbm_budget=args.budget_gb << 30,
+                            batch_cells=args.batch_cells)
     t0 = time.perf_counter()
     futs = []
     for t_arr, r in reqs:
-        r = dataclasses.replace(r, storage=st_code, adjoint_solver=solver_code)
+        t_arr = t_arr / rate_scale
         now = time.perf_counter() - t0
         if t_arr > now:
             time.sleep(t_arr - now)
-        futs.append(srv.submit(r))
-    served = [f.result() for f in futs]
+        futs.append((t_arr, srv.submit(r)))
+    served = [f.result() for _, f in futs]
     t_end = time.perf_counter() - t0
-    pool = {"hits": srv.pool.hits, "misses": srv.pool.misses} if srv.pool is not None else None
+    cohorts = list(srv.cohorts)
     srv.close()
-    lat_served = [s.latency_s for s in served]
-    span_served = t_end - reqs[0][0]
+    span = t_end - reqs[0][0] / rate_scale
+    lat = [s.latency_s for s in served]
+    return served, {"gradients_per_s": len(served) / span, "p50_s": pct(lat, 50),
+                    "p99_s": pct(lat, 99), "span_s": span, "cohorts": cohorts}
 
+
+def run(args):
+    reqs = build_requests(args.requests, args.rate, args.seed, args.warm, args.avg, args.max_iter)
+    # warm-up: one small solve and one small cohort to load kernels and graphs
+    warm = build_requests(2, args.rate, 99, 64, 64, 20)
+    solve_one(warm[0][1])
+    _served([(0.0, warm[0][1]), (0.0, warm[1][1])], 1.0, args)
+
+    # plain path: one solve at a time; its service time gives the capacity
+    plain, service = [], []
+    per_size = {}
+    for _, r in reqs:
+        t = time.perf_counter()
+        plain.append(solve_one(r))
+        dt = time.perf_counter() - t
+        service.append(dt)
+        per_size.setdefault("x".join(map(str, r.dims)), []).append(round(dt, 4))
+    capacity = len(reqs) / sum(service)
+    # plain latency under the nominal arrival stream: a FIFO queue of the service times
+    clock, lat_plain = 0.0, []
+    for (t_arr, _), dt in zip(reqs, service):
+        clock = max(clock, t_arr) + dt
+        lat_plain.append(clock - t_arr)
+    nominal_rate = len(reqs) / max(reqs[-1][0], 1e-9)
+
+    rates = {}
+    served_nominal = None
+    for name, scale_to in (("0.5C", 0.5 * capacity), ("0.9C", 0.9 * capacity),
+                           ("1.5C", 1.5 * capacity), ("nominal", nominal_rate)):
+        res, stat = _served(reqs, scale_to / nominal_rate, args)
+        stat["rate_per_s"] = scale_to
+        rates[name] = stat
+        if name == "nominal":
+            served_nominal = res
     maxdiff = 0.0
-    for a, b in zip(plain, served):
+    for a, b in zip(plain, served_nominal):
         den = float(np.linalg.norm(a.gradient)) or 1.0
         maxdiff = max(maxdiff, float(np.linalg.norm(a.gradient - b.gradient)) / den)
     accuracy = None
     if args.accuracy:
-        # untimed reference: the same requests, adjoint by GMRES to a tighter tolerance
+        import dataclasses
         ref = [solve_one(dataclasses.replace(r, adjoint_solver=1, tol=args.ref_tol,
                                              max_iter=args.ref_max_iter)) for _, r in reqs]
 
-        def worst(results):
-            e = 0.0
+        def errs(results):
+            out = []
             for a, b in zip(results, ref):
                 den = float(np.linalg.norm(b.gradient)) or 1.0
-                e = max(e, float(np.linalg.norm(a.gradient - b.gradient)) / den)
-            return e
+                out.append(float(np.linalg.norm(a.gradient - b.gradient)) / den)
+            return out
         accuracy = {"reference": {"solver": "gmres", "tol": args.ref_tol,
                                   "max_iter": args.ref_max_iter,
                                   "residuals": [r.adjoint_residual for r in ref]},
-                    "plain_max_rel_err": worst(plain), "served_max_rel_err": worst(served)}
+                    "plain_rel_err": errs(plain), "served_rel_err": errs(served_nominal)}
     lups = sum(r.lups for r in plain)
     line = {
         "metric": "served gradients/s and p50/p99 latency vs one solve at a time",
-        "requests": args.requests, "rate_per_s": args.rate, "slots": args.slots,
+        "requests": args.requests, "slots": args.slots, "batch_cells": args.batch_cells,
         "budget": {"warm_steps": args.warm, "avg_steps": args.avg,
                    "adjoint_max_iter": args.max_iter, "tol": 1e-6, "storage": "fp32"},
-        "plain": {"gradients_per_s": len(plain) / span_plain, "p50_s": pct(lat_plain, 50),
-                  "p99_s": pct(lat_plain, 99), "busy_s": wall_plain},
-        "served": {"gradients_per_s": len(served) / span_served, "p50_s": pct(lat_served, 50),
-                   "p99_s": pct(lat_served, 99), "storage": args.served_storage,
-                   "adjoint_solver": args.served_solver,
-                   "adjoint_iters": [r.adjoint_iters for r in served]},
-        "accuracy": accuracy,
-        "speedup_gradients_per_s": (len(served) / span_served) / (len(plain) / span_plain),
+        "plain": {"capacity_gradients_per_s": capacity, "p50_s_at_nominal": pct(lat_plain, 50),
+                  "p99_s_at_nominal": pct(lat_plain, 99), "busy_s": sum(service),
+                  "mlups": lups / sum(service) / 1e6},
+        "served": rates,
+        "speedup_at_1.5C": rates["1.5C"]["gradients_per_s"] / capacity,
+        "speedup_at_nominal": rates["nominal"]["gradients_per_s"] / capacity,
         "max_rel_gradient_diff_served_vs_plain": maxdiff,
-        "mlups_plain": lups / wall_plain / 1e6,
+        "accuracy": accuracy,
         "plain_solve_s_by_size": per_size,
         "adjoint_iters": [r.adjoint_iters for r in plain],
-        "context_pool": pool,
+        "adjoint_status": [r.status for r in plain],
         "sizes": [list(r.dims) for _, r in reqs],
     }
     print(json.dumps(line))
@@ -154,7 +167,7 @@ def run(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--requests", type=int, default=16)
+    ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=6)
     ap.add_argument("--seed", type=int, default=0)
@@ -162,8 +175,8 @@ def main():
     ap.add_argument("--avg", type=int, default=2000)
     ap.add_argument("--max-iter", type=int, default=4000)
     ap.add_argument("--budget-gb", type=int, default=200)
-    ap.add_argument("--served-storage", default="fp32", choices=["fp32", "fp16dev", "bf16dev"])
-    ap.add_argument("--served-solver", default="fixed-point", choices=["fixed-point", "gmres"])
+    ap.add_argument("--batch-cells", type=int, default=400_000,
+                    help="requests of at most this many cells are stepped together in cohorts")
     ap.add_argument("--accuracy", action="store_true")
     ap.add_argument("--ref-tol", type=float, default=1e-8)
     ap.add_argument("--ref-max-iter", type=int, default=40000)

@@ -190,7 +190,8 @@ def test_full_pipeline_steady_fp64_vs_oracle_gradient_sign_and_directional_fd():
 
 def test_compact_and_full_averages_agree_and_fbar_needs_full():
     # BGK / FTA linearisations read only rho and rho u of f_bar; the full
-    # average of f is optional there and gives the same record
+    # average of f is optional there and gives the same record up to the FP64
+    # summation order (the full average derives the moments after the window)
     P, d, R = _case(9, (300, 24, 1), 0.0, tau=0.8, u_in=0.04)
     Gs = []
     for full in (False, True):
@@ -205,7 +206,7 @@ def test_compact_and_full_averages_agree_and_fbar_needs_full():
         s.solve_adjoint(oobj.DISS, H.ADJ_EXACT, 1e-10, 100000)
         Gs.append(s.gradient())
         s.close()
-    assert np.array_equal(Gs[0], Gs[1])
+    assert rel_l2(Gs[1], Gs[0]) <= 1e-12
 
 
 def test_set_gbar_is_projected_onto_the_derivative_form():
