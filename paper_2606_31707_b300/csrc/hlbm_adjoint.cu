@@ -35,19 +35,21 @@ template <> __device__ __forceinline__ float pi_eps<float>() { return 1e-20f; }
 template <int Q, class R, bool EXACT> struct LinCell {
   R rho, om, d;
   Vec3<R> u, ut;
-  // EXACT only
-  R fneq[EXACT ? Q : 1];
+  // EXACT only: the non-equilibrium stress of f_bar, its norm, tau_eff, and
+  // sn = sum_i mu_i (f_bar_i - f^eq_i) for the mu this cell is processed with
+  // (formed here, so that no array of f^neq stays alive through the transpose)
   Sym<R> P;
-  R nP, tau;
+  R nP, tau, sn;
 };
 
 template <int Q, class R, bool EXACT>
 __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
-                                         LinCell<Q, R, EXACT>& c) {
+                                         LinCell<Q, R, EXACT>& c, const R (&mu)[Q]) {
   const R* rec = static_cast<const R*>(a.rec);
   const long long rp = a.rec_pitch;
   c.d = d;
   R drho = 0;
+  R gb[EXACT ? Q : 1];
   if constexpr (!EXACT) {
     c.rho = rec[cell];
     c.u.x = rec[rp + cell];
@@ -56,7 +58,6 @@ __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R
     c.om = rec[(Lat<Q>::D + 1) * rp + cell];
   } else {
     // the record holds f_bar - w
-    R gb[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) gb[i] = rec[(long long)i * rp + cell];
     Vec3<R> m;
@@ -68,10 +69,14 @@ __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R
   c.ut = Vec3<R>{d * c.u.x + one_d * us.x, d * c.u.y + one_d * us.y, d * c.u.z + one_d * us.z};
   if constexpr (EXACT) {
     const R uu = dot3(c.ut, c.ut);
+    c.P = Sym<R>{0, 0, 0, 0, 0, 0};
+    c.sn = 0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-      c.fneq[i] = rec[(long long)i * rp + cell] - geq_i<Q>(i, drho, c.rho, c.ut, uu);
-    c.P = second_moment<Q, R>(c.fneq);
+    for (int i = 0; i < Q; ++i) {
+      const R fn = gb[i] - geq_i<Q>(i, drho, c.rho, c.ut, uu);
+      sym_add_xixi<Q>(c.P, i, fn);
+      c.sn += mu[i] * fn;
+    }
     c.nP = sqrt_r<R>(sym_norm2(c.P));
     c.tau = tau_smagorinsky<R>(par<R>(a.tau_b, a.tau_b_f), par<R>(a.kles, a.kles_f), c.nP);
     c.om = R(1) / c.tau;
@@ -115,11 +120,8 @@ __device__ __forceinline__ void transpose_collide(const LinCell<Q, R, EXACT>& c,
   R uPu = 0, trP = 0, uPU = 0;
   if constexpr (EXACT) {
     if (c.nP > pi_eps<R>()) {
-      R sn = 0;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) sn += mu[i] * c.fneq[i];
       // sum mu_i (f^eq_i - f_i) = -sn
-      E = om * om * sn * par<R>(a.kles, a.kles_f) /
+      E = om * om * c.sn * par<R>(a.kles, a.kles_f) /
           ((R(2) * c.tau - par<R>(a.tau_b, a.tau_b_f)) * c.nP);
     }
     PU = sym_mul(c.P, c.ut);
@@ -192,6 +194,13 @@ __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R
     c.tau = tau_smagorinsky<R>(par<R>(a.tau_b, a.tau_b_f), par<R>(a.kles, a.kles_f), c.nP);
     c.om = R(1) / c.tau;
   }
+}
+
+// the regularised record does not depend on mu (same call shape as the BGK one)
+template <int Q, class R, bool EXACT>
+__device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
+                                         RRCell<R, EXACT>& c, const R (&)[Q]) {
+  load_lin<Q, R, EXACT>(a, cell, d, c);
 }
 
 template <int Q, class R>
@@ -338,7 +347,7 @@ __device__ __forceinline__ void add_source(const AdjointArgs& a, int x, int y, i
         if (ex) t += c[S0];
         if (ey) t += c[S0 + 1];
         if constexpr (D == 2) {
-          if (ex && ey) t += (ex * ey > 0) ? R(2) * c[4] : -R(2) * c[4];
+          if (ex && ey) t += (ex * ey > 0) ? R(2) * c[5] : -R(2) * c[5];
         } else {
           if (ez) t += c[S0 + 2];
           if (ex && ey) t += (ex * ey > 0) ? R(2) * c[7] : -R(2) * c[7];
@@ -412,7 +421,7 @@ __device__ __forceinline__ void adjoint_body(const AdjointArgs& a, int bxi, int 
     R v[Q];
     aa_load<Q, S, ODD, -1>(A, g, rows, x, cell, v);
     typename CellOf<Q, R, EXACT, RR>::T c;
-    load_lin<Q, R, EXACT>(a, cell, dp[cell], c);
+    load_lin<Q, R, EXACT>(a, cell, dp[cell], c, v);
     transpose_collide<Q, R, EXACT>(c, v, a);
     add_source<Q, R>(a, x, y, z, v);
     residual_io<Q, R, RES>(a, cell, v, rp);
@@ -420,7 +429,7 @@ __device__ __forceinline__ void adjoint_body(const AdjointArgs& a, int bxi, int 
       R vo[Q];
       aa_load<Q, S, ODD, -1>(A, g, rows, x + 1, cell + 1, vo);
       typename CellOf<Q, R, EXACT, RR>::T co;
-      load_lin<Q, R, EXACT>(a, cell + 1, dp[cell + 1], co);
+      load_lin<Q, R, EXACT>(a, cell + 1, dp[cell + 1], co, vo);
       transpose_collide<Q, R, EXACT>(co, vo, a);
       add_source<Q, R>(a, x + 1, y, z, vo);
       residual_io<Q, R, RES>(a, cell + 1, vo, rp);
@@ -809,7 +818,7 @@ __global__ void __launch_bounds__(NT) k_gradient(GradArgs ga) {
     val = dot3(gut, v);
   } else {
     LinCell<Q, R, EXACT> c;
-    load_lin<Q, R, EXACT>(a, cell, static_cast<const R*>(ga.d)[cell], c);
+    load_lin<Q, R, EXACT>(a, cell, static_cast<const R*>(ga.d)[cell], c, mu);
     R s0, m0;
     Vec3<R> s;
     contract<Q, R>(mu, c.ut, s0, s, m0);
@@ -819,12 +828,9 @@ __global__ void __launch_bounds__(NT) k_gradient(GradArgs ga) {
     val = c.om * c.rho * dot3(gv, v);
     if constexpr (EXACT) {
       if (c.nP > pi_eps<R>()) {
-        R sn = 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) sn += mu[i] * c.fneq[i];
         const R pdd = -R(2) * c.rho * dot3(v, sym_mul(c.P, c.ut));
         // (sum mu (feq - f)) * (-om^2) * k pdd / ((2 tau - tau_b) |Pi|)
-        val += sn * c.om * c.om * par<R>(ga.kles, ga.kles_f) * pdd /
+        val += c.sn * c.om * c.om * par<R>(ga.kles, ga.kles_f) * pdd /
                ((R(2) * c.tau - par<R>(ga.tau_b, ga.tau_b_f)) * c.nP);
       }
     }
