@@ -302,15 +302,54 @@ __device__ __forceinline__ void transpose_collide(const RRCell<R, EXACT>& c, R (
 template <int Q, class R, bool EXACT, bool RR> struct CellOf { using T = LinCell<Q, R, EXACT>; };
 template <int Q, class R, bool EXACT> struct CellOf<Q, R, EXACT, true> { using T = RRCell<R, EXACT>; };
 
+// v += g_bar at one cell from the coefficients c of the objective's derivative
+// polynomial in xi (nc = 2: J_FFA, c0 + c1 xi_x; otherwise J_DISS,
+// c0 + c . xi + xi . C . xi with the squares, then the doubled cross terms, in
+// the order of coef_basis)
+template <int Q, class R>
+__device__ __forceinline__ void expand_source(int nc, const R* c, R (&v)[Q]) {
+  using L = Lat<Q>;
+  constexpr int D = L::D;
+  if (nc == 2) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      R t = c[0];
+      if (L::cx(i)) t += L::cx(i) > 0 ? c[1] : -c[1];
+      v[i] += t;
+    }
+    return;
+  }
+  constexpr int S0 = 1 + D;  // first square coefficient
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int ex = L::cx(i), ey = L::cy(i), ez = L::cz(i);
+    R t = c[0];
+    if (ex) t += ex > 0 ? c[1] : -c[1];
+    if (ey) t += ey > 0 ? c[2] : -c[2];
+    if constexpr (D == 3) {
+      if (ez) t += ez > 0 ? c[3] : -c[3];
+    }
+    if (ex) t += c[S0];
+    if (ey) t += c[S0 + 1];
+    if constexpr (D == 2) {
+      if (ex && ey) t += (ex * ey > 0) ? R(2) * c[S0 + 2] : -R(2) * c[S0 + 2];
+    } else {
+      if (ez) t += c[S0 + 2];
+      if (ex && ey) t += (ex * ey > 0) ? R(2) * c[S0 + 3] : -R(2) * c[S0 + 3];
+      if (ex && ez) t += (ex * ez > 0) ? R(2) * c[S0 + 4] : -R(2) * c[S0 + 4];
+      if (ey && ez) t += (ey * ez > 0) ? R(2) * c[S0 + 5] : -R(2) * c[S0 + 5];
+    }
+    v[i] += t;
+  }
+}
+
 // lam += g_bar in the source box.  J_FFA and J_DISS store g_bar as the
 // coefficients of their derivative polynomials in xi (2 or 1 + D + D(D+1)/2 per
-// cell instead of q values) and the values are formed here, in the order of
-// coef_basis; J_MEA stores the q values.
+// cell instead of q values), expanded here; J_MEA stores the q values.
 template <int Q, class R>
 __device__ __forceinline__ void add_source(const AdjointArgs& a, int x, int y, int z, R (&v)[Q]) {
   if (x >= a.sb[0] && x < a.sb[1] && y >= a.sb[2] && y < a.sb[3] && z >= a.sb[4] && z < a.sb[5]) {
-    using L = Lat<Q>;
-    constexpr int D = L::D;
+    constexpr int D = Lat<Q>::D;
     const long long bc = (long long)(x - a.sb[0]) +
                          (long long)(a.sb[1] - a.sb[0]) *
                              ((long long)(y - a.sb[2]) + (long long)(a.sb[3] - a.sb[2]) * (z - a.sb[4]));
@@ -319,43 +358,13 @@ __device__ __forceinline__ void add_source(const AdjointArgs& a, int x, int y, i
     if (a.src_nc == 0) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) v[i] += src[(long long)i * sp + bc];
-    } else if (a.src_nc == 2) {
-      // J_FFA: c0 + c1 xi_x
-      const R c0 = src[bc], c1 = src[sp + bc];
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        R t = c0;
-        if (L::cx(i)) t += L::cx(i) > 0 ? c1 : -c1;
-        v[i] += t;
-      }
     } else {
-      // J_DISS: c0 + c . xi + xi . C . xi (squares, then doubled cross terms)
-      constexpr int NC = 1 + D + D * (D + 1) / 2;
-      R c[NC];
+      R c[1 + D + D * (D + 1) / 2];
+      const int nc = a.src_nc;
 #pragma unroll
-      for (int k = 0; k < NC; ++k) c[k] = src[(long long)k * sp + bc];
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const int ex = L::cx(i), ey = L::cy(i), ez = L::cz(i);
-        R t = c[0];
-        if (ex) t += ex > 0 ? c[1] : -c[1];
-        if (ey) t += ey > 0 ? c[2] : -c[2];
-        if constexpr (D == 3) {
-          if (ez) t += ez > 0 ? c[3] : -c[3];
-        }
-        constexpr int S0 = 1 + D;  // first square coefficient
-        if (ex) t += c[S0];
-        if (ey) t += c[S0 + 1];
-        if constexpr (D == 2) {
-          if (ex && ey) t += (ex * ey > 0) ? R(2) * c[5] : -R(2) * c[5];
-        } else {
-          if (ez) t += c[S0 + 2];
-          if (ex && ey) t += (ex * ey > 0) ? R(2) * c[7] : -R(2) * c[7];
-          if (ex && ez) t += (ex * ez > 0) ? R(2) * c[8] : -R(2) * c[8];
-          if (ey && ez) t += (ey * ez > 0) ? R(2) * c[9] : -R(2) * c[9];
-        }
-        v[i] += t;
-      }
+      for (int k = 0; k < 1 + D + D * (D + 1) / 2; ++k)
+        if (k < nc) c[k] = src[(long long)k * sp + bc];
+      expand_source<Q, R>(nc, c, v);
     }
   }
 }
@@ -626,20 +635,21 @@ __global__ void __launch_bounds__(NT) k_source(SourceArgs a) {
     const long long vol = (long long)bx * by * (a.box[5] - a.box[4]);
     const long long cell = cell_of(a.g, a.box[0] + xl, a.box[2] + yl, a.box[4] + zl);
     const int nc = ncoef(a.obj_slot, D);
-    R cf[10];
+    R cf[1 + D + D * (D + 1) / 2];
     R* src = static_cast<R*>(a.src);
-    for (int k = 0; k < nc; ++k) {
+#pragma unroll
+    for (int k = 0; k < 1 + D + D * (D + 1) / 2; ++k) {
+      if (k >= nc) break;
       cf[k] = (R)(a.gsum[(long long)k * a.g.N + cell] * a.inv_n);
       src[(long long)k * vol + bc] = cf[k];
     }
     // ||g_bar||^2 of the values the sweep forms from these coefficients
+    R gv[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      double gv = 0.0;
-      for (int k = 0; k < nc; ++k)
-        gv += (double)cf[k] * coef_basis(a.obj_slot, D, k, Lat<Q>::cx(i), Lat<Q>::cy(i), Lat<Q>::cz(i));
-      acc += gv * gv;
-    }
+    for (int i = 0; i < Q; ++i) gv[i] = R(0);
+    expand_source<Q, R>(nc, cf, gv);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) acc += (double)gv[i] * (double)gv[i];
   }
   __shared__ double sh[NT / 32];
   const double s = block_sum<NT>(acc, sh);

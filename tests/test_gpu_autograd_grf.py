@@ -5,16 +5,17 @@ d = 1 outside; drag J_FFA on the plane x = 300 and dissipation J_DISS over
 the whole domain).
 
 * The gradient that ``torch.autograd`` returns through ``HLBMObjective``
-  (FP32 populations, steady primal, adjoint to 2e-5, the FP32 floor of its
-  update criterion here) against the FP64
+  (FP32 populations, steady primal, adjoint by GMRES to 2e-5, the FP32 floor
+  of its update criterion here) against the FP64
   oracle's gradient: the oracle's steady state by Newton steps with its exact
   step Jacobian and its adjoint by a sparse direct solve (Eq. gradients_steady).
-  Bound 1e-4 relative L2 over the whole domain.
+  Bound 2e-4 relative L2 over the whole domain (FP32), 1e-6 for the same
+  path in FP64.
 * The same gradient against central differences of J (h = 1e-4) on 32 seeded
   cells of the design box, J evaluated with FP64 populations (FP32 would
-  cancel in the difference): 400 000 steps to the unperturbed steady state,
-  then 200 000 steps from it to each perturbed one (the slowest transient of
-  this case decays by about e^-10 over that stretch).
+  cancel in the difference): 1 000 000 steps to the unperturbed steady
+  state, then 200 000 steps from it to each perturbed one (the slowest
+  transient of this case decays by about e^-10 over that stretch).
 
 The oracle runs in a spawned process while the GPU works."""
 import concurrent.futures as cf
@@ -32,10 +33,17 @@ from paper_2606_31707_b300.autograd import HLBMObjective, PrimalSpec  # noqa: E4
 from tests.hlbm_cases import oracle_grf_gradients  # noqa: E402
 from workloads import Regions, make_workload  # noqa: E402
 
-TOL_ORACLE = 1e-4
-# the update criterion of the FP32 fixed-point iteration stalls near 1e-5 on
-# this case (the rounding of the FP32 adjoint populations): its tolerance
+# This steady case contracts slowly (the adjoint iteration needs ~6e5 sweeps
+# in FP64): FP32 rounding of the state and of the adjoint populations is
+# amplified to about 1e-4 of the gradient, so the FP32 bound against the oracle
+# is 2e-4; the FP64 path (same kernels in FP64) is held to 1e-6.
+TOL_ORACLE = 2e-4
+TOL_ORACLE_FP64 = 1e-6
+# the update criterion of an FP32 solve stalls near 1e-5 here (the rounding
+# of the FP32 adjoint populations): its tolerance; GMRES (the same fixed point)
+# reaches it in ~4e4 sweeps where the fixed-point iteration needs ~2e6
 TOL_ADJ_FP32 = 2e-5
+PRIMAL_STEPS = 1_000_000  # to the steady state (J converged to ~1e-12 in FP64)
 H_FD = 1e-4
 N_CELLS = 32
 
@@ -59,7 +67,7 @@ def oracle_future():
     ex.shutdown(wait=True)
 
 
-STEADY_STEPS = 400_000   # FP64 primal steps to the unperturbed steady state
+STEADY_STEPS = PRIMAL_STEPS   # FP64 primal steps to the unperturbed steady state
 FD_STEPS = 200_000       # steps from that state to each perturbed one
 
 
@@ -120,9 +128,10 @@ def test_autograd_grf_gradient_against_oracle_and_central_differences(oracle_fut
     dev = torch.device("cuda", 0)
     R = _regions(wl)
     tau = _tau0(wl)
-    # autograd, FP32 populations
-    s32 = Solver(9, wl.dims, tau, 0.0, storage=H.FP32, u_in=wl.u0, regions=R)
-    spec = PrimalSpec(steps=200000, avg_window=1, objective=objective, tol=TOL_ADJ_FP32,
+    # autograd, FP32 populations, the adjoint by GMRES on the same fixed point
+    s32 = Solver(9, wl.dims, tau, 0.0, storage=H.FP32, u_in=wl.u0, regions=R, adjoint_solver=1,
+                 gmres_restart=40, gmres_inner=100)
+    spec = PrimalSpec(steps=PRIMAL_STEPS, avg_window=1, objective=objective, tol=TOL_ADJ_FP32,
                       max_iter=1_000_000)
     dt = torch.from_numpy(wl.porosity.astype(np.float32)).to(dev).requires_grad_(True)
     J32 = HLBMObjective.apply(dt, s32, spec)
@@ -145,7 +154,17 @@ def test_autograd_grf_gradient_against_oracle_and_central_differences(oracle_fut
     G_ref, J_ref = ref[key]
     rel = float(np.linalg.norm(G - G_ref) / np.linalg.norm(G_ref))
     assert rel <= TOL_ORACLE, rel
-    assert abs(cd["J0"][objective] - J_ref) <= 1e-8 * abs(J_ref)
-    print(f"GRF case objective {objective}: autograd vs oracle rel L2 {rel:.2e}, "
-          f"vs central differences {worst:.2e} of max|G|, adjoint {it} sweeps to {res:.1e}, "
-          f"J drift of the FP64 steady state {cd['drift'][objective]:.1e}")
+    assert abs(cd["J0"][objective] - J_ref) <= 1e-10 * abs(J_ref)
+    # the same autograd path in FP64
+    s64 = Solver(9, wl.dims, tau, 0.0, storage=H.FP64, u_in=wl.u0, regions=R)
+    spec64 = PrimalSpec(steps=PRIMAL_STEPS, avg_window=1, objective=objective, tol=1e-11,
+                        max_iter=3_000_000)
+    d64 = torch.from_numpy(wl.porosity).to(dev).requires_grad_(True)
+    HLBMObjective.apply(d64, s64, spec64).backward()
+    G64 = d64.grad.detach().cpu().numpy()
+    s64.close()
+    rel64 = float(np.linalg.norm(G64 - G_ref) / np.linalg.norm(G_ref))
+    assert rel64 <= TOL_ORACLE_FP64, rel64
+    print(f"GRF case objective {objective}: autograd FP32 vs oracle rel L2 {rel:.2e} (FP64 "
+          f"{rel64:.2e}), vs central differences {worst:.2e} of max|G|, adjoint {it} sweeps to "
+          f"{res:.1e}, J drift of the FP64 steady state {cd['drift'][objective]:.1e}")
