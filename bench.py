@@ -57,14 +57,16 @@ CS2 = 1.0 / 3.0
 # keyed by a hash of the kernel sources at capture time; a kernel changed since
 # its capture reports traffic null.  Summaries: profiles/*.md.
 MEASURED_DRAM = {
-    # ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the two AA parities
-    # (profiles/k_primal_karman2d_re100.md, k_adjoint_karman2d_re100.md,
-    # k_primal_rr_les3d_re3900.md)
-    ("31489d5ea0988b20", "karman2d_re100", "fp32", "bgk", "primal_step_accumulate"): 34_510_000,
-    ("31489d5ea0988b20", "karman2d_re100", "fp32", "bgk", "primal_step_plain"): 18_050_000,
-    ("31489d5ea0988b20", "karman2d_re100", "fp32", "bgk", "adjoint_step_ffa"): 30_270_000,
-    ("31489d5ea0988b20", "les3d_re3900", "fp32", "rr", "primal_step_accumulate"): 6_872_420_000,
-    ("31489d5ea0988b20", "les3d_re3900", "fp32", "rr", "primal_step_plain"): 3_138_120_000,
+    # captured on the 640x320x24 slab of the LES grid (the same x-y plane, 4.9 M
+    # cells, the same bytes per update to 0.01 %) and scaled to the 640x320x100
+    # grid by the cell ratio 100 / 24 (profiles/k_primal_les3d_re3900.md,
+    # k_adjoint_les3d_re3900.md)
+    ("195446bda78a4685", "les3d_re3900", "fp32", "bgk", "primal_step_accumulate"): 7_705_357_867,
+    ("195446bda78a4685", "les3d_re3900", "fp32", "bgk", "primal_step_plain"): 2_957_523_204,
+    ("195446bda78a4685", "les3d_re3900", "fp32", "bgk", "adjoint_step_ffa"): 4_610_731_602,
+    ("195446bda78a4685", "les3d_re3900", "fp32", "bgk", "adjoint_step_diss"): 5_296_040_512,
+    ("195446bda78a4685", "les3d_re3900_slab", "fp32", "bgk", "primal_step_accumulate"): 1_849_285_888,
+    ("195446bda78a4685", "les3d_re3900_slab", "fp32", "bgk", "primal_step_plain"): 709_805_000,
 }
 
 
