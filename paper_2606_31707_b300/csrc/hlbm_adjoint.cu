@@ -32,50 +32,71 @@ template <> __device__ __forceinline__ double pi_eps<double>() { return 1e-30; }
 template <> __device__ __forceinline__ float pi_eps<float>() { return 1e-20f; }
 
 // Linearisation point of one cell, derived from the record.
-template <int Q, class R, bool EXACT> struct LinCell {
+template <int Q, class R, bool EXACT, int NR = 1> struct LinCell {
   R rho, om, d;
   Vec3<R> u, ut;
-  // EXACT only: the non-equilibrium stress of f_bar, its norm, tau_eff, and
-  // sn = sum_i mu_i (f_bar_i - f^eq_i) for the mu this cell is processed with
-  // (formed here, so that no array of f^neq stays alive through the transpose)
+  // EXACT only: rho - 1, the non-equilibrium stress of f_bar, its norm,
+  // tau_eff, and sg[r] = sum_i mu_i (f_bar_i - w_i) for the mu of each
+  // right-hand side r this cell is processed with (f_bar itself is not kept
+  // through the transpose)
+  R drho;
   Sym<R> P;
-  R nP, tau, sn;
+  R nP, tau, sg[NR];
 };
 
-template <int Q, class R, bool EXACT>
+template <int Q, class R, bool EXACT, int NR>
 __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
-                                         LinCell<Q, R, EXACT>& c, const R (&mu)[Q]) {
+                                         LinCell<Q, R, EXACT, NR>& c, const R (&mu)[Q],
+                                         const R (&mu2)[Q]) {
+  constexpr int D = Lat<Q>::D;
   const R* rec = static_cast<const R*>(a.rec);
   const long long rp = a.rec_pitch;
   c.d = d;
-  R drho = 0;
   R gb[EXACT ? Q : 1];
+  Sym<R> M2;
   if constexpr (!EXACT) {
     c.rho = rec[cell];
     c.u.x = rec[rp + cell];
     c.u.y = rec[2 * rp + cell];
-    c.u.z = Lat<Q>::D == 3 ? rec[3 * rp + cell] : R(0);
-    c.om = rec[(Lat<Q>::D + 1) * rp + cell];
+    c.u.z = D == 3 ? rec[3 * rp + cell] : R(0);
+    c.om = rec[(D + 1) * rp + cell];
   } else {
-    // the record holds f_bar - w
+    // the record holds g = f_bar - w: rho - 1 = sum g, rho u = sum xi g,
+    // M2 = sum xi xi g
 #pragma unroll
     for (int i = 0; i < Q; ++i) gb[i] = rec[(long long)i * rp + cell];
-    Vec3<R> m;
-    moments_dev<Q>(gb, drho, c.rho, m, c.u);
+    Mom<R> ax, dg;
+    class_moments<Q, R>(gb, ax, dg);
+    c.drho = gb[0] + ax.m0 + dg.m0;
+    c.rho = R(1) + c.drho;
+    const R inv = R(1) / c.rho;
+    c.u = Vec3<R>{(ax.m1.x + dg.m1.x) * inv, (ax.m1.y + dg.m1.y) * inv,
+                  D == 3 ? (ax.m1.z + dg.m1.z) * inv : R(0)};
+    M2 = Sym<R>{ax.m2.xx + dg.m2.xx, ax.m2.yy + dg.m2.yy, ax.m2.zz + dg.m2.zz, dg.m2.xy,
+                dg.m2.xz, dg.m2.yz};
   }
   const R one_d = R(1) - d;
   const Vec3<R> us{par<R>(a.us[0], a.us_f[0]), par<R>(a.us[1], a.us_f[1]),
                    par<R>(a.us[2], a.us_f[2])};
   c.ut = Vec3<R>{d * c.u.x + one_d * us.x, d * c.u.y + one_d * us.y, d * c.u.z + one_d * us.z};
   if constexpr (EXACT) {
-    const R uu = dot3(c.ut, c.ut);
-    c.P = Sym<R>{0, 0, 0, 0, 0, 0};
-    c.sn = 0;
+    // Pi = sum xi xi (f_bar - f^eq(rho, u~)) = M2 - (rho - 1)/3 I - rho u~ u~: the
+    // lattice sums of f^eq - w are (rho - 1) c_s^2 I + rho u~ u~ on both lattices
+    const R t = c.drho * R(1.0 / 3.0);
+    const Vec3<R>& w = c.ut;
+    c.P = Sym<R>{M2.xx - t - c.rho * w.x * w.x, M2.yy - t - c.rho * w.y * w.y,
+                 D == 3 ? M2.zz - t - c.rho * w.z * w.z : R(0), M2.xy - c.rho * w.x * w.y,
+                 D == 3 ? M2.xz - c.rho * w.x * w.z : R(0),
+                 D == 3 ? M2.yz - c.rho * w.y * w.z : R(0)};
+    R sg = mu[0] * gb[0];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const R fn = gb[i] - geq_i<Q>(i, drho, c.rho, c.ut, uu);
-      sym_add_xixi<Q>(c.P, i, fn);
-      c.sn += mu[i] * fn;
+    for (int i = 1; i < Q; ++i) sg += mu[i] * gb[i];
+    c.sg[0] = sg;
+    if constexpr (NR == 2) {
+      R sg2 = mu2[0] * gb[0];
+#pragma unroll
+      for (int i = 1; i < Q; ++i) sg2 += mu2[i] * gb[i];
+      c.sg[1] = sg2;
     }
     c.nP = sqrt_r<R>(sym_norm2(c.P));
     c.tau = tau_smagorinsky<R>(par<R>(a.tau_b, a.tau_b_f), par<R>(a.kles, a.kles_f), c.nP);
@@ -83,61 +104,92 @@ __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R
   }
 }
 
-// s0 = sum w_i mu_i, s = sum w_i mu_i xi_i (3 + 9 xi_i.u~), m0 = sum mu_i f^eq_i / rho
-template <int Q, class R>
-__device__ __forceinline__ void contract(const R (&mu)[Q], const Vec3<R>& ut, R& s0, Vec3<R>& s,
-                                         R& m0) {
-  using L = Lat<Q>;
-  const R uu = dot3(ut, ut);
-  s0 = 0;
-  m0 = 0;
-  s = Vec3<R>{0, 0, 0};
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const R cu = xi_dot<Q>(i, ut);
-    const R wm = R(L::w(i)) * mu[i];
-    s0 += wm;
-    m0 += wm * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-    const R t = wm * (R(3) + R(9) * cu);
-    if (L::cx(i)) s.x += L::cx(i) > 0 ? t : -t;
-    if (L::cy(i)) s.y += L::cy(i) > 0 ? t : -t;
-    if (L::cz(i)) s.z += L::cz(i) > 0 ? t : -t;
-  }
+template <int Q, class R, bool EXACT>
+__device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
+                                         LinCell<Q, R, EXACT, 1>& c, const R (&mu)[Q]) {
+  load_lin<Q, R, EXACT, 1>(a, cell, d, c, mu, mu);
 }
 
-// lam = C_f^T mu + g at one cell (mu is overwritten with lam)
-template <int Q, class R, bool EXACT>
-__device__ __forceinline__ void transpose_collide(const LinCell<Q, R, EXACT>& c, R (&mu)[Q],
-                                                  const AdjointArgs& a) {
-  R s0, m0;
-  Vec3<R> s;
-  contract<Q, R>(mu, c.ut, s0, s, m0);
-  const Vec3<R> gv{s.x - R(3) * c.ut.x * s0, s.y - R(3) * c.ut.y * s0, s.z - R(3) * c.ut.z * s0};
-  const R ug = dot3(c.u, gv);
-  const R om = c.om;
-  R E = 0;
-  Vec3<R> PU{0, 0, 0};
-  R uPu = 0, trP = 0, uPU = 0;
+// Contractions of mu at the linearisation point, from the weighted moments
+// a0 = sum w mu, a1 = sum w mu xi, A2 = sum w mu xi xi (c_i = xi_i . u~):
+//   m0 = sum mu_i f^eq_i / rho = a0 (1 - 3/2 u~.u~) + 3 a1.u~ + 9/2 u~.A2.u~
+//   qe = sum mu_i (f^eq_i - w_i) = (rho - 1) a0 + rho (m0 - a0)
+//   gv = sum w mu (3 xi + 9 c xi) - 3 u~ a0 = 3 a1 + 9 A2 u~ - 3 u~ a0
+template <class R> struct MuC { R m0, qe; Vec3<R> gv; };
+
+template <int Q, class R>
+__device__ __forceinline__ MuC<R> mu_contract(const R (&mu)[Q], const Vec3<R>& ut, R drho,
+                                              R rho) {
+  using L = Lat<Q>;
+  constexpr int D = L::D;
+  Mom<R> ax, dg;
+  class_moments<Q, R>(mu, ax, dg);
+  const R wa = R(L::w(1)), wd = R(L::w(Q - 1));
+  const R a0 = R(L::w(0)) * mu[0] + wa * ax.m0 + wd * dg.m0;
+  const Vec3<R> a1{wa * ax.m1.x + wd * dg.m1.x, wa * ax.m1.y + wd * dg.m1.y,
+                   D == 3 ? wa * ax.m1.z + wd * dg.m1.z : R(0)};
+  const Sym<R> A2{wa * ax.m2.xx + wd * dg.m2.xx, wa * ax.m2.yy + wd * dg.m2.yy,
+                  D == 3 ? wa * ax.m2.zz + wd * dg.m2.zz : R(0), wd * dg.m2.xy,
+                  D == 3 ? wd * dg.m2.xz : R(0), D == 3 ? wd * dg.m2.yz : R(0)};
+  Vec3<R> A2u;
+  if constexpr (D == 3) {
+    A2u = sym_mul(A2, ut);
+  } else {
+    A2u = Vec3<R>{A2.xx * ut.x + A2.xy * ut.y, A2.xy * ut.x + A2.yy * ut.y, R(0)};
+  }
+  const R uu = dot3(ut, ut);
+  const R a1u = D == 3 ? dot3(a1, ut) : a1.x * ut.x + a1.y * ut.y;
+  const R uAu = D == 3 ? dot3(ut, A2u) : ut.x * A2u.x + ut.y * A2u.y;
+  const R h = R(3) * a1u + R(4.5) * uAu - R(1.5) * uu * a0;
+  MuC<R> r;
+  r.m0 = a0 + h;
+  r.qe = drho * a0 + rho * h;
+  r.gv = Vec3<R>{R(3) * a1.x + R(9) * A2u.x - R(3) * ut.x * a0,
+                 R(3) * a1.y + R(9) * A2u.y - R(3) * ut.y * a0,
+                 R(3) * a1.z + R(9) * A2u.z - R(3) * ut.z * a0};
+  return r;
+}
+
+// lam = C_f^T mu + g at one cell (mu is overwritten with lam).  The transposed
+// collision is a quadratic polynomial in xi_j,
+//   lam_j = (1 - omega) mu_j + K0 + xi_j . K1 + xi_j . K2 . xi_j,
+//   K0 = omega (m0 - d u.gv) + E (2 d u.Pi u~ - u~.Pi u~ - tr Pi / 3),
+//   K1 = omega d gv - 2 d E Pi u~,   K2 = E Pi,
+// evaluated over opposite pairs (xi_opp = -xi: the K0 and K2 parts are shared,
+// the K1 part changes sign).
+template <int Q, class R, bool EXACT, int NR>
+__device__ __forceinline__ void transpose_collide(const LinCell<Q, R, EXACT, NR>& c, R (&mu)[Q],
+                                                  const AdjointArgs& a, int r = 0) {
+  const MuC<R> k = mu_contract<Q, R>(mu, c.ut, EXACT ? c.drho : c.rho - R(1), c.rho);
+  const R om = c.om, d = c.d;
+  const R ug = dot3(c.u, k.gv);
+  R K0 = om * (k.m0 - d * ug);
+  const R odg = om * d;
+  Vec3<R> K1{odg * k.gv.x, odg * k.gv.y, odg * k.gv.z};
+  Sym<R> K2{0, 0, 0, 0, 0, 0};
   if constexpr (EXACT) {
     if (c.nP > pi_eps<R>()) {
-      // sum mu_i (f^eq_i - f_i) = -sn
-      E = om * om * c.sn * par<R>(a.kles, a.kles_f) /
-          ((R(2) * c.tau - par<R>(a.tau_b, a.tau_b_f)) * c.nP);
+      // sum mu_i (f_bar_i - f^eq_i) = sg - qe
+      const R E = om * om * (c.sg[r] - k.qe) * par<R>(a.kles, a.kles_f) /
+                  ((R(2) * c.tau - par<R>(a.tau_b, a.tau_b_f)) * c.nP);
+      const Vec3<R> PU = sym_mul(c.P, c.ut);
+      const R uPu = dot3(c.ut, PU), uPU = dot3(c.u, PU);
+      const R trP = c.P.xx + c.P.yy + c.P.zz;
+      K0 += E * (R(2) * d * uPU - uPu - trP * R(1.0 / 3.0));
+      const R e2 = R(2) * d * E;
+      K1 = Vec3<R>{K1.x - e2 * PU.x, K1.y - e2 * PU.y, K1.z - e2 * PU.z};
+      K2 = Sym<R>{E * c.P.xx, E * c.P.yy, E * c.P.zz, E * c.P.xy, E * c.P.xz, E * c.P.yz};
     }
-    PU = sym_mul(c.P, c.ut);
-    uPu = dot3(c.ut, PU);
-    trP = c.P.xx + c.P.yy + c.P.zz;
-    uPU = dot3(c.u, PU);
   }
+  const R c1 = R(1) - om;
+  mu[0] = c1 * mu[0] + K0;
 #pragma unroll
-  for (int j = 0; j < Q; ++j) {
-    R v = (R(1) - om) * mu[j] + om * (m0 + c.d * (xi_dot<Q>(j, gv) - ug));
-    if constexpr (EXACT) {
-      const R pdp = xi_P_xi<Q>(j, c.P) - trP * R(1.0 / 3.0) - uPu -
-                    R(2) * c.d * (xi_dot<Q>(j, PU) - uPU);
-      v += E * pdp;
-    }
-    mu[j] = v;
+  for (int i = 1; i < Q; i += 2) {
+    R psi = K0;
+    if constexpr (EXACT) psi += xi_P_xi<Q>(i, K2);
+    const R phi = xi_dot<Q>(i, K1);
+    mu[i] = c1 * mu[i] + (psi + phi);
+    mu[i + 1] = c1 * mu[i + 1] + (psi - phi);
   }
 }
 
@@ -196,10 +248,15 @@ __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R
   }
 }
 
-// the regularised record does not depend on mu (same call shape as the BGK one)
+// the regularised record does not depend on mu (same call shapes as the BGK one)
 template <int Q, class R, bool EXACT>
 __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
                                          RRCell<R, EXACT>& c, const R (&)[Q]) {
+  load_lin<Q, R, EXACT>(a, cell, d, c);
+}
+template <int Q, class R, bool EXACT>
+__device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
+                                         RRCell<R, EXACT>& c, const R (&)[Q], const R (&)[Q]) {
   load_lin<Q, R, EXACT>(a, cell, d, c);
 }
 
@@ -295,12 +352,16 @@ __device__ __forceinline__ void rr_transpose(const RRCell<R, EXACT>& c, R (&mu)[
 
 template <int Q, class R, bool EXACT>
 __device__ __forceinline__ void transpose_collide(const RRCell<R, EXACT>& c, R (&mu)[Q],
-                                                  const AdjointArgs& a) {
+                                                  const AdjointArgs& a, int = 0) {
   rr_transpose<Q, R, EXACT>(c, mu, a, nullptr);
 }
 
-template <int Q, class R, bool EXACT, bool RR> struct CellOf { using T = LinCell<Q, R, EXACT>; };
-template <int Q, class R, bool EXACT> struct CellOf<Q, R, EXACT, true> { using T = RRCell<R, EXACT>; };
+template <int Q, class R, bool EXACT, bool RR, int NR = 1> struct CellOf {
+  using T = LinCell<Q, R, EXACT, NR>;
+};
+template <int Q, class R, bool EXACT, int NR> struct CellOf<Q, R, EXACT, true, NR> {
+  using T = RRCell<R, EXACT>;
+};
 
 // v += g_bar at one cell from the coefficients c of the objective's derivative
 // polynomial in xi (nc = 2: J_FFA, c0 + c1 xi_x; otherwise J_DISS,
@@ -346,8 +407,21 @@ __device__ __forceinline__ void expand_source(int nc, const R* c, R (&v)[Q]) {
 // lam += g_bar in the source box.  J_FFA and J_DISS store g_bar as the
 // coefficients of their derivative polynomials in xi (2 or 1 + D + D(D+1)/2 per
 // cell instead of q values), expanded here; J_MEA stores the q values.
+__device__ __forceinline__ AdjRhs rhs_of(const AdjointArgs& a) {
+  AdjRhs r;
+  r.lam = a.lam;
+  r.src = a.src;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.sb[k] = a.sb[k];
+  r.src_pitch = a.src_pitch;
+  r.src_nc = a.src_nc;
+  r.snap = a.snap;
+  r.red = a.red;
+  return r;
+}
+
 template <int Q, class R>
-__device__ __forceinline__ void add_source(const AdjointArgs& a, int x, int y, int z, R (&v)[Q]) {
+__device__ __forceinline__ void add_source(const AdjRhs& a, int x, int y, int z, R (&v)[Q]) {
   if (x >= a.sb[0] && x < a.sb[1] && y >= a.sb[2] && y < a.sb[3] && z >= a.sb[4] && z < a.sb[5]) {
     constexpr int D = Lat<Q>::D;
     const long long bc = (long long)(x - a.sb[0]) +
@@ -395,20 +469,25 @@ __device__ __forceinline__ void outlet_transpose(R (&th)[Q], const R (&lo)[Q], R
   for (int j = 0; j < Q; ++j) th[j] += (xi_dot<Q>(j, h) - uh) * inv;
 }
 
+// The squared update of every population is added to the thread's partial
+// without rounding error: FP64 sweeps add in FP64; FP32 sweeps add each square
+// to an unevaluated pair of floats (error-free TwoSum), which the block sums in
+// pairs and converts to FP64 once per warp.  (Differences and squares in FP64
+// made the comparing sweep FP64-bound: 3.5 ms against 1.1 ms for a plain sweep
+// on the LES grid.)
 template <int Q, class R, int RES>
-__device__ __forceinline__ void residual_io(const AdjointArgs& a, long long cell, const R (&v)[Q],
-                                            double& rp) {
+__device__ __forceinline__ void residual_io(const AdjRhs& a, long long pitch, long long cell,
+                                            const R (&v)[Q], typename JAcc<R>::T& rp) {
   if (RES == 0) return;
   R* sn = static_cast<R*>(a.snap);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    R* p = sn + (long long)i * a.g.pitch + cell;
+    R* p = sn + (long long)i * pitch + cell;
     if (RES == 1) {
       *p = v[i];
     } else {
-      // squared update in FP64 (only the comparing sweep, once per check interval)
-      const double dlt = (double)v[i] - (double)*p;
-      rp += dlt * dlt;
+      const R dlt = v[i] - *p;
+      jadd(rp, dlt * dlt);
     }
   }
 }
@@ -423,25 +502,26 @@ __device__ __forceinline__ void adjoint_body(const AdjointArgs& a, int bxi, int 
   const int x = bxi * blockDim.x + threadIdx.x;
   R* A = static_cast<R*>(a.lam);
   const R* dp = static_cast<const R*>(a.d);
-  double rp = 0.0;
+  typename JAcc<R>::T rp{};
   if (x < g.nx - 1) {
     const long long cell = cell_of(g, x, y, z);
     const Rows rows = make_rows<Lat<Q>::D>(g, y, z);
     R v[Q];
     aa_load<Q, S, ODD, -1>(A, g, rows, x, cell, v);
     typename CellOf<Q, R, EXACT, RR>::T c;
+    const AdjRhs r0 = rhs_of(a);
     load_lin<Q, R, EXACT>(a, cell, dp[cell], c, v);
     transpose_collide<Q, R, EXACT>(c, v, a);
-    add_source<Q, R>(a, x, y, z, v);
-    residual_io<Q, R, RES>(a, cell, v, rp);
+    add_source<Q, R>(r0, x, y, z, v);
+    residual_io<Q, R, RES>(r0, g.pitch, cell, v, rp);
     if (x == g.nx - 2) {
       R vo[Q];
       aa_load<Q, S, ODD, -1>(A, g, rows, x + 1, cell + 1, vo);
       typename CellOf<Q, R, EXACT, RR>::T co;
       load_lin<Q, R, EXACT>(a, cell + 1, dp[cell + 1], co, vo);
       transpose_collide<Q, R, EXACT>(co, vo, a);
-      add_source<Q, R>(a, x + 1, y, z, vo);
-      residual_io<Q, R, RES>(a, cell + 1, vo, rp);
+      add_source<Q, R>(r0, x + 1, y, z, vo);
+      residual_io<Q, R, RES>(r0, g.pitch, cell + 1, vo, rp);
       outlet_transpose<Q, R>(v, vo, c.rho, c.u);
 #pragma unroll
       for (int i = 0; i < Q; ++i) vo[i] = R(0);
@@ -465,14 +545,16 @@ __device__ __forceinline__ void adjoint_body(const AdjointArgs& a, int bxi, int 
 // 120 registers.  Chosen by timing sweeps on the LES case (640x320x100):
 //   BGK exact LES: none 1419 us, 4 blocks 1262, 5: 1270; again with the
 //     slice of the benchmark (J_FFA / J_DISS sweeps, GLUPS): 3: 16.1 / 12.9,
-//     4: 18.4 / 14.9, 5: 18.9 / 15.4, 6: 17.9 / 14.7
+//     4: 18.4 / 14.9, 5: 18.9 / 15.4, 6: 17.9 / 14.7; with the transposed
+//     collision written through the weighted moments of mu: none 23.4 / 19.4,
+//     4: 23.0 / 18.9, 5: 23.3 / 19.5, 6: 24.3 / 20.6
 //   RR exact:      none 1265, 4: 1154, 5: 1091
 //   RR frozen:     none 1167, 5: 1057, 6: 1043
 #ifndef HLBM_AMINB_D3Q19
 #define HLBM_AMINB_D3Q19 0
 #endif
 #ifndef HLBM_AMINB_D3Q19_EXACT
-#define HLBM_AMINB_D3Q19_EXACT 5
+#define HLBM_AMINB_D3Q19_EXACT 6
 #endif
 #ifndef HLBM_AMINB_D3Q19_RR
 #define HLBM_AMINB_D3Q19_RR 6
@@ -566,6 +648,129 @@ cudaError_t launch_adjoint(const AdjointArgs& a, int q, bool dbl, bool odd, bool
                            bool rr, cudaStream_t s) {
   return rr ? launch_adj_c<true>(a, q, dbl, odd, exact, res, s)
             : launch_adj_c<false>(a, q, dbl, odd, exact, res, s);
+}
+
+// ----------------------------------------------------------------------------
+// Paired sweep: the adjoints of two objectives about the same averaged state
+// (J_FFA and J_DISS share the linearisation record and the porosity), one
+// cell update each with the arithmetic of the single sweep, in one kernel:
+// the record and the porosity are read once for both.
+// ----------------------------------------------------------------------------
+template <int Q, class R, bool ODD, bool EXACT, int RES>
+__device__ __forceinline__ void adjoint_pair_body(const AdjointArgs& a, int bxi, int y, int z,
+                                                  long long blin) {
+  constexpr int S = RealStore<R>::S;
+  const Grid& g = a.g;
+  const int x = bxi * blockDim.x + threadIdx.x;
+  R* A0 = static_cast<R*>(a.lam);
+  R* A1 = static_cast<R*>(a.two.lam);
+  const R* dp = static_cast<const R*>(a.d);
+  typename JAcc<R>::T rp0{}, rp1{};
+  if (x < g.nx - 1) {
+    const long long cell = cell_of(g, x, y, z);
+    const Rows rows = make_rows<Lat<Q>::D>(g, y, z);
+    const AdjRhs r0 = rhs_of(a);
+    R v[Q], w[Q];
+    aa_load<Q, S, ODD, -1>(A0, g, rows, x, cell, v);
+    aa_load<Q, S, ODD, -1>(A1, g, rows, x, cell, w);
+    LinCell<Q, R, EXACT, 2> c;
+    load_lin<Q, R, EXACT, 2>(a, cell, dp[cell], c, v, w);
+    transpose_collide<Q, R, EXACT>(c, v, a, 0);
+    add_source<Q, R>(r0, x, y, z, v);
+    residual_io<Q, R, RES>(r0, g.pitch, cell, v, rp0);
+    transpose_collide<Q, R, EXACT>(c, w, a, 1);
+    add_source<Q, R>(a.two, x, y, z, w);
+    residual_io<Q, R, RES>(a.two, g.pitch, cell, w, rp1);
+    if (x == g.nx - 2) {
+      // the outflow column: its own cell update, folded into column nx - 2
+      R vo[Q], wo[Q];
+      aa_load<Q, S, ODD, -1>(A0, g, rows, x + 1, cell + 1, vo);
+      aa_load<Q, S, ODD, -1>(A1, g, rows, x + 1, cell + 1, wo);
+      LinCell<Q, R, EXACT, 2> co;
+      load_lin<Q, R, EXACT, 2>(a, cell + 1, dp[cell + 1], co, vo, wo);
+      transpose_collide<Q, R, EXACT>(co, vo, a, 0);
+      add_source<Q, R>(r0, x + 1, y, z, vo);
+      residual_io<Q, R, RES>(r0, g.pitch, cell + 1, vo, rp0);
+      transpose_collide<Q, R, EXACT>(co, wo, a, 1);
+      add_source<Q, R>(a.two, x + 1, y, z, wo);
+      residual_io<Q, R, RES>(a.two, g.pitch, cell + 1, wo, rp1);
+      outlet_transpose<Q, R>(v, vo, c.rho, c.u);
+      outlet_transpose<Q, R>(w, wo, c.rho, c.u);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) vo[i] = R(0);
+      aa_store<Q, S, ODD, -1>(A0, g, rows, x + 1, cell + 1, vo);
+      aa_store<Q, S, ODD, -1>(A1, g, rows, x + 1, cell + 1, vo);
+    }
+    if (x == 0) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        v[i] = R(0);
+        w[i] = R(0);
+      }
+    }
+    aa_store<Q, S, ODD, -1>(A0, g, rows, x, cell, v);
+    aa_store<Q, S, ODD, -1>(A1, g, rows, x, cell, w);
+  }
+  if (RES == 2) {
+    __shared__ double sh[NT / 32];
+    const double s0 = block_sum<NT>(rp0, sh);
+    if (threadIdx.x == 0) a.red[blin] = s0;
+    __syncthreads();
+    const double s1 = block_sum<NT>(rp1, sh);
+    if (threadIdx.x == 0) a.two.red[blin] = s1;
+  }
+}
+
+// resident blocks per SM requested for the FP32 D3Q19 paired sweeps (0: none)
+#ifndef HLBM_AMINB_PAIR_D3Q19
+#define HLBM_AMINB_PAIR_D3Q19 0
+#endif
+#ifndef HLBM_AMINB_PAIR_D3Q19_EXACT
+#define HLBM_AMINB_PAIR_D3Q19_EXACT 4
+#endif
+template <int Q, class R, bool EXACT>
+constexpr int adjoint_pair_min_blocks() {
+  if (Q != 19 || sizeof(R) != 4) return 0;
+  return EXACT ? HLBM_AMINB_PAIR_D3Q19_EXACT : HLBM_AMINB_PAIR_D3Q19;
+}
+
+template <int Q, class R, bool ODD, bool EXACT, int RES>
+__global__ void __launch_bounds__(NT) k_adjoint_pair(AdjointArgs a) {
+  adjoint_pair_body<Q, R, ODD, EXACT, RES>(a, blockIdx.x, blockIdx.y, blockIdx.z, block_linear());
+}
+template <int Q, class R, bool ODD, bool EXACT, int RES, int MB>
+__global__ void __launch_bounds__(NT, MB) k_adjoint_pair_mb(AdjointArgs a) {
+  adjoint_pair_body<Q, R, ODD, EXACT, RES>(a, blockIdx.x, blockIdx.y, blockIdx.z, block_linear());
+}
+
+template <int Q, class R, bool ODD, bool EXACT, int RES>
+static void launch_pair_one(const AdjointArgs& a, dim3 grid, int bx, cudaStream_t s) {
+  constexpr int mb = adjoint_pair_min_blocks<Q, R, EXACT>();
+  if constexpr (mb > 0) k_adjoint_pair_mb<Q, R, ODD, EXACT, RES, (mb > 0 ? mb : 1)><<<grid, bx, 0, s>>>(a);
+  else k_adjoint_pair<Q, R, ODD, EXACT, RES><<<grid, bx, 0, s>>>(a);
+}
+
+template <int Q, class R>
+static cudaError_t launch_pair_qr(const AdjointArgs& a, bool odd, bool exact, int res, cudaStream_t s) {
+  const int bx = a.g.bx;
+  dim3 grid((a.g.nx + bx - 1) / bx, a.g.ny, a.g.nz);
+#define HLBM_P(O, E, RS) launch_pair_one<Q, R, O, E, RS>(a, grid, bx, s)
+#define HLBM_PR(O, E) \
+  do { if (res == 0) HLBM_P(O, E, 0); else if (res == 1) HLBM_P(O, E, 1); else HLBM_P(O, E, 2); } while (0)
+  if (!odd) { if (!exact) HLBM_PR(false, false); else HLBM_PR(false, true); }
+  else      { if (!exact) HLBM_PR(true, false);  else HLBM_PR(true, true); }
+#undef HLBM_PR
+#undef HLBM_P
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_pair(const AdjointArgs& a, int q, bool dbl, bool odd, bool exact, int res,
+                                cudaStream_t s) {
+  if (q == 9) return dbl ? launch_pair_qr<9, double>(a, odd, exact, res, s)
+                         : launch_pair_qr<9, float>(a, odd, exact, res, s);
+  if (q == 19) return dbl ? launch_pair_qr<19, double>(a, odd, exact, res, s)
+                          : launch_pair_qr<19, float>(a, odd, exact, res, s);
+  return cudaErrorInvalidValue;
 }
 
 // ----------------------------------------------------------------------------
@@ -829,18 +1034,15 @@ __global__ void __launch_bounds__(NT) k_gradient(GradArgs ga) {
   } else {
     LinCell<Q, R, EXACT> c;
     load_lin<Q, R, EXACT>(a, cell, static_cast<const R*>(ga.d)[cell], c, mu);
-    R s0, m0;
-    Vec3<R> s;
-    contract<Q, R>(mu, c.ut, s0, s, m0);
+    const MuC<R> k = mu_contract<Q, R>(mu, c.ut, EXACT ? c.drho : c.rho - R(1), c.rho);
     const Vec3<R> v{c.u.x - par<R>(ga.us[0], ga.us_f[0]), c.u.y - par<R>(ga.us[1], ga.us_f[1]),
                     c.u.z - par<R>(ga.us[2], ga.us_f[2])};
-    const Vec3<R> gv{s.x - R(3) * c.ut.x * s0, s.y - R(3) * c.ut.y * s0, s.z - R(3) * c.ut.z * s0};
-    val = c.om * c.rho * dot3(gv, v);
+    val = c.om * c.rho * dot3(k.gv, v);
     if constexpr (EXACT) {
       if (c.nP > pi_eps<R>()) {
         const R pdd = -R(2) * c.rho * dot3(v, sym_mul(c.P, c.ut));
         // (sum mu (feq - f)) * (-om^2) * k pdd / ((2 tau - tau_b) |Pi|)
-        val += c.sn * c.om * c.om * par<R>(ga.kles, ga.kles_f) * pdd /
+        val += (c.sg[0] - k.qe) * c.om * c.om * par<R>(ga.kles, ga.kles_f) * pdd /
                ((R(2) * c.tau - par<R>(ga.tau_b, ga.tau_b_f)) * c.nP);
       }
     }

@@ -85,6 +85,7 @@ struct hlbm_ctx {
   unsigned* err_dev = nullptr;
   unsigned* err_host = nullptr;
   double* scal_dev = nullptr;
+  double* fin = nullptr;     // partials and ticket of launch_finalize_sum
   double* scal_host = nullptr;
   // staging
   double* stage = nullptr;
@@ -540,12 +541,14 @@ int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau, doub
   if (!c->f || !c->d) { hlbm_destroy(c); return HLBM_ENOMEM; }
   if (cudaMalloc(&c->err_dev, 64) != cudaSuccess || cudaMallocHost(&c->err_host, 64) != cudaSuccess ||
       cudaMalloc(&c->scal_dev, 64) != cudaSuccess || cudaMallocHost(&c->scal_host, 64) != cudaSuccess ||
+      cudaMalloc(&c->fin, kFinScratchBytes) != cudaSuccess ||
       cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
     cudaGetLastError();
     hlbm_destroy(c);
     return HLBM_ENOMEM;
   }
   cudaMemsetAsync(c->err_dev, 0, 64, c->stream);
+  cudaMemsetAsync(c->fin, 0, kFinScratchBytes, c->stream);
   // porosity 1 everywhere, uniform inflow equilibrium
   int rc = cuda_check(c, CNT(c, launch_fill_real)(c->d, real_is_double(c), c->g.N, 1.0, c->stream), "porosity");
   if (rc == HLBM_OK)
@@ -849,7 +852,7 @@ int hlbm_run_tangent(hlbm_ctx* c, long steps, const void* delta, int dtype, int 
   const bool les = c->Cs > 0.0;
   for (long n = 0; n < steps; ++n) {
     HLBM_TRY(c, CNT(c, launch_tangent)(a, c->q, c->storage, c->phase == 1, les, c->stream), "tangent");
-    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, c->nblk, c->jhist + n, c->stream), "reduce");
+    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, c->nblk, c->jhist + n, c->fin, c->stream), "reduce");
     c->phase ^= 1;
   }
   HLBM_TRY(c, cudaMemcpyAsync(jdot_out, c->jhist, (size_t)steps * 8, cudaMemcpyDeviceToHost, c->stream), "copy");
@@ -882,14 +885,14 @@ int hlbm_objective(hlbm_ctx* c, int obj, double* J) {
     int nb = 0;
     HLBM_TRY(c, CNT(c, launch_mea_eval)(c->fsum, 1.0 / (double)c->nsamples, c->d, c->g, c->q,
                                         real_is_double(c), c->red, c->red + nbm, &nb, c->stream), "mea");
-    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, nb, c->scal_dev, c->stream), "reduce");
-    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red + nbm, nb, c->scal_dev + 1, c->stream), "reduce");
+    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, nb, c->scal_dev, c->fin, c->stream), "reduce");
+    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red + nbm, nb, c->scal_dev + 1, c->fin, c->stream), "reduce");
     HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 16, cudaMemcpyDeviceToHost, c->stream), "copy");
     HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
     *J = c->scal_host[0] / (c->scal_host[1] > 0 ? c->scal_host[1] : 1.0);
     return HLBM_OK;
   }
-  HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->jblk[o], c->njslot, c->scal_dev, c->stream), "reduce");
+  HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->jblk[o], c->njslot, c->scal_dev, c->fin, c->stream), "reduce");
   HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
   HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
   *J = c->scal_host[0] / (double)c->nsamples;
@@ -1160,7 +1163,7 @@ static int adjoint_setup(hlbm_ctx* c, int obj, int mode, AdjSetup* out) {
     if (!c->fsum) return set_err(c, HLBM_ESTATE, "J_MEA needs the averaged f");
     HLBM_TRY(c, CNT(c, launch_mea_eval)(c->fsum, 1.0 / (double)c->nsamples, c->d, c->g, c->q, dbl,
                                         c->red, c->red + nb_src, &nbs, c->stream), "mea");
-    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red + nb_src, nbs, c->scal_dev, c->stream), "reduce");
+    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red + nb_src, nbs, c->scal_dev, c->fin, c->stream), "reduce");
     HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
     HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
     const double area = c->scal_host[0] > 0 ? c->scal_host[0] : 1.0;
@@ -1177,7 +1180,7 @@ static int adjoint_setup(hlbm_ctx* c, int obj, int mode, AdjSetup* out) {
     sa.red = c->red;
     HLBM_TRY(c, CNT(c, launch_source)(sa, c->q, dbl, &nbs, c->stream), "source");
   }
-  HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, nbs, c->scal_dev, c->stream), "reduce");
+  HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, nbs, c->scal_dev, c->fin, c->stream), "reduce");
   HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
   HLBM_TRY(c, cudaMemsetAsync(c->lam, 0, lam_bytes, c->stream), "memset");
   HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
@@ -1249,7 +1252,7 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
       cudaError_t e = launch_adjoint(a, c->q, dbl, odd, exact, res, c->rr, c->stream);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = launch_finalize_sum(c->red, nb_adj, c->scal_dev, c->stream);
+    cudaError_t e = launch_finalize_sum(c->red, nb_adj, c->scal_dev, c->fin, c->stream);
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream);
   };
@@ -1645,6 +1648,7 @@ void hlbm_destroy(hlbm_ctx* c) {
   if (c->err_dev) cudaFree(c->err_dev);
   if (c->err_host) cudaFreeHost(c->err_host);
   if (c->scal_dev) cudaFree(c->scal_dev);
+  if (c->fin) cudaFree(c->fin);
   if (c->scal_host) cudaFreeHost(c->scal_host);
   for (auto& row : c->pgraph)
     for (auto& pg : row)
@@ -1947,7 +1951,7 @@ int hlbm_batch_solve_adjoint(hlbm_batch* b, hlbm_ctx* const* ctxs, int n, const 
     k_done += chunk;
     for (int k : active) {
       hlbm_ctx* c = ctxs[k];
-      HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, su[k].nb_adj, c->scal_dev, s), "reduce");
+      HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, su[k].nb_adj, c->scal_dev, c->fin, s), "reduce");
       HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, s), "copy");
     }
     HLBM_TRY(c0, cudaStreamSynchronize(s), "sync");

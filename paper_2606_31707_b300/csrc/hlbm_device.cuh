@@ -251,10 +251,12 @@ __device__ __forceinline__ void moments(const R (&f)[Q], R& rho, Vec3<R>& u) {
   u.z = mz * inv;
 }
 
+// Per-direction sums below start at -0: -0 + x is x for every x, so the
+// compiler drops the first addition (+0 + x is not x when x is -0).
 template <int Q, class R>
 __device__ __forceinline__ R xi_dot(int i, const Vec3<R>& v) {
   using L = Lat<Q>;
-  R s = 0;
+  R s = R(-0.0);
   if (L::cx(i)) s += L::cx(i) > 0 ? v.x : -v.x;
   if (L::cy(i)) s += L::cy(i) > 0 ? v.y : -v.y;
   if (L::cz(i)) s += L::cz(i) > 0 ? v.z : -v.z;
@@ -323,7 +325,7 @@ template <class R> __device__ __forceinline__ R dot3(const Vec3<R>& a, const Vec
 template <int Q, class R> __device__ __forceinline__ R xi_P_xi(int i, const Sym<R>& P) {
   using L = Lat<Q>;
   const int a = L::cx(i), b = L::cy(i), c = L::cz(i);
-  R s = 0;
+  R s = R(-0.0);
   if (a) s += P.xx;
   if (b) s += P.yy;
   if (c) s += P.zz;
@@ -331,6 +333,57 @@ template <int Q, class R> __device__ __forceinline__ R xi_P_xi(int i, const Sym<
   if (a && c) s += (a * c > 0) ? R(2) * P.xz : -R(2) * P.xz;
   if (b && c) s += (b * c > 0) ? R(2) * P.yz : -R(2) * P.yz;
   return s;
+}
+
+// Moments m0 = sum v, m1 = sum v xi, m2 = sum v xi xi of a per-direction field
+// over one weight class of the lattice: the axis directions (|xi|^2 = 1) or the
+// diagonal ones (|xi|^2 = 2).  Both lattices list opposite directions as pairs
+// (2k+1, 2k+2), so the sums run over pairs: with s = v_i + v_opp and
+// t = v_i - v_opp a pair adds s to m0 and m2 and xi_i t to m1.  Weighted moments
+// (sum w v ...) are w_axis times the axis class plus w_diag times the diagonal
+// class, plus w_0 v_0 in m0.
+template <class R> struct Mom { R m0; Vec3<R> m1; Sym<R> m2; };
+
+template <int Q> __host__ __device__ constexpr bool axis_dir(int i) {
+  return (Lat<Q>::cx(i) != 0) + (Lat<Q>::cy(i) != 0) + (Lat<Q>::cz(i) != 0) == 1;
+}
+template <int Q> __host__ __device__ constexpr bool weight_classes_hold() {
+  for (int i = 1; i < Q; ++i) {
+    if (Lat<Q>::opp(i) != ((i & 1) ? i + 1 : i - 1)) return false;
+    if (Lat<Q>::w(i) != (axis_dir<Q>(i) ? Lat<Q>::w(1) : Lat<Q>::w(Q - 1))) return false;
+  }
+  return true;
+}
+static_assert(weight_classes_hold<9>() && weight_classes_hold<19>(),
+              "direction order: rest, then opposite pairs; one weight per class");
+
+template <int Q, class R>
+__device__ __forceinline__ void pair_add(Mom<R>& m, int i, R s, R t) {
+  using L = Lat<Q>;
+  const int a = L::cx(i), b = L::cy(i), c = L::cz(i);
+  m.m0 += s;
+  if (a) m.m1.x += a > 0 ? t : -t;
+  if (b) m.m1.y += b > 0 ? t : -t;
+  if (c) m.m1.z += c > 0 ? t : -t;
+  if (a) m.m2.xx += s;
+  if (b) m.m2.yy += s;
+  if (c) m.m2.zz += s;
+  if (a && b) m.m2.xy += (a * b > 0) ? s : -s;
+  if (a && c) m.m2.xz += (a * c > 0) ? s : -s;
+  if (b && c) m.m2.yz += (b * c > 0) ? s : -s;
+}
+
+template <int Q, class R>
+__device__ __forceinline__ void class_moments(const R (&v)[Q], Mom<R>& ax, Mom<R>& dg) {
+  const R z = R(-0.0);
+  ax = Mom<R>{z, {z, z, z}, {z, z, z, z, z, z}};
+  dg = ax;
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const R s = v[i] + v[i + 1], t = v[i] - v[i + 1];
+    if (axis_dir<Q>(i)) pair_add<Q, R>(ax, i, s, t);
+    else pair_add<Q, R>(dg, i, s, t);
+  }
 }
 
 // positive root of tau^2 - tb tau - kles |Pi| = 0, kles = (9 sqrt 2 / 2) Cs^2

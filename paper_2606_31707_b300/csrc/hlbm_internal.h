@@ -125,8 +125,13 @@ cudaError_t launch_set_porosity(void* d, bool dbl, const double* in, long long n
 cudaError_t launch_convert_f32_to_f64(const float* in, double* out, long long n, cudaStream_t s);
 cudaError_t launch_convert_f64_to_f32(const double* in, float* out, long long n, cudaStream_t s);
 cudaError_t launch_real_to_f64(const void* in, bool dbl, double* out, long long n, cudaStream_t s);
-// out = sum of v[0..n) in a fixed order (one block)
-cudaError_t launch_finalize_sum(const double* v, long long n, double* out, cudaStream_t s);
+// out = sum of v[0..n) in a fixed order (up to kFinBlocks blocks); scratch holds
+// kFinBlocks partials and then a ticket word that must be zero at the first call
+// (each call leaves it zero).  Calls sharing a scratch must not overlap.
+constexpr int kFinBlocks = 296;
+constexpr size_t kFinScratchBytes = (size_t)(kFinBlocks + 1) * 8;
+cudaError_t launch_finalize_sum(const double* v, long long n, double* out, double* scratch,
+                                cudaStream_t s);
 cudaError_t launch_scale(double* v, long long n, double s_, cudaStream_t s);
 cudaError_t launch_fill_real(void* v, bool dbl, long long n, double value, cudaStream_t s);
 
@@ -161,6 +166,18 @@ struct SourceArgs {
 };
 cudaError_t launch_source(const SourceArgs& a, int q, bool dbl, int* nblocks, cudaStream_t s);
 
+// The part of an adjoint sweep that belongs to one right-hand side (the
+// fields of the same names in AdjointArgs).
+struct AdjRhs {
+  void* lam;
+  const void* src;
+  int sb[6];
+  long long src_pitch;
+  int src_nc;
+  void* snap;
+  double* red;
+};
+
 struct AdjointArgs {
   void* lam;           // AA array of the adjoint (real), q planes of g.pitch
   Grid g;
@@ -178,11 +195,18 @@ struct AdjointArgs {
   int src_nc;
   void* snap;          // residual snapshot (real, q planes of g.pitch)
   double* red;         // per-block partial of the residual
+  AdjRhs two;          // the second right-hand side of a paired sweep (launch_adjoint_pair)
 };
 // res: 0 plain, 1 write the snapshot (even kernels), 2 compare (odd kernels)
 cudaError_t launch_adjoint(const AdjointArgs& a, int q, bool dbl, bool odd, bool exact, int res,
                            bool rr, cudaStream_t s);
 int adjoint_blocks(const Grid& g);
+// one sweep of two adjoints about the same linearisation (two objectives): the
+// first right-hand side in the fields of a, the second in a.two; each with the
+// arithmetic of launch_adjoint, the record and porosity read once per cell;
+// BGK (compact or exact record)
+cudaError_t launch_adjoint_pair(const AdjointArgs& a, int q, bool dbl, bool odd, bool exact, int res,
+                                cudaStream_t s);
 // one sweep of several contexts in one launch (see launch_primal_batch): FP32,
 // compact linearisation record (BGK / frozen turbulence), res as launch_adjoint
 cudaError_t launch_adjoint_batch(const AdjointArgs* tab, const int4* tiles, int ntiles, int q,

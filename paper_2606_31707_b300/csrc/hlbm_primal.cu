@@ -197,9 +197,14 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
   using L = Lat<Q>;
   constexpr int D = L::D;
   const Grid& gr = a.g;
-  R drho, rho;
-  Vec3<R> m, u;
-  moments_dev<Q>(g, drho, rho, m, u);
+  // rho - 1 = sum g, m = rho u = sum xi g, M2 = sum xi xi g over the opposite pairs
+  Mom<R> ax, dg;
+  class_moments<Q, R>(g, ax, dg);
+  const R drho = g[0] + ax.m0 + dg.m0;
+  const R rho = R(1) + drho;
+  const Vec3<R> m{ax.m1.x + dg.m1.x, ax.m1.y + dg.m1.y, D == 3 ? ax.m1.z + dg.m1.z : R(0)};
+  const R inv_rho = R(1) / rho;
+  const Vec3<R> u{m.x * inv_rho, m.y * inv_rho, m.z * inv_rho};
   if (!(rho > R(0)) || !(fabs(u.x) + fabs(u.y) + fabs(u.z) < R(1e30))) atomicOr(a.err, 1u);
   const Vec3<R> us{par<R>(a.us[0], a.us_f[0]), par<R>(a.us[1], a.us_f[1]),
                    par<R>(a.us[2], a.us_f[2])};
@@ -213,22 +218,17 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
   R nP = 0;
   const bool diss_here = ACC > 0 && (a.obj_mask & 2) && x >= a.db[0] && x < a.db[1] &&
                          y >= a.db[2] && y < a.db[3] && z >= a.db[4] && z < a.db[5];
-  // No array of f - f^eq stays alive across the collision (which recomputes
-  // f^eq): BGK sums the non-equilibrium stress direction by direction; the
-  // regularised collision, which reads f only through its moments up to
-  // order 2, takes it from the second moment of f - w,
-  //   Pi = sum xi xi (f - w) - rho u~ u~ - (rho - 1)/3 I.
-  // (Each form gave the fewer registers for its collision.)
-  Sym<R> M2{0, 0, 0, 0, 0, 0};  // sum xi xi (f - w), averaged for the RR linearisation
-  if constexpr (RR) {
-    M2 = second_moment<Q>(g);
+  // The non-equilibrium stress from the second moment of f - w (the lattice
+  // sums of f^eq - w are (rho - 1)/3 I + rho u~ u~ on both lattices):
+  //   Pi = sum xi xi (f - w) - rho u~ u~ - (rho - 1)/3 I,
+  // so no array of f - f^eq is formed.
+  const Sym<R> M2{ax.m2.xx + dg.m2.xx, ax.m2.yy + dg.m2.yy, D == 3 ? ax.m2.zz + dg.m2.zz : R(0),
+                  dg.m2.xy, D == 3 ? dg.m2.xz : R(0), D == 3 ? dg.m2.yz : R(0)};
+  if (RR || LES || diss_here) {
     const R t = drho * R(1.0 / 3.0);
     P = Sym<R>{M2.xx - rho * ut.x * ut.x - t, M2.yy - rho * ut.y * ut.y - t,
                D == 3 ? M2.zz - rho * ut.z * ut.z - t : R(0), M2.xy - rho * ut.x * ut.y,
-               M2.xz - rho * ut.x * ut.z, M2.yz - rho * ut.y * ut.z};
-  } else if (LES || diss_here) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) sym_add_xixi<Q>(P, i, g[i] - geq_i<Q>(i, drho, rho, ut, uu));
+               D == 3 ? M2.xz - rho * ut.x * ut.z : R(0), D == 3 ? M2.yz - rho * ut.y * ut.z : R(0)};
   }
   if (LES || diss_here) nP = sqrt_r<R>(sym_norm2(P));
   const R kles = par<R>(a.kles, a.kles_f);
@@ -390,8 +390,27 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
       g[i] = R(Lat<Q>::w(i)) * (C0 + xi_dot<Q>(i, V) + rc2 + c45 * xPx + cu * (rc2 + R(3) * c45 * xPx));
     }
   } else {
+    // BGK toward f^eq(rho, u~): g_i <- g_i - omega (g_i - (f^eq_i - w_i)), with
+    // f^eq_i - w_i = w_i (A + B c^2) + w_i T c, c = xi_i . u~,
+    // A = rho - 1 - 3/2 rho u~.u~, B = 9/2 rho, T = 3 rho, formed over the
+    // opposite pairs (c changes sign, the rest is shared).  The update keeps
+    // the form g - omega (g - g^eq), whose rounding is relative to the small
+    // non-equilibrium part; (1 - omega) g + omega g^eq rounds relative to g and
+    // g^eq themselves, which at omega near 1.5 is about twice as much.
+    const R A_ = drho - R(1.5) * rho * uu, B_ = R(4.5) * rho, T_ = R(3) * rho;
+    const R wa = R(L::w(1)), wd = R(L::w(Q - 1));
+    const R aA = wa * A_, aB = wa * B_, aT = wa * T_;
+    const R dA = wd * A_, dB = wd * B_, dT = wd * T_;
+    g[0] -= om * (g[0] - R(L::w(0)) * A_);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] -= om * (g[i] - geq_i<Q>(i, drho, rho, ut, uu));
+    for (int i = 1; i < Q; i += 2) {
+      const bool axd = axis_dir<Q>(i);
+      const R cu = xi_dot<Q>(i, ut);
+      const R sym = (axd ? aA : dA) + (axd ? aB : dB) * (cu * cu);
+      const R anti = (axd ? aT : dT) * cu;
+      g[i] -= om * (g[i] - (sym + anti));
+      g[i + 1] -= om * (g[i + 1] - (sym - anti));
+    }
   }
   aa_store<Q, S, ODD, +1>(A, gr, rows, x, cell, g);
   return u;
@@ -404,14 +423,16 @@ __device__ __forceinline__ Vec3<typename Store<S>::real> cell_update(
 //   D2Q9 BGK averaging:   none 18.5 us, 8 blocks 16.4 us (64 registers)
 //   D3Q19 BGK averaging with the shared-memory prefetch of the staged sums and
 //   no barrier (the exact-LES window, full f): none 1621 us (108 / 134
-//   registers even / odd), 4: 1452, 5: 1447, 6: 1582 (spills)
+//   registers even / odd), 4: 1452, 5: 1447, 6: 1582 (spills); after the
+//   collision was written over opposite pairs with the stress from the second
+//   moment (GLUPS in the benchmark slice): 4: 14.46, 5: 14.71, 6: 15.06
 //   D3Q19 RR averaging:   none 1800 us, 4: 1880, 5: 1687
 //   D3Q19 RR plain:       none 712 us, 4: 796
 #ifndef HLBM_MINB_ACC_D2Q9
 #define HLBM_MINB_ACC_D2Q9 8
 #endif
 #ifndef HLBM_MINB_ACC_D3Q19
-#define HLBM_MINB_ACC_D3Q19 4
+#define HLBM_MINB_ACC_D3Q19 6
 #endif
 #ifndef HLBM_MINB_ACC_RR_D2Q9
 #define HLBM_MINB_ACC_RR_D2Q9 0
@@ -786,16 +807,48 @@ cudaError_t launch_real_to_f64(const void* in, bool dbl, double* out, long long 
   return cudaGetLastError();
 }
 
-__global__ void k_finalize_sum(const double* v, long long n, double* out) {
+// Sum of v[0..n) in a fixed order: block b sums the contiguous range
+// [b chunk, (b+1) chunk) (thread-strided, then the block tree) into part[b];
+// the last block to finish (atomic ticket, taken after the partial is written
+// and fenced) adds the partials in block order and resets the ticket for the
+// next call.  No block waits for another.  (One block for the whole sum took
+// 195 us for the 640 000 per-warp objective slots of the LES grid, bound by
+// that one SM's FP64 pipe.)
+__global__ void __launch_bounds__(256) k_finalize_sum(const double* v, long long n, long long chunk,
+                                                      double* part, unsigned* ticket, double* out) {
   __shared__ double sh[256 / 32];
+  __shared__ bool last;
+  const long long lo = (long long)blockIdx.x * chunk;
+  const long long hi = lo + chunk < n ? lo + chunk : n;
   double acc = 0.0;
-  for (long long k = threadIdx.x; k < n; k += blockDim.x) acc += v[k];
+  for (long long k = lo + threadIdx.x; k < hi; k += blockDim.x) acc += v[k];
   const double t = block_sum<256>(acc, sh);
-  if (threadIdx.x == 0) *out = t;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    double a2 = 0.0;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x)
+      a2 += static_cast<volatile double*>(part)[k];
+    const double r = block_sum<256>(a2, sh);
+    if (threadIdx.x == 0) {
+      *out = r;
+      *ticket = 0u;
+    }
+  }
 }
 
-cudaError_t launch_finalize_sum(const double* v, long long n, double* out, cudaStream_t s) {
-  k_finalize_sum<<<1, 256, 0, s>>>(v, n, out);
+cudaError_t launch_finalize_sum(const double* v, long long n, double* out, double* scratch,
+                                cudaStream_t s) {
+  long long nb = (n + 4095) / 4096;
+  if (nb < 1) nb = 1;
+  if (nb > kFinBlocks) nb = kFinBlocks;
+  const long long chunk = (n + nb - 1) / nb;
+  k_finalize_sum<<<(unsigned)nb, 256, 0, s>>>(v, n, chunk, scratch,
+                                               reinterpret_cast<unsigned*>(scratch + kFinBlocks), out);
   return cudaGetLastError();
 }
 

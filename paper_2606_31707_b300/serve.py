@@ -47,6 +47,8 @@ class Request:
     tag: object = None
     t_submit: float = 0.0
     adjoint_solver: int = 0              # 0 fixed point, 1 restarted GMRES (same fixed point)
+    gmres_restart: int = 30
+    gmres_inner: int = 100               # sweep pairs per Krylov operator application
     block_x: int = 0                     # threads per block along x (0: chosen by grid size)
 
 
@@ -187,7 +189,8 @@ class SensitivityServer:
     def submit(self, req: Request) -> Future:
         fut: Future = Future()
         req.t_submit = time.perf_counter()
-        need = footprint_bytes(req.q, req.dims, req.storage, adjoint_solver=req.adjoint_solver)
+        need = footprint_bytes(req.q, req.dims, req.storage, adjoint_solver=req.adjoint_solver,
+                               gmres_restart=req.gmres_restart)
         if need > self.budget:
             fut.set_exception(H.HlbmError(H.ENOMEM, "request larger than the HBM budget"))
             return fut
@@ -373,11 +376,13 @@ def solve_one(req: Request, solver: Optional[Solver] = None, keep_context: bool 
     if solver is None:
         s = Solver(req.q, req.dims, req.tau, req.Cs, storage=req.storage, u_in=req.u_in,
                    regions=req.regions, objectives=req.objective,
-                   adjoint_solver=req.adjoint_solver, block_x=req.block_x)
+                   adjoint_solver=req.adjoint_solver, gmres_restart=req.gmres_restart,
+                   gmres_inner=req.gmres_inner, block_x=req.block_x)
     else:
         s = solver
         s.configure(req.tau, req.Cs, u_in=req.u_in, regions=req.regions, objectives=req.objective,
-                    adjoint_solver=req.adjoint_solver)
+                    adjoint_solver=req.adjoint_solver, gmres_restart=req.gmres_restart,
+                    gmres_inner=req.gmres_inner)
     ok = False
     try:
         s.set_porosity(req.porosity)
