@@ -44,15 +44,17 @@ template <int Q, class R, bool EXACT, int NR = 1> struct LinCell {
   R nP, tau, sg[NR];
 };
 
-template <int Q, class R, bool EXACT, int NR>
-__device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
-                                         LinCell<Q, R, EXACT, NR>& c, const R (&mu)[Q],
-                                         const R (&mu2)[Q]) {
+// The linearisation point of a cell from the record; with EXACT, gb receives
+// the record's f_bar - w for the sums sg (record_dot), which need the mu of
+// each right-hand side.
+template <int Q, class R, bool EXACT, int NR, bool WITH_MU = false>
+__device__ __forceinline__ void load_record(const AdjointArgs& a, long long cell, R d,
+                                            LinCell<Q, R, EXACT, NR>& c, R (&gb)[EXACT ? Q : 1],
+                                            const R* mu = nullptr) {
   constexpr int D = Lat<Q>::D;
   const R* rec = static_cast<const R*>(a.rec);
   const long long rp = a.rec_pitch;
   c.d = d;
-  R gb[EXACT ? Q : 1];
   Sym<R> M2;
   if constexpr (!EXACT) {
     c.rho = rec[cell];
@@ -88,15 +90,12 @@ __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R
                  D == 3 ? M2.zz - t - c.rho * w.z * w.z : R(0), M2.xy - c.rho * w.x * w.y,
                  D == 3 ? M2.xz - c.rho * w.x * w.z : R(0),
                  D == 3 ? M2.yz - c.rho * w.y * w.z : R(0)};
-    R sg = mu[0] * gb[0];
+    if constexpr (WITH_MU) {
+      // sg[0] for a single right-hand side, formed while gb is at hand
+      R sg = mu[0] * gb[0];
 #pragma unroll
-    for (int i = 1; i < Q; ++i) sg += mu[i] * gb[i];
-    c.sg[0] = sg;
-    if constexpr (NR == 2) {
-      R sg2 = mu2[0] * gb[0];
-#pragma unroll
-      for (int i = 1; i < Q; ++i) sg2 += mu2[i] * gb[i];
-      c.sg[1] = sg2;
+      for (int i = 1; i < Q; ++i) sg += mu[i] * gb[i];
+      c.sg[0] = sg;
     }
     c.nP = sqrt_r<R>(sym_norm2(c.P));
     c.tau = tau_smagorinsky<R>(par<R>(a.tau_b, a.tau_b_f), par<R>(a.kles, a.kles_f), c.nP);
@@ -104,10 +103,20 @@ __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R
   }
 }
 
+// sum_i mu_i (f_bar_i - w_i)
+template <int Q, class R>
+__device__ __forceinline__ R record_dot(const R (&mu)[Q], const R (&gb)[Q]) {
+  R sg = mu[0] * gb[0];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) sg += mu[i] * gb[i];
+  return sg;
+}
+
 template <int Q, class R, bool EXACT>
 __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
                                          LinCell<Q, R, EXACT, 1>& c, const R (&mu)[Q]) {
-  load_lin<Q, R, EXACT, 1>(a, cell, d, c, mu, mu);
+  R gb[EXACT ? Q : 1];
+  load_record<Q, R, EXACT, 1, true>(a, cell, d, c, gb, mu);
 }
 
 // Contractions of mu at the linearisation point, from the weighted moments
@@ -656,60 +665,60 @@ cudaError_t launch_adjoint(const AdjointArgs& a, int q, bool dbl, bool odd, bool
 // cell update each with the arithmetic of the single sweep, in one kernel:
 // the record and the porosity are read once for both.
 // ----------------------------------------------------------------------------
+// One right-hand side r of the paired sweep at a cell whose linearisation
+// point c (and record gb) is loaded: the update of the single sweep, with the
+// outflow column folded in at x = nx - 2.
+template <int Q, class R, bool ODD, bool EXACT, int RES>
+__device__ __forceinline__ void pair_rhs(const AdjointArgs& a, const AdjRhs& rh, int r,
+                                         LinCell<Q, R, EXACT, 2>& c, const R (&gb)[EXACT ? Q : 1],
+                                         const Rows& rows, int x, int y, int z, long long cell,
+                                         typename JAcc<R>::T& rp) {
+  constexpr int S = RealStore<R>::S;
+  const Grid& g = a.g;
+  R* A = static_cast<R*>(rh.lam);
+  R v[Q];
+  aa_load<Q, S, ODD, -1>(A, g, rows, x, cell, v);
+  if constexpr (EXACT) c.sg[r] = record_dot<Q, R>(v, gb);
+  transpose_collide<Q, R, EXACT>(c, v, a, r);
+  add_source<Q, R>(rh, x, y, z, v);
+  residual_io<Q, R, RES>(rh, g.pitch, cell, v, rp);
+  if (x == g.nx - 2) {
+    R vo[Q];
+    aa_load<Q, S, ODD, -1>(A, g, rows, x + 1, cell + 1, vo);
+    R gbo[EXACT ? Q : 1];
+    LinCell<Q, R, EXACT, 2> co;
+    load_record<Q, R, EXACT, 2>(a, cell + 1, static_cast<const R*>(a.d)[cell + 1], co, gbo);
+    if constexpr (EXACT) co.sg[r] = record_dot<Q, R>(vo, gbo);
+    transpose_collide<Q, R, EXACT>(co, vo, a, r);
+    add_source<Q, R>(rh, x + 1, y, z, vo);
+    residual_io<Q, R, RES>(rh, g.pitch, cell + 1, vo, rp);
+    outlet_transpose<Q, R>(v, vo, c.rho, c.u);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) vo[i] = R(0);
+    aa_store<Q, S, ODD, -1>(A, g, rows, x + 1, cell + 1, vo);
+  }
+  if (x == 0) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = R(0);
+  }
+  aa_store<Q, S, ODD, -1>(A, g, rows, x, cell, v);
+}
+
 template <int Q, class R, bool ODD, bool EXACT, int RES>
 __device__ __forceinline__ void adjoint_pair_body(const AdjointArgs& a, int bxi, int y, int z,
                                                   long long blin) {
-  constexpr int S = RealStore<R>::S;
   const Grid& g = a.g;
   const int x = bxi * blockDim.x + threadIdx.x;
-  R* A0 = static_cast<R*>(a.lam);
-  R* A1 = static_cast<R*>(a.two.lam);
-  const R* dp = static_cast<const R*>(a.d);
   typename JAcc<R>::T rp0{}, rp1{};
   if (x < g.nx - 1) {
     const long long cell = cell_of(g, x, y, z);
     const Rows rows = make_rows<Lat<Q>::D>(g, y, z);
-    const AdjRhs r0 = rhs_of(a);
-    R v[Q], w[Q];
-    aa_load<Q, S, ODD, -1>(A0, g, rows, x, cell, v);
-    aa_load<Q, S, ODD, -1>(A1, g, rows, x, cell, w);
+    // the linearisation point once; the two fields one after the other
+    R gb[EXACT ? Q : 1];
     LinCell<Q, R, EXACT, 2> c;
-    load_lin<Q, R, EXACT, 2>(a, cell, dp[cell], c, v, w);
-    transpose_collide<Q, R, EXACT>(c, v, a, 0);
-    add_source<Q, R>(r0, x, y, z, v);
-    residual_io<Q, R, RES>(r0, g.pitch, cell, v, rp0);
-    transpose_collide<Q, R, EXACT>(c, w, a, 1);
-    add_source<Q, R>(a.two, x, y, z, w);
-    residual_io<Q, R, RES>(a.two, g.pitch, cell, w, rp1);
-    if (x == g.nx - 2) {
-      // the outflow column: its own cell update, folded into column nx - 2
-      R vo[Q], wo[Q];
-      aa_load<Q, S, ODD, -1>(A0, g, rows, x + 1, cell + 1, vo);
-      aa_load<Q, S, ODD, -1>(A1, g, rows, x + 1, cell + 1, wo);
-      LinCell<Q, R, EXACT, 2> co;
-      load_lin<Q, R, EXACT, 2>(a, cell + 1, dp[cell + 1], co, vo, wo);
-      transpose_collide<Q, R, EXACT>(co, vo, a, 0);
-      add_source<Q, R>(r0, x + 1, y, z, vo);
-      residual_io<Q, R, RES>(r0, g.pitch, cell + 1, vo, rp0);
-      transpose_collide<Q, R, EXACT>(co, wo, a, 1);
-      add_source<Q, R>(a.two, x + 1, y, z, wo);
-      residual_io<Q, R, RES>(a.two, g.pitch, cell + 1, wo, rp1);
-      outlet_transpose<Q, R>(v, vo, c.rho, c.u);
-      outlet_transpose<Q, R>(w, wo, c.rho, c.u);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) vo[i] = R(0);
-      aa_store<Q, S, ODD, -1>(A0, g, rows, x + 1, cell + 1, vo);
-      aa_store<Q, S, ODD, -1>(A1, g, rows, x + 1, cell + 1, vo);
-    }
-    if (x == 0) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        v[i] = R(0);
-        w[i] = R(0);
-      }
-    }
-    aa_store<Q, S, ODD, -1>(A0, g, rows, x, cell, v);
-    aa_store<Q, S, ODD, -1>(A1, g, rows, x, cell, w);
+    load_record<Q, R, EXACT, 2>(a, cell, static_cast<const R*>(a.d)[cell], c, gb);
+    pair_rhs<Q, R, ODD, EXACT, RES>(a, rhs_of(a), 0, c, gb, rows, x, y, z, cell, rp0);
+    pair_rhs<Q, R, ODD, EXACT, RES>(a, a.two, 1, c, gb, rows, x, y, z, cell, rp1);
   }
   if (RES == 2) {
     __shared__ double sh[NT / 32];

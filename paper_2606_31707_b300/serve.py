@@ -49,6 +49,8 @@ class Request:
     adjoint_solver: int = 0              # 0 fixed point, 1 restarted GMRES (same fixed point)
     gmres_restart: int = 30
     gmres_inner: int = 100               # sweep pairs per Krylov operator application
+    warm_start: bool = False             # on a reused context, start the adjoint from the
+                                         # previous request's (same fixed point and tolerance)
     block_x: int = 0                     # threads per block along x (0: chosen by grid size)
 
 
@@ -382,7 +384,7 @@ def solve_one(req: Request, solver: Optional[Solver] = None, keep_context: bool 
         s = solver
         s.configure(req.tau, req.Cs, u_in=req.u_in, regions=req.regions, objectives=req.objective,
                     adjoint_solver=req.adjoint_solver, gmres_restart=req.gmres_restart,
-                    gmres_inner=req.gmres_inner)
+                    gmres_inner=req.gmres_inner, adjoint_warm_start=req.warm_start)
     ok = False
     try:
         s.set_porosity(req.porosity)

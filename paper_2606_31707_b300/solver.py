@@ -23,7 +23,8 @@ class Solver:
                  accum_stride: int = 1, check_every: int = 100, stream=None,
                  u_solid=(0.0, 0.0, 0.0), average_full_f: bool = False,
                  adjoint_solver: int = 0, gmres_restart: int = 30, gmres_inner: int = 100,
-                 collision: int = H.COLL_BGK, inflow_profile=None, block_x: int = 0):
+                 collision: int = H.COLL_BGK, inflow_profile=None, block_x: int = 0,
+                 adjoint_warm_start: bool = False):
         self.q = lattice
         self.dims = tuple(int(v) for v in dims)
         self.dim = 2 if lattice == 9 else 3
@@ -34,6 +35,7 @@ class Solver:
         opt.gmres_inner = gmres_inner
         opt.collision = collision
         opt.block_x = block_x
+        opt.adjoint_warm_start = int(adjoint_warm_start)
         prof = None
         if inflow_profile is not None:
             prof = np.ascontiguousarray(inflow_profile, dtype=np.float64).ravel()
@@ -81,7 +83,7 @@ class Solver:
                   objectives: int = H.OBJ_DRAG_FFA | H.OBJ_DISSIPATION, tau_adj: float = 0.0,
                   accum_stride: int = 1, check_every: int = 100, u_solid=(0.0, 0.0, 0.0),
                   average_full_f: bool = False, adjoint_solver: int = 0, gmres_restart: int = 30,
-                  gmres_inner: int = 100, inflow_profile=None):
+                  gmres_inner: int = 100, inflow_profile=None, adjoint_warm_start: bool = False):
         """New physical parameters for this context (same grid and storage)."""
         opt = self._options(self.opt.storage, u_in, regions, objectives, tau_adj, accum_stride,
                             check_every, u_solid, average_full_f)
@@ -89,6 +91,7 @@ class Solver:
         opt.gmres_restart = gmres_restart
         opt.gmres_inner = gmres_inner
         opt.collision = self.opt.collision
+        opt.adjoint_warm_start = int(adjoint_warm_start)
         prof = None
         if inflow_profile is not None:
             prof = np.ascontiguousarray(inflow_profile, dtype=np.float64).ravel()
@@ -130,10 +133,20 @@ class Solver:
                       max_iter: int = 100000):
         return H.hlbm_solve_adjoint(self.ctx, obj, mode, tol, max_iter)
 
-    def gradient(self, out=None):
+    def solve_adjoint_pair(self, mode: int = H.ADJ_EXACT, tol: float = 1e-8,
+                           max_iter: int = 100000):
+        """The J_FFA and J_DISS adjoints together (paired sweeps)."""
+        return H.hlbm_solve_adjoint_pair(self.ctx, mode, tol, max_iter)
+
+    def gradient(self, out=None, objective=None):
+        """dJ/dd over the design box: of the last solve's objective, or of
+        `objective` (whose adjoint a single or paired solve computed)."""
         if out is None:
             out = np.empty(self.design_shape, dtype=np.float64)
-        H.hlbm_gradient(self.ctx, out)
+        if objective is None:
+            H.hlbm_gradient(self.ctx, out)
+        else:
+            H.hlbm_gradient_of(self.ctx, objective, out)
         return out
 
     _NCOMP = {H.FIELD_RHO: 1, H.FIELD_U: None, H.FIELD_F: "q", H.FIELD_FBAR: "q",
