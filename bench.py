@@ -12,10 +12,7 @@ grid, continuing the flow from the previous step:
   the dissipation (J_DISS) objectives: the linearisation at the window's
   mean, M adjoint sweeps of the fixed-point iteration from zero for each
   (tolerance 0: a fixed sweep count, so the status is NOT_CONVERGED by
-  construction and is reported with the residual) and the gradient.  The two
-  adjoints are iterated together in paired sweeps (one launch updates both
-  fields and reads the linearisation record once; --no-adjoint-pair runs them
-  one after the other; the regularised collision always does).
+  construction and is reported with the residual) and the gradient.
 
 value = lattice updates of the slice (N x (P + W + 2 M)) per second on the
 device, inputs resident; e2e = the same through the C ABI with host buffers
@@ -104,8 +101,6 @@ def parse():
     ap.add_argument("--slice-sweeps", type=int, default=64,
                     help="adjoint sweeps per objective and step (M)")
     ap.add_argument("--adjoint-mode", default="exact", choices=["exact", "fta"])
-    ap.add_argument("--no-adjoint-pair", dest="adjoint_pair", action="store_false",
-                    help="solve the two adjoints one after the other instead of in paired sweeps")
     ap.add_argument("--tau-adj", type=float, default=None,
                     help="adjoint relaxation time, the regularisation of Sec. 5.4 "
                          "(default: 0.6, the paper's LES setting, when C_S > 0, else tau0)")
@@ -157,8 +152,7 @@ def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False, rr=False):
     Cs > 0; inside the objective regions the dJ/df coefficients (2 on the
     drag plane, 1 + D + D(D+1)/2 in the dissipation box) and dJ/dd.  The
     regularised collision's adjoint record is rho, u, omega and the stress
-    (2 + D + D(D+1)/2 planes).  The paired sweep updates both adjoints and
-    reads the record and the porosity once."""
+    (2 + D + D(D+1)/2 planes)."""
     q = wl.q
     nx, ny, nz = wl.dims
     N = nx * ny * nz
@@ -178,9 +172,7 @@ def bytes_model(wl, storage_bytes, real_bytes, exact_rec=False, rr=False):
     # the source: the derivative polynomial's coefficients in the objective's region
     adj_ffa = (2 * q + rec + 1) * real_bytes + ffa_cells * 2 * real_bytes / N
     adj_diss = (2 * q + rec + 1) * real_bytes + diss_cells * (1 + D + D * (D + 1) // 2) * real_bytes / N
-    # the paired sweep (both adjoints, one read of the record and porosity)
-    adj_pair = adj_ffa + adj_diss - (rec + 1) * real_bytes
-    return dict(plain=plain, acc=acc, adj_ffa=adj_ffa, adj_diss=adj_diss, adj_pair=adj_pair)
+    return dict(plain=plain, acc=acc, adj_ffa=adj_ffa, adj_diss=adj_diss)
 
 
 # ---------------------------------------------------------------------------
@@ -304,11 +296,9 @@ def run_ours(args, rank, world):
     objectives = (H.OBJ_DRAG_FFA, H.OBJ_DISSIPATION)
     last = [None, None]
 
-    pair = args.adjoint_pair and args.collision != "rr"
-
     def zero_phase():
         return dict(plain_ms=0.0, plain_launch=0, acc_ms=0.0, acc_launch=0, adj_ms=[0.0, 0.0],
-                    adj_launch=[0, 0], adj_iters=[0, 0], pair_ms=0.0, pair_launch=0)
+                    adj_launch=[0, 0], adj_iters=[0, 0])
 
     phase = zero_phase()
 
@@ -326,18 +316,6 @@ def run_ours(args, rank, world):
             phase["acc_launch"] += st.primal_launches
         lups = (Pn + Wn) * N
         Js = [s.objective(o) for o in objectives]
-        if pair:
-            # both adjoints in paired sweeps (each sweep updates both fields)
-            _, per = s.solve_adjoint_pair(mode, 0.0, M)
-            st = s.stats()
-            if record:
-                phase["pair_ms"] += st.adjoint_ms
-                phase["pair_launch"] += st.adjoint_launches
-            for k, o in enumerate(objectives):
-                last[k] = per[k]
-                lups += per[k][1] * N
-                H.hlbm_gradient_of(s.ctx, o, g_host[k] if host else g_dev[k])
-            return lups, Js
         for k, o in enumerate(objectives):
             status, it, res = s.solve_adjoint(o, mode, 0.0, M)
             last[k] = (status, it, res)
@@ -401,7 +379,7 @@ def run_ours(args, rank, world):
         acc = gradient_accuracy(args, wl, s, H, Solver, mode, coll, stream, d_dev, torch, dev)
     s.close()
     return dict(wl=wl, value=value, ms=ms, lups=lups, e2e=e2e, launches=launches,
-                phase=phase_dev, clocks=clocks, Js=Js, adjoint=adj_state, accuracy=acc, pair=pair)
+                phase=phase_dev, clocks=clocks, Js=Js, adjoint=adj_state, accuracy=acc)
 
 
 def gradient_accuracy(args, wl, s, H, Solver, mode, coll, stream, d_dev, torch, dev):
@@ -457,8 +435,6 @@ def roofline_of(res, args, storage_bytes, real_bytes):
     for k, key in enumerate(("adj_ffa", "adj_diss")):
         if ph["adj_launch"][k]:
             cand.append((f"adjoint_step_{key[4:]}", ph["adj_ms"][k], ph["adj_launch"][k], bm[key], 1))
-    if ph.get("pair_launch"):
-        cand.append(("adjoint_step_pair", ph["pair_ms"], ph["pair_launch"], bm["adj_pair"], 2))
     name, ms, launches, bpl, _ = max(cand, key=lambda c: c[1])
     per_launch_s = ms * 1e-3 / launches
     achieved = bpl * N / per_launch_s / 1e9
@@ -678,7 +654,6 @@ def main():
     roof = roofline_of(res, args, sb, rb)
     cpu = None if args.no_cpu_baseline else cpu_baseline(args, wl)
     cfg = config_of(wl, args)
-    cfg["adjoint"]["paired_sweeps"] = res["pair"]
     cfg["adjoint"]["last_step"] = {"drag_ffa": res["adjoint"][0], "dissipation": res["adjoint"][1]}
     line = {
         "metric": METRIC,

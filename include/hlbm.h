@@ -189,11 +189,13 @@ int hlbm_create(hlbm_ctx** out, int lattice, const int dims[3], double tau,
 /* Change the physical parameters of an existing context without
  * reallocating it: relaxation time tau, Smagorinsky constant Cs and, from
  * opt (may be NULL), u_in, u_solid, tau_adj, objectives, the regions,
- * accum_stride, check_every, average_full_f, the adjoint solver settings and
- * the inflow profile (NULL restores the uniform inflow); storage, stream,
- * allocator, block_x and collision keep their creation values (a different
- * collision is HLBM_EINVAL).  Clears the averages and the adjoint; the state
- * and the porosity are kept.  Arguments are checked before anything changes,
+ * accum_stride, check_every, average_full_f, the adjoint solver settings
+ * (adjoint_solver, gmres_*, adjoint_warm_start) and the inflow profile (NULL
+ * restores the uniform inflow); storage, stream, allocator, block_x and
+ * collision keep their creation values (a different collision is
+ * HLBM_EINVAL).  Clears the averages and the adjoint result (the adjoint
+ * array itself stays, as the start of a warm-started solve); the state and
+ * the porosity are kept.  Arguments are checked before anything changes,
  * so an HLBM_EINVAL leaves the context as it was.  Lets a server reuse a
  * context (and its captured graphs) for a new request of the same grid. */
 int hlbm_configure(hlbm_ctx* ctx, double tau, double Cs, const hlbm_options* opt);
@@ -245,34 +247,10 @@ int hlbm_objective(hlbm_ctx* ctx, int objective, double* J_out);
 int hlbm_solve_adjoint(hlbm_ctx* ctx, int objective, int mode, double tol,
                        long max_iter, long* iters_out, double* residual_out);
 
-/* The adjoints of J_FFA and J_DISS about the same averaged state (the two
- * objectives of Sec. 4.2 and 4.3 share the linearisation of Eq.
- * adjoint_unsteady), iterated together: every paired sweep applies one
- * fixed-point iteration of hlbm_solve_adjoint to each, with the same
- * arithmetic, in one kernel launch that reads the linearisation record and
- * the porosity once per cell for both.  Both start from lambda = 0 and the
- * sweeps go on until both update criteria are <= tol (each checked every
- * check_every sweeps, as in hlbm_solve_adjoint) or max_iter sweeps.
- * Needs both objectives in the averaging mask; BGK collision and the
- * fixed-point solver only (HLBM_EINVAL for the regularised collision or
- * opt.adjoint_solver = 1).  iters_out, residual_out, status_out: two
- * entries each ([0] J_FFA, [1] J_DISS; the sweeps at which each met its
- * criterion, else the last), may be NULL.  Returns the worse status: an
- * error if either diverged or became non-finite, else HLBM_NOT_CONVERGED
- * unless both converged.  Afterwards hlbm_gradient_of gives each
- * objective's gradient (hlbm_gradient that of J_FFA). */
-int hlbm_solve_adjoint_pair(hlbm_ctx* ctx, int mode, double tol, long max_iter,
-                            long* iters_out, double* residual_out, int* status_out);
-
 /* Gradient dJ/dd over the design box, x fastest (Eq. gradients_unsteady),
  * for the objective of the last solve: dJ/dd_bar + sum_i mu_i dC_i/dd.
  * out holds box-volume values of dtype, host or device. */
 int hlbm_gradient(hlbm_ctx* ctx, void* out, int dtype, int on_device);
-
-/* The same for `objective`, from the last solve that computed its adjoint
- * (hlbm_solve_adjoint, or either objective of hlbm_solve_adjoint_pair);
- * HLBM_ESTATE if there is none for the current averaged state. */
-int hlbm_gradient_of(hlbm_ctx* ctx, int objective, void* out, int dtype, int on_device);
 
 /* Read a field (see HLBM_FIELD_*) in canonical order into out. */
 int hlbm_get_field(hlbm_ctx* ctx, int which, void* out, int dtype, int on_device);

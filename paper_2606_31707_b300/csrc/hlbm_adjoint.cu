@@ -32,29 +32,25 @@ template <> __device__ __forceinline__ double pi_eps<double>() { return 1e-30; }
 template <> __device__ __forceinline__ float pi_eps<float>() { return 1e-20f; }
 
 // Linearisation point of one cell, derived from the record.
-template <int Q, class R, bool EXACT, int NR = 1> struct LinCell {
+template <int Q, class R, bool EXACT> struct LinCell {
   R rho, om, d;
   Vec3<R> u, ut;
   // EXACT only: rho - 1, the non-equilibrium stress of f_bar, its norm,
-  // tau_eff, and sg[r] = sum_i mu_i (f_bar_i - w_i) for the mu of each
-  // right-hand side r this cell is processed with (f_bar itself is not kept
-  // through the transpose)
+  // tau_eff, and sg = sum_i mu_i (f_bar_i - w_i) for the mu this cell is
+  // processed with (f_bar itself is not kept through the transpose)
   R drho;
   Sym<R> P;
-  R nP, tau, sg[NR];
+  R nP, tau, sg;
 };
 
-// The linearisation point of a cell from the record; with EXACT, gb receives
-// the record's f_bar - w for the sums sg (record_dot), which need the mu of
-// each right-hand side.
-template <int Q, class R, bool EXACT, int NR, bool WITH_MU = false>
-__device__ __forceinline__ void load_record(const AdjointArgs& a, long long cell, R d,
-                                            LinCell<Q, R, EXACT, NR>& c, R (&gb)[EXACT ? Q : 1],
-                                            const R* mu = nullptr) {
+template <int Q, class R, bool EXACT>
+__device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
+                                         LinCell<Q, R, EXACT>& c, const R (&mu)[Q]) {
   constexpr int D = Lat<Q>::D;
   const R* rec = static_cast<const R*>(a.rec);
   const long long rp = a.rec_pitch;
   c.d = d;
+  R gb[EXACT ? Q : 1];
   Sym<R> M2;
   if constexpr (!EXACT) {
     c.rho = rec[cell];
@@ -90,33 +86,14 @@ __device__ __forceinline__ void load_record(const AdjointArgs& a, long long cell
                  D == 3 ? M2.zz - t - c.rho * w.z * w.z : R(0), M2.xy - c.rho * w.x * w.y,
                  D == 3 ? M2.xz - c.rho * w.x * w.z : R(0),
                  D == 3 ? M2.yz - c.rho * w.y * w.z : R(0)};
-    if constexpr (WITH_MU) {
-      // sg[0] for a single right-hand side, formed while gb is at hand
-      R sg = mu[0] * gb[0];
+    R sg = mu[0] * gb[0];
 #pragma unroll
-      for (int i = 1; i < Q; ++i) sg += mu[i] * gb[i];
-      c.sg[0] = sg;
-    }
+    for (int i = 1; i < Q; ++i) sg += mu[i] * gb[i];
+    c.sg = sg;
     c.nP = sqrt_r<R>(sym_norm2(c.P));
     c.tau = tau_smagorinsky<R>(par<R>(a.tau_b, a.tau_b_f), par<R>(a.kles, a.kles_f), c.nP);
     c.om = R(1) / c.tau;
   }
-}
-
-// sum_i mu_i (f_bar_i - w_i)
-template <int Q, class R>
-__device__ __forceinline__ R record_dot(const R (&mu)[Q], const R (&gb)[Q]) {
-  R sg = mu[0] * gb[0];
-#pragma unroll
-  for (int i = 1; i < Q; ++i) sg += mu[i] * gb[i];
-  return sg;
-}
-
-template <int Q, class R, bool EXACT>
-__device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
-                                         LinCell<Q, R, EXACT, 1>& c, const R (&mu)[Q]) {
-  R gb[EXACT ? Q : 1];
-  load_record<Q, R, EXACT, 1, true>(a, cell, d, c, gb, mu);
 }
 
 // Contractions of mu at the linearisation point, from the weighted moments
@@ -166,9 +143,9 @@ __device__ __forceinline__ MuC<R> mu_contract(const R (&mu)[Q], const Vec3<R>& u
 //   K1 = omega d gv - 2 d E Pi u~,   K2 = E Pi,
 // evaluated over opposite pairs (xi_opp = -xi: the K0 and K2 parts are shared,
 // the K1 part changes sign).
-template <int Q, class R, bool EXACT, int NR>
-__device__ __forceinline__ void transpose_collide(const LinCell<Q, R, EXACT, NR>& c, R (&mu)[Q],
-                                                  const AdjointArgs& a, int r = 0) {
+template <int Q, class R, bool EXACT>
+__device__ __forceinline__ void transpose_collide(const LinCell<Q, R, EXACT>& c, R (&mu)[Q],
+                                                  const AdjointArgs& a) {
   const MuC<R> k = mu_contract<Q, R>(mu, c.ut, EXACT ? c.drho : c.rho - R(1), c.rho);
   const R om = c.om, d = c.d;
   const R ug = dot3(c.u, k.gv);
@@ -179,7 +156,7 @@ __device__ __forceinline__ void transpose_collide(const LinCell<Q, R, EXACT, NR>
   if constexpr (EXACT) {
     if (c.nP > pi_eps<R>()) {
       // sum mu_i (f_bar_i - f^eq_i) = sg - qe
-      const R E = om * om * (c.sg[r] - k.qe) * par<R>(a.kles, a.kles_f) /
+      const R E = om * om * (c.sg - k.qe) * par<R>(a.kles, a.kles_f) /
                   ((R(2) * c.tau - par<R>(a.tau_b, a.tau_b_f)) * c.nP);
       const Vec3<R> PU = sym_mul(c.P, c.ut);
       const R uPu = dot3(c.ut, PU), uPU = dot3(c.u, PU);
@@ -261,11 +238,6 @@ __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R
 template <int Q, class R, bool EXACT>
 __device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
                                          RRCell<R, EXACT>& c, const R (&)[Q]) {
-  load_lin<Q, R, EXACT>(a, cell, d, c);
-}
-template <int Q, class R, bool EXACT>
-__device__ __forceinline__ void load_lin(const AdjointArgs& a, long long cell, R d,
-                                         RRCell<R, EXACT>& c, const R (&)[Q], const R (&)[Q]) {
   load_lin<Q, R, EXACT>(a, cell, d, c);
 }
 
@@ -361,16 +333,12 @@ __device__ __forceinline__ void rr_transpose(const RRCell<R, EXACT>& c, R (&mu)[
 
 template <int Q, class R, bool EXACT>
 __device__ __forceinline__ void transpose_collide(const RRCell<R, EXACT>& c, R (&mu)[Q],
-                                                  const AdjointArgs& a, int = 0) {
+                                                  const AdjointArgs& a) {
   rr_transpose<Q, R, EXACT>(c, mu, a, nullptr);
 }
 
-template <int Q, class R, bool EXACT, bool RR, int NR = 1> struct CellOf {
-  using T = LinCell<Q, R, EXACT, NR>;
-};
-template <int Q, class R, bool EXACT, int NR> struct CellOf<Q, R, EXACT, true, NR> {
-  using T = RRCell<R, EXACT>;
-};
+template <int Q, class R, bool EXACT, bool RR> struct CellOf { using T = LinCell<Q, R, EXACT>; };
+template <int Q, class R, bool EXACT> struct CellOf<Q, R, EXACT, true> { using T = RRCell<R, EXACT>; };
 
 // v += g_bar at one cell from the coefficients c of the objective's derivative
 // polynomial in xi (nc = 2: J_FFA, c0 + c1 xi_x; otherwise J_DISS,
@@ -660,129 +628,6 @@ cudaError_t launch_adjoint(const AdjointArgs& a, int q, bool dbl, bool odd, bool
 }
 
 // ----------------------------------------------------------------------------
-// Paired sweep: the adjoints of two objectives about the same averaged state
-// (J_FFA and J_DISS share the linearisation record and the porosity), one
-// cell update each with the arithmetic of the single sweep, in one kernel:
-// the record and the porosity are read once for both.
-// ----------------------------------------------------------------------------
-// One right-hand side r of the paired sweep at a cell whose linearisation
-// point c (and record gb) is loaded: the update of the single sweep, with the
-// outflow column folded in at x = nx - 2.
-template <int Q, class R, bool ODD, bool EXACT, int RES>
-__device__ __forceinline__ void pair_rhs(const AdjointArgs& a, const AdjRhs& rh, int r,
-                                         LinCell<Q, R, EXACT, 2>& c, const R (&gb)[EXACT ? Q : 1],
-                                         const Rows& rows, int x, int y, int z, long long cell,
-                                         typename JAcc<R>::T& rp) {
-  constexpr int S = RealStore<R>::S;
-  const Grid& g = a.g;
-  R* A = static_cast<R*>(rh.lam);
-  R v[Q];
-  aa_load<Q, S, ODD, -1>(A, g, rows, x, cell, v);
-  if constexpr (EXACT) c.sg[r] = record_dot<Q, R>(v, gb);
-  transpose_collide<Q, R, EXACT>(c, v, a, r);
-  add_source<Q, R>(rh, x, y, z, v);
-  residual_io<Q, R, RES>(rh, g.pitch, cell, v, rp);
-  if (x == g.nx - 2) {
-    R vo[Q];
-    aa_load<Q, S, ODD, -1>(A, g, rows, x + 1, cell + 1, vo);
-    R gbo[EXACT ? Q : 1];
-    LinCell<Q, R, EXACT, 2> co;
-    load_record<Q, R, EXACT, 2>(a, cell + 1, static_cast<const R*>(a.d)[cell + 1], co, gbo);
-    if constexpr (EXACT) co.sg[r] = record_dot<Q, R>(vo, gbo);
-    transpose_collide<Q, R, EXACT>(co, vo, a, r);
-    add_source<Q, R>(rh, x + 1, y, z, vo);
-    residual_io<Q, R, RES>(rh, g.pitch, cell + 1, vo, rp);
-    outlet_transpose<Q, R>(v, vo, c.rho, c.u);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) vo[i] = R(0);
-    aa_store<Q, S, ODD, -1>(A, g, rows, x + 1, cell + 1, vo);
-  }
-  if (x == 0) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) v[i] = R(0);
-  }
-  aa_store<Q, S, ODD, -1>(A, g, rows, x, cell, v);
-}
-
-template <int Q, class R, bool ODD, bool EXACT, int RES>
-__device__ __forceinline__ void adjoint_pair_body(const AdjointArgs& a, int bxi, int y, int z,
-                                                  long long blin) {
-  const Grid& g = a.g;
-  const int x = bxi * blockDim.x + threadIdx.x;
-  typename JAcc<R>::T rp0{}, rp1{};
-  if (x < g.nx - 1) {
-    const long long cell = cell_of(g, x, y, z);
-    const Rows rows = make_rows<Lat<Q>::D>(g, y, z);
-    // the linearisation point once; the two fields one after the other
-    R gb[EXACT ? Q : 1];
-    LinCell<Q, R, EXACT, 2> c;
-    load_record<Q, R, EXACT, 2>(a, cell, static_cast<const R*>(a.d)[cell], c, gb);
-    pair_rhs<Q, R, ODD, EXACT, RES>(a, rhs_of(a), 0, c, gb, rows, x, y, z, cell, rp0);
-    pair_rhs<Q, R, ODD, EXACT, RES>(a, a.two, 1, c, gb, rows, x, y, z, cell, rp1);
-  }
-  if (RES == 2) {
-    __shared__ double sh[NT / 32];
-    const double s0 = block_sum<NT>(rp0, sh);
-    if (threadIdx.x == 0) a.red[blin] = s0;
-    __syncthreads();
-    const double s1 = block_sum<NT>(rp1, sh);
-    if (threadIdx.x == 0) a.two.red[blin] = s1;
-  }
-}
-
-// resident blocks per SM requested for the FP32 D3Q19 paired sweeps (0: none)
-#ifndef HLBM_AMINB_PAIR_D3Q19
-#define HLBM_AMINB_PAIR_D3Q19 0
-#endif
-#ifndef HLBM_AMINB_PAIR_D3Q19_EXACT
-#define HLBM_AMINB_PAIR_D3Q19_EXACT 4
-#endif
-template <int Q, class R, bool EXACT>
-constexpr int adjoint_pair_min_blocks() {
-  if (Q != 19 || sizeof(R) != 4) return 0;
-  return EXACT ? HLBM_AMINB_PAIR_D3Q19_EXACT : HLBM_AMINB_PAIR_D3Q19;
-}
-
-template <int Q, class R, bool ODD, bool EXACT, int RES>
-__global__ void __launch_bounds__(NT) k_adjoint_pair(AdjointArgs a) {
-  adjoint_pair_body<Q, R, ODD, EXACT, RES>(a, blockIdx.x, blockIdx.y, blockIdx.z, block_linear());
-}
-template <int Q, class R, bool ODD, bool EXACT, int RES, int MB>
-__global__ void __launch_bounds__(NT, MB) k_adjoint_pair_mb(AdjointArgs a) {
-  adjoint_pair_body<Q, R, ODD, EXACT, RES>(a, blockIdx.x, blockIdx.y, blockIdx.z, block_linear());
-}
-
-template <int Q, class R, bool ODD, bool EXACT, int RES>
-static void launch_pair_one(const AdjointArgs& a, dim3 grid, int bx, cudaStream_t s) {
-  constexpr int mb = adjoint_pair_min_blocks<Q, R, EXACT>();
-  if constexpr (mb > 0) k_adjoint_pair_mb<Q, R, ODD, EXACT, RES, (mb > 0 ? mb : 1)><<<grid, bx, 0, s>>>(a);
-  else k_adjoint_pair<Q, R, ODD, EXACT, RES><<<grid, bx, 0, s>>>(a);
-}
-
-template <int Q, class R>
-static cudaError_t launch_pair_qr(const AdjointArgs& a, bool odd, bool exact, int res, cudaStream_t s) {
-  const int bx = a.g.bx;
-  dim3 grid((a.g.nx + bx - 1) / bx, a.g.ny, a.g.nz);
-#define HLBM_P(O, E, RS) launch_pair_one<Q, R, O, E, RS>(a, grid, bx, s)
-#define HLBM_PR(O, E) \
-  do { if (res == 0) HLBM_P(O, E, 0); else if (res == 1) HLBM_P(O, E, 1); else HLBM_P(O, E, 2); } while (0)
-  if (!odd) { if (!exact) HLBM_PR(false, false); else HLBM_PR(false, true); }
-  else      { if (!exact) HLBM_PR(true, false);  else HLBM_PR(true, true); }
-#undef HLBM_PR
-#undef HLBM_P
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adjoint_pair(const AdjointArgs& a, int q, bool dbl, bool odd, bool exact, int res,
-                                cudaStream_t s) {
-  if (q == 9) return dbl ? launch_pair_qr<9, double>(a, odd, exact, res, s)
-                         : launch_pair_qr<9, float>(a, odd, exact, res, s);
-  if (q == 19) return dbl ? launch_pair_qr<19, double>(a, odd, exact, res, s)
-                          : launch_pair_qr<19, float>(a, odd, exact, res, s);
-  return cudaErrorInvalidValue;
-}
-
-// ----------------------------------------------------------------------------
 // linearisation record from the running sums
 // ----------------------------------------------------------------------------
 template <int Q, class R>
@@ -1051,7 +896,7 @@ __global__ void __launch_bounds__(NT) k_gradient(GradArgs ga) {
       if (c.nP > pi_eps<R>()) {
         const R pdd = -R(2) * c.rho * dot3(v, sym_mul(c.P, c.ut));
         // (sum mu (feq - f)) * (-om^2) * k pdd / ((2 tau - tau_b) |Pi|)
-        val += (c.sg[0] - k.qe) * c.om * c.om * par<R>(ga.kles, ga.kles_f) * pdd /
+        val += (c.sg - k.qe) * c.om * c.om * par<R>(ga.kles, ga.kles_f) * pdd /
                ((R(2) * c.tau - par<R>(ga.tau_b, ga.tau_b_f)) * c.nP);
       }
     }

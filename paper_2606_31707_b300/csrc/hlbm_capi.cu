@@ -81,16 +81,7 @@ struct hlbm_ctx {
   int src_obj = 0;  // objective whose g_bar the source buffer holds
   int last_mode = 0;
   bool have_adjoint = false;
-  // the second adjoint of a paired solve (J_DISS next to J_FFA in lam)
-  void* lam2 = nullptr;
-  void* snap2 = nullptr;
-  void* src2 = nullptr;
-  size_t src2_bytes = 0;
-  double* red2 = nullptr;
-  long long red2_n = 0;
-  int src2_obj = 0;
-  bool have_adjoint2 = false;
-  bool lam_set = false, lam2_set = false;  // the adjoint arrays hold a solve's result
+  bool lam_set = false;  // the adjoint array holds a solve's result (warm start)
   // scalars
   unsigned* err_dev = nullptr;
   unsigned* err_host = nullptr;
@@ -114,7 +105,7 @@ struct hlbm_ctx {
     AdjointArgs args{};
     long chunk = 0;
     bool exact = false;
-  } agraph, agraph2;  // single, paired
+  } agraph;
   bool graphs_ok = true;
   hlbm_stats stats{};
   std::string msg;
@@ -610,6 +601,7 @@ int hlbm_configure(hlbm_ctx* c, double tau, double Cs, const hlbm_options* opt) 
     n.adjoint_solver = opt->adjoint_solver;
     n.gmres_restart = opt->gmres_restart;
     n.gmres_inner = opt->gmres_inner;
+    n.adjoint_warm_start = opt->adjoint_warm_start;
     n.inflow_ux = nullptr;  // the context keeps its own device copy
     c->opt = n;
   }
@@ -622,7 +614,7 @@ int hlbm_configure(hlbm_ctx* c, double tau, double Cs, const hlbm_options* opt) 
   c->nsamples = 0;
   c->acc_mask = 0;
   c->generation++;
-  c->have_adjoint = c->have_adjoint2 = false;
+  c->have_adjoint = false;
   return HLBM_OK;
 }
 
@@ -680,7 +672,7 @@ int hlbm_init_equilibrium(hlbm_ctx* c, const void* rho, const void* u, int dtype
   c->nsamples = 0;
   c->acc_mask = 0;
   c->generation++;
-  c->have_adjoint = c->have_adjoint2 = false;
+  c->have_adjoint = false;
   return HLBM_OK;
 }
 
@@ -802,7 +794,7 @@ int hlbm_run_primal(hlbm_ctx* c, long steps, long W) {
   if (W > 0) {
     c->nsamples = samples;
     c->generation++;
-    c->have_adjoint = c->have_adjoint2 = false;
+    c->have_adjoint = false;
     // a window that averaged f itself derives the moment sums from it
     if (c->full_f)
       HLBM_TRY(c, CNT(c, launch_moments_of_sums)(c->fsum, c->q, c->g.N, c->msum, c->rr, c->stream),
@@ -874,7 +866,7 @@ int hlbm_run_tangent(hlbm_ctx* c, long steps, const void* delta, int dtype, int 
   c->nsamples = 0;
   c->acc_mask = 0;
   c->generation++;
-  c->have_adjoint = c->have_adjoint2 = false;
+  c->have_adjoint = false;
   return HLBM_OK;
 }
 
@@ -948,9 +940,9 @@ static int prepare_linearisation(hlbm_ctx* c, int mode) {
   return HLBM_OK;
 }
 
-static AdjointArgs adjoint_args(hlbm_ctx* c, int mode, const int sb[6], int slot = 0) {
+static AdjointArgs adjoint_args(hlbm_ctx* c, int mode, const int sb[6]) {
   AdjointArgs a{};
-  a.lam = slot ? c->lam2 : c->lam;
+  a.lam = c->lam;
   a.g = c->g;
   a.d = c->d;
   a.rec = c->rec;
@@ -960,14 +952,13 @@ static AdjointArgs adjoint_args(hlbm_ctx* c, int mode, const int sb[6], int slot
   for (int k = 0; k < 3; ++k) { a.us[k] = c->opt.u_solid[k]; a.us_f[k] = (float)a.us[k]; }
   a.tau_b_f = (float)a.tau_b;
   a.kles_f = (float)a.kles;
-  a.src = slot ? c->src2 : c->src;
+  a.src = c->src;
   std::memcpy(a.sb, sb, sizeof a.sb);
   a.src_pitch = (long long)(sb[1] - sb[0]) * (sb[3] - sb[2]) * (sb[5] - sb[4]);
   // J_MEA keeps its q values; the others their derivative-polynomial coefficients
-  const int so = slot ? c->src2_obj : c->src_obj;
-  a.src_nc = so == HLBM_OBJ_DRAG_MEA ? 0 : ncoef(obj_slot(so), c->D);
-  a.snap = slot ? c->snap2 : c->snap;
-  a.red = slot ? c->red2 : c->red;
+  a.src_nc = c->src_obj == HLBM_OBJ_DRAG_MEA ? 0 : ncoef(obj_slot(c->src_obj), c->D);
+  a.snap = c->snap;
+  a.red = c->red;
   (void)mode;
   return a;
 }
@@ -1136,22 +1127,15 @@ struct AdjSetup {
   bool warm;  // the solve starts from the adjoint array's content
 };
 
-static int adjoint_setup(hlbm_ctx* c, int obj, int mode, AdjSetup* out, int slot = 0) {
-  // slot 1: the buffers of the second adjoint of a paired solve
-  void*& lam = slot ? c->lam2 : c->lam;
-  void*& snap = slot ? c->snap2 : c->snap;
-  void*& srcb = slot ? c->src2 : c->src;
-  size_t& srcb_bytes = slot ? c->src2_bytes : c->src_bytes;
-  double*& red = slot ? c->red2 : c->red;
-  long long& red_n = slot ? c->red2_n : c->red_n;
+static int adjoint_setup(hlbm_ctx* c, int obj, int mode, AdjSetup* out) {
   const int o = obj_slot(obj);
   if (o < 0 || (mode != HLBM_ADJ_EXACT && mode != HLBM_ADJ_FTA))
     return set_err(c, HLBM_EINVAL, "bad objective or mode");
   if (c->nsamples < 1 || !(c->acc_mask & obj)) return set_err(c, HLBM_ESTATE, "run the primal with this objective averaged first");
   const bool dbl = real_is_double(c);
   const size_t lam_bytes = (size_t)c->q * c->g.pitch * real_bytes(c);
-  if (!lam && !(lam = dalloc(c, lam_bytes))) return set_err(c, HLBM_ENOMEM, "lambda");
-  if (!snap && !(snap = dalloc(c, lam_bytes))) return set_err(c, HLBM_ENOMEM, "snapshot");
+  if (!c->lam && !(c->lam = dalloc(c, lam_bytes))) return set_err(c, HLBM_ENOMEM, "lambda");
+  if (!c->snap && !(c->snap = dalloc(c, lam_bytes))) return set_err(c, HLBM_ENOMEM, "snapshot");
   const long long nb_adj = adjoint_blocks(c->g);
   int sb[6];
   objective_box(c, obj, sb);
@@ -1159,57 +1143,57 @@ static int adjoint_setup(hlbm_ctx* c, int obj, int mode, AdjSetup* out, int slot
   const long long nb_src = (long long)((sb[1] - sb[0] + NT - 1) / NT) * (sb[3] - sb[2]) * (sb[5] - sb[4]);
   long long need_red = nb_adj > nb_src ? nb_adj : nb_src;
   if (need_red < 2 * nb_src) need_red = 2 * nb_src;  // J_MEA: values and counts
-  if (red_n < need_red) {
-    dfree(c, red);
-    red = (double*)dalloc(c, (size_t)need_red * 8);
-    red_n = red ? need_red : 0;
-    if (!red) return set_err(c, HLBM_ENOMEM, "reduction buffer");
+  if (c->red_n < need_red) {
+    dfree(c, c->red);
+    c->red = (double*)dalloc(c, (size_t)need_red * 8);
+    c->red_n = c->red ? need_red : 0;
+    if (!c->red) return set_err(c, HLBM_ENOMEM, "reduction buffer");
   }
   const size_t src_bytes = (size_t)c->q * vol * real_bytes(c);
-  if (srcb_bytes < src_bytes) {
-    dfree(c, srcb);
-    srcb = dalloc(c, src_bytes);
-    srcb_bytes = srcb ? src_bytes : 0;
-    if (!srcb) return set_err(c, HLBM_ENOMEM, "source");
+  if (c->src_bytes < src_bytes) {
+    dfree(c, c->src);
+    c->src = dalloc(c, src_bytes);
+    c->src_bytes = c->src ? src_bytes : 0;
+    if (!c->src) return set_err(c, HLBM_ENOMEM, "source");
   }
   int rc = prepare_linearisation(c, mode);
   if (rc) return rc;
   const bool exact = c->rec_mode == 1 || c->rec_mode == 4;
 
-  if (slot == 0) HLBM_TRY(c, cudaEventRecord(c->ev0, c->stream), "event");
+  HLBM_TRY(c, cudaEventRecord(c->ev0, c->stream), "event");
   int nbs = 0;
   if (obj == HLBM_OBJ_DRAG_MEA) {
     // constant dJ_MEA/df over the grid; first the number of surface nodes
     if (!c->fsum) return set_err(c, HLBM_ESTATE, "J_MEA needs the averaged f");
     HLBM_TRY(c, CNT(c, launch_mea_eval)(c->fsum, 1.0 / (double)c->nsamples, c->d, c->g, c->q, dbl,
-                                        red, red + nb_src, &nbs, c->stream), "mea");
-    HLBM_TRY(c, CNT(c, launch_finalize_sum)(red + nb_src, nbs, c->scal_dev, c->fin, c->stream), "reduce");
+                                        c->red, c->red + nb_src, &nbs, c->stream), "mea");
+    HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red + nb_src, nbs, c->scal_dev, c->fin, c->stream), "reduce");
     HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
     HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
     const double area = c->scal_host[0] > 0 ? c->scal_host[0] : 1.0;
-    HLBM_TRY(c, CNT(c, launch_mea_source)(c->d, c->g, c->q, dbl, 1.0 / area, srcb, red, &nbs,
+    HLBM_TRY(c, CNT(c, launch_mea_source)(c->d, c->g, c->q, dbl, 1.0 / area, c->src, c->red, &nbs,
                                           c->stream), "source");
   } else {
     SourceArgs sa{};
     sa.gsum = c->gsum[o];
     sa.obj_slot = o;
     sa.inv_n = 1.0 / (double)c->nsamples;
-    sa.src = srcb;
+    sa.src = c->src;
     std::memcpy(sa.box, sb, sizeof sa.box);
     sa.g = c->g;
-    sa.red = red;
+    sa.red = c->red;
     HLBM_TRY(c, CNT(c, launch_source)(sa, c->q, dbl, &nbs, c->stream), "source");
   }
-  HLBM_TRY(c, CNT(c, launch_finalize_sum)(red, nbs, c->scal_dev, c->fin, c->stream), "reduce");
+  HLBM_TRY(c, CNT(c, launch_finalize_sum)(c->red, nbs, c->scal_dev, c->fin, c->stream), "reduce");
   HLBM_TRY(c, cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
-  const bool warm = c->opt.adjoint_warm_start != 0 && (slot ? c->lam2_set : c->lam_set);
-  if (!warm) HLBM_TRY(c, cudaMemsetAsync(lam, 0, lam_bytes, c->stream), "memset");
+  const bool warm = c->opt.adjoint_warm_start != 0 && c->lam_set;
+  if (!warm) HLBM_TRY(c, cudaMemsetAsync(c->lam, 0, lam_bytes, c->stream), "memset");
   HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
   double gnorm = std::sqrt(c->scal_host[0]);
   if (!(gnorm > 0.0)) gnorm = 1.0;
 
-  (slot ? c->src2_obj : c->src_obj) = obj;
-  out->a = adjoint_args(c, mode, sb, slot);
+  c->src_obj = obj;
+  out->a = adjoint_args(c, mode, sb);
   out->exact = exact;
   out->nb_adj = nb_adj;
   out->gnorm = gnorm;
@@ -1248,7 +1232,6 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
   if (!c) return HLBM_EINVAL;
   if (!(tol >= 0) || max_iter < 2) return set_err(c, HLBM_EINVAL, "bad tol or max_iter");
   AdjSetup su{};
-  c->have_adjoint2 = false;  // the record may change: a paired J_DISS adjoint is no longer valid
   int rc = adjoint_setup(c, obj, mode, &su);
   if (rc) return rc;
   const bool dbl = real_is_double(c);
@@ -1330,10 +1313,10 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
   return adjoint_finish(c, obj, mode, status, k, launches, exact);
 }
 
-static int run_gradient(hlbm_ctx* c, const int box[6], double* out, double* mu_out, int slot = 0) {
-  const int o = obj_slot(slot ? c->src2_obj : c->last_obj);
+static int run_gradient(hlbm_ctx* c, const int box[6], double* out, double* mu_out) {
+  const int o = obj_slot(c->last_obj);
   GradArgs ga{};
-  ga.lam = slot ? c->lam2 : c->lam;
+  ga.lam = c->lam;
   ga.g = c->g;
   ga.d = c->d;
   ga.rec = c->rec;
@@ -1364,137 +1347,6 @@ int hlbm_gradient(hlbm_ctx* c, void* out, int dtype, int on_device) {
   rc = run_gradient(c, b, c->stage, nullptr);
   if (rc) return rc;
   return stage_out(c, out, dtype, on_device, vol);
-}
-
-int hlbm_gradient_of(hlbm_ctx* c, int obj, void* out, int dtype, int on_device) {
-  if (!c || !out) return HLBM_EINVAL;
-  if (obj_slot(obj) < 0) return set_err(c, HLBM_EINVAL, "bad objective");
-  int slot = -1;
-  if (c->have_adjoint && c->last_obj == obj) slot = 0;
-  else if (c->have_adjoint2 && c->src2_obj == obj) slot = 1;
-  if (slot < 0 || c->rec_generation != c->generation)
-    return set_err(c, HLBM_ESTATE, "solve this objective's adjoint first");
-  const int* b = c->opt.design_box;
-  const long long vol = (long long)(b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]);
-  int rc = ensure_stage(c, (size_t)vol * 12);
-  if (rc) return rc;
-  rc = run_gradient(c, b, c->stage, nullptr, slot);
-  if (rc) return rc;
-  return stage_out(c, out, dtype, on_device, vol);
-}
-
-int hlbm_solve_adjoint_pair(hlbm_ctx* c, int mode, double tol, long max_iter, long* iters_out,
-                            double* res_out, int* status_out) {
-  if (!c) return HLBM_EINVAL;
-  if (!(tol >= 0) || max_iter < 2) return set_err(c, HLBM_EINVAL, "bad tol or max_iter");
-  if (c->rr || c->opt.adjoint_solver != 0)
-    return set_err(c, HLBM_EINVAL, "the paired solve is the fixed-point iteration of the BGK adjoint");
-  AdjSetup s0{}, s1{};
-  c->have_adjoint = c->have_adjoint2 = false;
-  int rc = adjoint_setup(c, HLBM_OBJ_DRAG_FFA, mode, &s0, 0);
-  if (rc) return rc;
-  rc = adjoint_setup(c, HLBM_OBJ_DISSIPATION, mode, &s1, 1);
-  if (rc) return rc;
-  const bool dbl = real_is_double(c);
-  const bool exact = s0.exact;
-  AdjointArgs a = s0.a;
-  a.two.lam = s1.a.lam;
-  a.two.src = s1.a.src;
-  std::memcpy(a.two.sb, s1.a.sb, sizeof a.two.sb);
-  a.two.src_pitch = s1.a.src_pitch;
-  a.two.src_nc = s1.a.src_nc;
-  a.two.snap = s1.a.snap;
-  a.two.red = s1.a.red;
-  const long long nb_adj = s0.nb_adj;
-  const double gn[2] = {s0.gnorm, s1.gnorm};
-  const long m = c->opt.check_every;
-  long k = 0, launches = 0;
-  double r[2] = {INFINITY, INFINITY}, rmin[2] = {INFINITY, INFINITY};
-  int st[2] = {HLBM_NOT_CONVERGED, HLBM_NOT_CONVERGED};
-  long it[2] = {0, 0};
-  auto enqueue_chunk = [&](long chunk) -> cudaError_t {
-    for (long j = 0; j < chunk; ++j) {
-      const bool odd = (j & 1) != 0;
-      const int res = j == chunk - 2 ? 1 : (j == chunk - 1 ? 2 : 0);
-      cudaError_t e = launch_adjoint_pair(a, c->q, dbl, odd, exact, res, c->stream);
-      if (e != cudaSuccess) return e;
-    }
-    cudaError_t e = launch_finalize_sum(c->red, nb_adj, c->scal_dev, c->fin, c->stream);
-    if (e == cudaSuccess) e = launch_finalize_sum(c->red2, nb_adj, c->scal_dev + 1, c->fin, c->stream);
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(c->scal_host, c->scal_dev, 16, cudaMemcpyDeviceToHost, c->stream);
-  };
-  auto& ag = c->agraph2;
-  if (ag.exec && (ag.chunk != m || ag.exact != exact || std::memcmp(&ag.args, &a, sizeof a) != 0)) {
-    cudaGraphExecDestroy(ag.exec);
-    ag.exec = nullptr;
-  }
-  bool stop = false;
-  while (k < max_iter && !stop) {
-    long chunk = max_iter - k < m ? max_iter - k : m;
-    if (chunk & 1) chunk += 1;
-    if (chunk < 2) chunk = 2;
-    if (chunk == m && c->graphs_ok && !ag.exec) {
-      cudaGraph_t graph = nullptr;
-      bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-      if (ok) ok = enqueue_chunk(chunk) == cudaSuccess;
-      if (cudaStreamEndCapture(c->stream, &graph) != cudaSuccess) ok = false;
-      if (ok && cudaGraphInstantiate(&ag.exec, graph, 0) != cudaSuccess) {
-        ok = false;
-        ag.exec = nullptr;
-      }
-      if (graph) cudaGraphDestroy(graph);
-      if (!ok) {
-        cudaGetLastError();
-        c->graphs_ok = false;
-      } else {
-        ag.args = a;
-        ag.chunk = m;
-        ag.exact = exact;
-      }
-    }
-    if (chunk == m && ag.exec) {
-      HLBM_TRY(c, cudaGraphLaunch(ag.exec, c->stream), "graph launch");
-    } else {
-      HLBM_TRY(c, enqueue_chunk(chunk), "adjoint launch");
-    }
-    c->stats.kernels_total += chunk + 2;
-    launches += chunk;
-    k += chunk;
-    HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
-    // each adjoint keeps its own criterion; the sweeps go on until both meet it
-    // (a converged one keeps converging in the meantime)
-    bool all = true;
-    for (int o = 0; o < 2; ++o) {
-      if (st[o] == HLBM_OK) continue;
-      r[o] = std::sqrt(c->scal_host[o]) / gn[o];
-      it[o] = k;
-      if (!std::isfinite(r[o])) { st[o] = HLBM_ENONFINITE; stop = true; }
-      else {
-        if (r[o] < rmin[o]) rmin[o] = r[o];
-        if (r[o] <= tol) st[o] = HLBM_OK;
-        else if (r[o] > 1e6 * rmin[o] && rmin[o] > 0) { st[o] = HLBM_EDIVERGED; stop = true; }
-      }
-      if (st[o] != HLBM_OK) all = false;
-    }
-    if (all) stop = true;
-  }
-  for (int o = 0; o < 2; ++o) {
-    if (iters_out) iters_out[o] = it[o];
-    if (res_out) res_out[o] = r[o];
-    if (status_out) status_out[o] = st[o];
-  }
-  // the worse of the two statuses (errors before NOT_CONVERGED before OK)
-  int status = HLBM_OK;
-  for (int o = 0; o < 2; ++o) {
-    if (st[o] < 0 && (status >= 0 || st[o] < status)) status = st[o];
-    else if (status == HLBM_OK && st[o] == HLBM_NOT_CONVERGED) status = HLBM_NOT_CONVERGED;
-  }
-  rc = adjoint_finish(c, HLBM_OBJ_DRAG_FFA, mode, status, k, launches, exact);
-  c->stats.adjoint_bytes_per_lup = (4.0 * c->q + (exact ? c->q : c->D + 2) + 1) * real_bytes(c);
-  c->have_adjoint2 = c->have_adjoint;
-  c->lam2_set = c->have_adjoint2;
-  return rc;
 }
 
 int hlbm_get_field(hlbm_ctx* c, int which, void* out, int dtype, int on_device) {
@@ -1652,7 +1504,7 @@ int hlbm_set_field(hlbm_ctx* c, int which, const void* data, int dtype, int on_d
   HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
   c->nsamples = 1;
   c->generation++;
-  c->have_adjoint = c->have_adjoint2 = false;
+  c->have_adjoint = false;
   return HLBM_OK;
 }
 
@@ -1758,7 +1610,7 @@ int hlbm_load(hlbm_ctx* c, const char* path) {
   c->nsamples = h.nsamples;
   c->acc_mask = h.acc_mask;
   c->generation++;
-  c->have_adjoint = c->have_adjoint2 = false;
+  c->have_adjoint = false;
   return HLBM_OK;
 }
 
@@ -1789,10 +1641,6 @@ void hlbm_destroy(hlbm_ctx* c) {
   }
   dfree(c, c->lam);
   dfree(c, c->snap);
-  dfree(c, c->lam2);
-  dfree(c, c->snap2);
-  dfree(c, c->src2);
-  dfree(c, c->red2);
   dfree(c, c->rec);
   dfree(c, c->src);
   dfree(c, c->red);
@@ -1813,7 +1661,6 @@ void hlbm_destroy(hlbm_ctx* c) {
     for (auto& pg : row)
       if (pg.exec) cudaGraphExecDestroy(pg.exec);
   if (c->agraph.exec) cudaGraphExecDestroy(c->agraph.exec);
-  if (c->agraph2.exec) cudaGraphExecDestroy(c->agraph2.exec);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -2046,7 +1893,7 @@ int hlbm_batch_run_primal(hlbm_batch* b, hlbm_ctx* const* ctxs, int n, long step
     if (W > 0) {
       c->nsamples = W;
       c->generation++;
-      c->have_adjoint = c->have_adjoint2 = false;
+      c->have_adjoint = false;
     }
     unsigned err = 0;
     rc = read_err(c, &err);

@@ -166,8 +166,9 @@ struct SourceArgs {
 };
 cudaError_t launch_source(const SourceArgs& a, int q, bool dbl, int* nblocks, cudaStream_t s);
 
-// The part of an adjoint sweep that belongs to one right-hand side (the
-// fields of the same names in AdjointArgs).
+// The part of an adjoint sweep that belongs to its right-hand side (the
+// fields of the same names in AdjointArgs), as the source and residual
+// helpers of the sweep read it.
 struct AdjRhs {
   void* lam;
   const void* src;
@@ -195,18 +196,11 @@ struct AdjointArgs {
   int src_nc;
   void* snap;          // residual snapshot (real, q planes of g.pitch)
   double* red;         // per-block partial of the residual
-  AdjRhs two;          // the second right-hand side of a paired sweep (launch_adjoint_pair)
 };
 // res: 0 plain, 1 write the snapshot (even kernels), 2 compare (odd kernels)
 cudaError_t launch_adjoint(const AdjointArgs& a, int q, bool dbl, bool odd, bool exact, int res,
                            bool rr, cudaStream_t s);
 int adjoint_blocks(const Grid& g);
-// one sweep of two adjoints about the same linearisation (two objectives): the
-// first right-hand side in the fields of a, the second in a.two; each with the
-// arithmetic of launch_adjoint, the record and porosity read once per cell;
-// BGK (compact or exact record)
-cudaError_t launch_adjoint_pair(const AdjointArgs& a, int q, bool dbl, bool odd, bool exact, int res,
-                                cudaStream_t s);
 // one sweep of several contexts in one launch (see launch_primal_batch): FP32,
 // compact linearisation record (BGK / frozen turbulence), res as launch_adjoint
 cudaError_t launch_adjoint_batch(const AdjointArgs* tab, const int4* tiles, int ntiles, int q,

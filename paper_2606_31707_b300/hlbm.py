@@ -106,11 +106,7 @@ def _load():
         "hlbm_objective": (C.c_int, [P, C.c_int, C.POINTER(C.c_double)]),
         "hlbm_solve_adjoint": (C.c_int, [P, C.c_int, C.c_int, C.c_double, C.c_long,
                                          C.POINTER(C.c_long), C.POINTER(C.c_double)]),
-        "hlbm_solve_adjoint_pair": (C.c_int, [P, C.c_int, C.c_double, C.c_long,
-                                              C.POINTER(C.c_long), C.POINTER(C.c_double),
-                                              C.POINTER(C.c_int)]),
         "hlbm_gradient": (C.c_int, [P, P, C.c_int, C.c_int]),
-        "hlbm_gradient_of": (C.c_int, [P, C.c_int, P, C.c_int, C.c_int]),
         "hlbm_get_field": (C.c_int, [P, C.c_int, P, C.c_int, C.c_int]),
         "hlbm_set_field": (C.c_int, [P, C.c_int, P, C.c_int, C.c_int]),
         "hlbm_get_stats": (C.c_int, [P, C.POINTER(hlbm_stats)]),
@@ -139,7 +135,7 @@ _lib = _load()
 EXPORTED = ("hlbm_velocity_set", "hlbm_default_options", "hlbm_create", "hlbm_configure",
             "hlbm_set_porosity",
             "hlbm_init_equilibrium", "hlbm_run_primal", "hlbm_run_tangent", "hlbm_objective", "hlbm_solve_adjoint",
-            "hlbm_solve_adjoint_pair", "hlbm_gradient", "hlbm_gradient_of", "hlbm_get_field", "hlbm_set_field", "hlbm_get_stats", "hlbm_save",
+            "hlbm_gradient", "hlbm_get_field", "hlbm_set_field", "hlbm_get_stats", "hlbm_save",
             "hlbm_load", "hlbm_last_error", "hlbm_destroy", "hlbm_batch_create",
             "hlbm_batch_run_primal", "hlbm_batch_solve_adjoint", "hlbm_batch_destroy",
             "hlbm_objective_noalloc")
@@ -274,24 +270,9 @@ def hlbm_solve_adjoint(ctx, objective: int, mode: int, tol: float, max_iter: int
     return st, it.value, res.value
 
 
-def hlbm_solve_adjoint_pair(ctx, mode: int, tol: float, max_iter: int):
-    """Both J_FFA and J_DISS adjoints in paired sweeps; returns (worst status,
-    [(status, sweeps, residual)] for J_FFA then J_DISS)."""
-    it = (C.c_long * 2)()
-    res = (C.c_double * 2)()
-    st = (C.c_int * 2)()
-    worst = _check(ctx, _lib.hlbm_solve_adjoint_pair(ctx, mode, tol, max_iter, it, res, st))
-    return worst, [(st[k], it[k], res[k]) for k in range(2)]
-
-
 def hlbm_gradient(ctx, out):
     p, dt, dev, keep = _buf(out, writable=True)
     return _check(ctx, _lib.hlbm_gradient(ctx, p, dt, dev))
-
-
-def hlbm_gradient_of(ctx, objective: int, out):
-    p, dt, dev, keep = _buf(out, writable=True)
-    return _check(ctx, _lib.hlbm_gradient_of(ctx, objective, p, dt, dev))
 
 
 def hlbm_get_field(ctx, which: int, out):

@@ -133,20 +133,10 @@ class Solver:
                       max_iter: int = 100000):
         return H.hlbm_solve_adjoint(self.ctx, obj, mode, tol, max_iter)
 
-    def solve_adjoint_pair(self, mode: int = H.ADJ_EXACT, tol: float = 1e-8,
-                           max_iter: int = 100000):
-        """The J_FFA and J_DISS adjoints together (paired sweeps)."""
-        return H.hlbm_solve_adjoint_pair(self.ctx, mode, tol, max_iter)
-
-    def gradient(self, out=None, objective=None):
-        """dJ/dd over the design box: of the last solve's objective, or of
-        `objective` (whose adjoint a single or paired solve computed)."""
+    def gradient(self, out=None):
         if out is None:
             out = np.empty(self.design_shape, dtype=np.float64)
-        if objective is None:
-            H.hlbm_gradient(self.ctx, out)
-        else:
-            H.hlbm_gradient_of(self.ctx, objective, out)
+        H.hlbm_gradient(self.ctx, out)
         return out
 
     _NCOMP = {H.FIELD_RHO: 1, H.FIELD_U: None, H.FIELD_F: "q", H.FIELD_FBAR: "q",
