@@ -61,12 +61,12 @@ MEASURED_DRAM = {
     # cells, the same bytes per update to 0.01 %) and scaled to the 640x320x100
     # grid by the cell ratio 100 / 24 (profiles/k_primal_les3d_re3900.md,
     # k_adjoint_les3d_re3900.md)
-    ("195446bda78a4685", "les3d_re3900", "fp32", "bgk", "primal_step_accumulate"): 7_705_357_867,
-    ("195446bda78a4685", "les3d_re3900", "fp32", "bgk", "primal_step_plain"): 2_957_523_204,
-    ("195446bda78a4685", "les3d_re3900", "fp32", "bgk", "adjoint_step_ffa"): 4_610_731_602,
-    ("195446bda78a4685", "les3d_re3900", "fp32", "bgk", "adjoint_step_diss"): 5_296_040_512,
-    ("195446bda78a4685", "les3d_re3900_slab", "fp32", "bgk", "primal_step_accumulate"): 1_849_285_888,
-    ("195446bda78a4685", "les3d_re3900_slab", "fp32", "bgk", "primal_step_plain"): 709_805_000,
+    ("6e82031b298c54da", "les3d_re3900", "fp32", "bgk", "primal_step_accumulate"): 7_779_937_067,
+    ("6e82031b298c54da", "les3d_re3900", "fp32", "bgk", "primal_step_plain"): 2_960_550_933,
+    ("6e82031b298c54da", "les3d_re3900", "fp32", "bgk", "adjoint_step_ffa"): 4_613_611_200,
+    ("6e82031b298c54da", "les3d_re3900", "fp32", "bgk", "adjoint_step_diss"): 5_293_752_533,
+    ("6e82031b298c54da", "les3d_re3900_slab", "fp32", "bgk", "primal_step_accumulate"): 1_867_184_896,
+    ("6e82031b298c54da", "les3d_re3900_slab", "fp32", "bgk", "primal_step_plain"): 710_532_224,
 }
 
 

@@ -184,9 +184,9 @@ def test_warm_started_adjoint_reaches_the_same_fixed_point(solver):
     fbar = _developed(q, dims, 0.0)
     kw = dict(storage=H.FP64, u_in=P.u_in, regions=R, adjoint_solver=solver, gmres_restart=30,
               gmres_inner=20)
-    # GMRES's result is checked once by the update criterion, which it meets
-    # to about 5e-11 here
-    tol, bound = (1e-12, 1e-9) if solver == 0 else (1e-10, 1e-7)
+    # GMRES stops on its own residual; the update criterion, checked once on its
+    # result, comes out about 50-100 times its tolerance here (NOT_CONVERGED)
+    tol, bound = (1e-12, 1e-9) if solver == 0 else (1e-12, 1e-8)
     out = {}
     for name, dd, warm in (("first", d, True), ("warm", d2, True), ("cold", d2, False)):
         if name != "warm":
@@ -197,7 +197,10 @@ def test_warm_started_adjoint_reaches_the_same_fixed_point(solver):
         s.run_primal(1, 1)
         st, it, r = s.solve_adjoint(oobj.FFA, H.ADJ_EXACT, tol, 400000)
         print(f"warm start, solver {solver}: {name} status {st}, {it} sweeps, residual {r:.3e}")
-        assert st == H.OK, (name, st, it, r)
+        if solver == 0:
+            assert st == H.OK, (name, st, it, r)
+        else:
+            assert st in (H.OK, H.NOT_CONVERGED) and r <= 1e-9, (name, st, it, r)
         out[name] = (it, s.gradient())
         if name != "first":
             s.close()
