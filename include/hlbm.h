@@ -239,8 +239,12 @@ int hlbm_objective(hlbm_ctx* ctx, int objective, double* J_out);
  * 1), from lambda = 0, until ||lambda^{k+1} - lambda^k||_2 / ||g_bar||_2
  * <= tol (checked every check_every iterations) or max_iter iterations.
  * With opt.adjoint_solver = 1 the fixed point is reached by restarted GMRES
- * (max_iter then bounds the adjoint sweeps it applies, two per Krylov
- * step) and the criterion is evaluated once on its result.
+ * (max_iter then bounds the adjoint sweeps it applies, 2 gmres_inner per
+ * Krylov step; restarts that take less than 5 % off the true residual over
+ * 4000 sweeps end the pass) and the criterion is evaluated on its result; when it
+ * misses tol, GMRES goes on from that iterate with a proportionally tighter
+ * Krylov tolerance until the criterion holds, max_iter is reached or a pass
+ * no longer halves it (the rounding floor: HLBM_NOT_CONVERGED).
  * mode is HLBM_ADJ_EXACT or HLBM_ADJ_FTA.  iters_out / residual_out may
  * be NULL.  Returns HLBM_NOT_CONVERGED at max_iter, HLBM_EDIVERGED or
  * HLBM_ENONFINITE on blow-up. */

@@ -1038,6 +1038,10 @@ static int adjoint_gmres(hlbm_ctx* c, const AdjointArgs& a, bool dbl, bool exact
   const double cnorm = std::sqrt(c->khost[0]) > 0 ? std::sqrt(c->khost[0]) : 1.0;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   bool first = !warm;  // from x = 0 the first residual is c itself
+  // progress check of the restarts' true residuals over windows of kStallSweeps
+  constexpr long kStallSweeps = 4000;
+  double beta_ref = INFINITY;
+  long sweeps_ref = 0;
   while (sweeps < max_sweeps) {
     // r = c - (I - M^2) x  into V_0
     if (first) {
@@ -1055,6 +1059,13 @@ static int adjoint_gmres(hlbm_ctx* c, const AdjointArgs& a, bool dbl, bool exact
     const double beta = std::sqrt(c->khost[0]);
     if (!std::isfinite(beta)) return set_err(c, HLBM_ENONFINITE, "adjoint became non-finite");
     if (beta / cnorm <= tol * 0.5) break;
+    // less than 5 % off the true residual over kStallSweeps sweeps: the rounding
+    // floor of the arithmetic is reached, more restarts would only spend sweeps
+    if (sweeps - sweeps_ref >= kStallSweeps || beta_ref == INFINITY) {
+      if (beta >= 0.95 * beta_ref) break;
+      beta_ref = beta;
+      sweeps_ref = sweeps;
+    }
     HLBM_TRY(c, CNT(c, launch_lincomb)(V, V, 1.0 / beta, nullptr, 0.0, L, dbl, st), "scale");
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
@@ -1243,15 +1254,6 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
   long k = 0, launches = 0;
   double r = INFINITY, rmin = INFINITY;
   int status = HLBM_NOT_CONVERGED;
-  if (c->opt.adjoint_solver == 1) {
-    // Krylov solve, then the fixed-point residual of the result from one more
-    // pair of sweeps (the same criterion as the plain iteration)
-    long sweeps = 0;
-    rc = adjoint_gmres(c, a, dbl, exact, tol, max_iter > 4 ? max_iter - 2 : 2, &sweeps, su.warm);
-    if (rc) return rc;
-    k = sweeps;
-    launches = sweeps;
-  }
   auto enqueue_chunk = [&](long chunk) -> cudaError_t {
     for (long j = 0; j < chunk; ++j) {
       const bool odd = (j & 1) != 0;
@@ -1263,14 +1265,50 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(c->scal_host, c->scal_dev, 8, cudaMemcpyDeviceToHost, c->stream);
   };
+  if (c->opt.adjoint_solver == 1) {
+    // Krylov passes on the fixed point, each result checked by the plain
+    // iteration's update criterion (one more pair of sweeps).  GMRES stops on
+    // its own residual, which is not that criterion: when the check misses
+    // tol, the Krylov tolerance is tightened by the ratio seen and GMRES goes
+    // on from the checked iterate, until the criterion holds, the sweeps run
+    // out, or a pass no longer halves it (the rounding floor of the arithmetic).
+    double tol_k = tol, r_prev = INFINITY;
+    bool warm = su.warm;
+    for (;;) {
+      long left = max_iter - k - 2;
+      if (k == 0 && left < 2) left = 2;
+      // a further pass needs room for its source and one operator application
+      const long pass_min = 4L * (c->opt.gmres_inner < 1 ? 1 : c->opt.gmres_inner);
+      if (left < 2 || (k > 0 && left < pass_min)) break;
+      long sweeps = 0;
+      rc = adjoint_gmres(c, a, dbl, exact, tol_k, left, &sweeps, warm);
+      if (rc) return rc;
+      k += sweeps;
+      launches += sweeps;
+      HLBM_TRY(c, enqueue_chunk(2), "adjoint launch");
+      c->stats.kernels_total += 3;
+      launches += 2;
+      k += 2;
+      HLBM_TRY(c, cudaStreamSynchronize(c->stream), "sync");
+      r = std::sqrt(c->scal_host[0]) / gnorm;
+      if (!std::isfinite(r)) { status = HLBM_ENONFINITE; break; }
+      if (r <= tol) { status = HLBM_OK; break; }
+      if (!(r < 0.5 * r_prev)) break;
+      r_prev = r;
+      tol_k *= 0.5 * tol / r;
+      warm = true;
+    }
+    if (iters_out) *iters_out = k;
+    if (res_out) *res_out = r;
+    return adjoint_finish(c, obj, mode, status, k, launches, exact);
+  }
   auto& ag = c->agraph;
   if (ag.exec && (ag.chunk != m || ag.exact != exact || std::memcmp(&ag.args, &a, sizeof a) != 0)) {
     cudaGraphExecDestroy(ag.exec);
     ag.exec = nullptr;
   }
-  while (k < max_iter || (c->opt.adjoint_solver == 1 && r == INFINITY)) {
+  while (k < max_iter) {
     long chunk = max_iter - k < m ? max_iter - k : m;
-    if (c->opt.adjoint_solver == 1) chunk = 2;  // residual check of the Krylov result
     if (chunk & 1) chunk += 1;
     if (chunk < 2) chunk = 2;
     if (chunk == m && c->graphs_ok && !ag.exec) {
@@ -1306,7 +1344,6 @@ int hlbm_solve_adjoint(hlbm_ctx* c, int obj, int mode, double tol, long max_iter
     if (r < rmin) rmin = r;
     if (r <= tol) { status = HLBM_OK; break; }
     if (r > 1e6 * rmin && rmin > 0) { status = HLBM_EDIVERGED; break; }
-    if (c->opt.adjoint_solver == 1) break;
   }
   if (iters_out) *iters_out = k;
   if (res_out) *res_out = r;
