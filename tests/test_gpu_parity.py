@@ -401,6 +401,27 @@ def test_inflow_profile_steps_match_oracle(q, dims):
     s.close()
 
 
+@pytest.mark.parametrize("q,dims,Cs", [(9, (300, 24, 1), 0.0), (19, (140, 10, 4), 0.1)])
+def test_fp32_objective_reductions_on_a_written_state(q, dims, Cs):
+    # the objective sums of one FP32 averaging step from a state the oracle wrote:
+    # the per-cell terms are summed as pairs of floats and the warps in FP64, so
+    # what is left is the FP32 rounding of the state itself (J_FFA cancels about
+    # two digits of its O(u0^2) plane terms)
+    P, d, R = _case(q, dims, Cs, tau=0.8, u_in=0.04)
+    fbar = _developed(q, dims, Cs)
+    s = _solver(P, R, H.FP32)
+    perm = direction_perm(s.xi, P)
+    s.set_porosity(d)
+    s.set_field(H.FIELD_F, to_lib(fbar, perm))
+    s.run_primal(1, 1)
+    out = omf.run_primal(fbar, d, P, 1, 1, R, 3)
+    for o in (oobj.FFA, oobj.DISS):
+        rel = abs(s.objective(o) - out[("Jbar", o)]) / abs(out[("Jbar", o)])
+        print(f"FP32 objective {o} on a written state: rel {rel:.2e}")
+        assert rel <= 1e-5
+    s.close()
+
+
 @pytest.mark.parametrize("q,dims,Cs,coll", [(9, (300, 24, 1), 0.0, H.COLL_BGK),
                                            (9, (300, 24, 1), 0.2, H.COLL_BGK),
                                            (19, (150, 10, 6), 0.15, H.COLL_BGK),
@@ -427,7 +448,9 @@ def test_fp32_staged_averages_match_oracle(q, dims, Cs, coll):
         if o == oobj.DISS:
             assert rel_l2(s.field(df), out[("dJdd_bar", o)]) <= 1e-4
         # J_FFA is a small difference of O(u0^2) plane sums (a cancellation of
-        # about two digits), so its FP32 bound is looser than the fields'
+        # about two digits), so the drift of a 160-step FP32 trajectory shows in it
+        # more than in the fields; the sums themselves are held to 1e-5 from a
+        # written state (test_fp32_objective_reductions_on_a_written_state)
         assert abs(s.objective(o) - out[("Jbar", o)]) <= 5e-4 * abs(out[("Jbar", o)])
     if Cs > 0:
         assert rel_l2(s.field(H.FIELD_TAU_T), out["tau_t_bar"]) <= 1e-4
