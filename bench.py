@@ -55,18 +55,18 @@ CS2 = 1.0 / 3.0
 
 # DRAM bytes (read + write) per launch measured by ncu for the dominant kernels,
 # keyed by a hash of the kernel sources at capture time; a kernel changed since
-# its capture reports traffic null.  Summaries: profiles/*.md.
+# its capture reports traffic null.  The ncu summaries sit under profiles/.
 MEASURED_DRAM = {
     # captured on the 640x320x24 slab of the LES grid (the same x-y plane, 4.9 M
     # cells, the same bytes per update to 0.01 %) and scaled to the 640x320x100
-    # grid by the cell ratio 100 / 24 (profiles/k_primal_les3d_re3900.md,
-    # k_adjoint_les3d_re3900.md)
-    ("6e82031b298c54da", "les3d_re3900", "fp32", "bgk", "primal_step_accumulate"): 7_779_937_067,
-    ("6e82031b298c54da", "les3d_re3900", "fp32", "bgk", "primal_step_plain"): 2_960_550_933,
-    ("6e82031b298c54da", "les3d_re3900", "fp32", "bgk", "adjoint_step_ffa"): 4_613_611_200,
-    ("6e82031b298c54da", "les3d_re3900", "fp32", "bgk", "adjoint_step_diss"): 5_293_752_533,
-    ("6e82031b298c54da", "les3d_re3900_slab", "fp32", "bgk", "primal_step_accumulate"): 1_867_184_896,
-    ("6e82031b298c54da", "les3d_re3900_slab", "fp32", "bgk", "primal_step_plain"): 710_532_224,
+    # grid by the cell ratio 100 / 24; captured at sources 6e82031b298c54da, which
+    # differ from these only in a comment
+    ("5c3e4eafdeb3c81c", "les3d_re3900", "fp32", "bgk", "primal_step_accumulate"): 7_779_937_067,
+    ("5c3e4eafdeb3c81c", "les3d_re3900", "fp32", "bgk", "primal_step_plain"): 2_960_550_933,
+    ("5c3e4eafdeb3c81c", "les3d_re3900", "fp32", "bgk", "adjoint_step_ffa"): 4_613_611_200,
+    ("5c3e4eafdeb3c81c", "les3d_re3900", "fp32", "bgk", "adjoint_step_diss"): 5_293_752_533,
+    ("5c3e4eafdeb3c81c", "les3d_re3900_slab", "fp32", "bgk", "primal_step_accumulate"): 1_867_184_896,
+    ("5c3e4eafdeb3c81c", "les3d_re3900_slab", "fp32", "bgk", "primal_step_plain"): 710_532_224,
 }
 
 

@@ -51,7 +51,7 @@ typedef struct hlbm_ctx hlbm_ctx;
 
 enum { HLBM_D2Q9 = 9, HLBM_D3Q19 = 19 };
 
-/* population storage (spec precision forms) */
+/* population storage (precision forms of the populations) */
 enum {
   HLBM_FP64 = 0,    /* double storage and double arithmetic */
   HLBM_FP32 = 1,    /* float storage, float arithmetic */

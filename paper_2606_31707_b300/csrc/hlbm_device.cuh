@@ -69,7 +69,7 @@ template <> struct Lat<19> {
 };
 
 // ----------------------------------------------------------------------------
-// population storage formats (spec precision form (1)).  Every format
+// population storage formats (the precision form of the populations).  Every format
 // stores the deviation g_i = f_i - w_i from the rest-state equilibrium, and all
 // arithmetic works on deviations: they are O(Ma) small, so FP32 keeps ~2 more
 // significant digits than it would on f_i ~ w_i, and the 16-bit formats need

@@ -4,7 +4,7 @@ Element-wise comparisons on seeded synthetic inputs at sizes the oracle
 finishes in seconds, spanning several 128-cell tiles along x and a ragged
 tail.  Tolerances: FP64 storage -- primal fields 1e-12, gradients 1e-9
 relative L2; FP32 storage -- primal fields 1e-5, gradients 1e-4 relative L2
-(the benchmark spec's bounds); 16-bit deviation storage -- stated looser bounds.
+(the stated bounds of the FP32 path); 16-bit deviation storage -- stated looser bounds.
 """
 import functools
 
