@@ -8,7 +8,11 @@ run join immediately and their kernels overlap on the GPU (each slot owns a
 context and a CUDA stream, driven by its own host thread; the C ABI releases
 the GIL).  All state of a request stays on the device until its gradient is
 copied out.  Every reduction in the library is per request and in a fixed
-order, so a result does not depend on what else is running.
+order, so a result does not depend on what else is running.  A request marked
+``warm_start`` that lands on a pooled context starts its adjoint from the
+previous request's adjoint on that context (the same fixed point and
+stopping rule, from a nearby start); its result then matches a cold solve
+within the request's tolerance rather than bitwise.
 
 This module is orchestration only: every arithmetic step runs in the CUDA
 library.
