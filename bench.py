@@ -427,15 +427,15 @@ def roofline_of(res, args, storage_bytes, real_bytes):
                      exact_rec=(wl.Cs > 0 and args.adjoint_mode == "exact"),
                      rr=args.collision == "rr")
     ph = res["phase"]
-    cand = []  # (kernel, ms, launches, bytes per cell and launch, lattice updates per cell and launch)
+    cand = []  # (kernel, ms, launches, bytes per cell and launch)
     if ph["plain_launch"]:
-        cand.append(("primal_step_plain", ph["plain_ms"], ph["plain_launch"], bm["plain"], 1))
+        cand.append(("primal_step_plain", ph["plain_ms"], ph["plain_launch"], bm["plain"]))
     if ph["acc_launch"]:
-        cand.append(("primal_step_accumulate", ph["acc_ms"], ph["acc_launch"], bm["acc"], 1))
+        cand.append(("primal_step_accumulate", ph["acc_ms"], ph["acc_launch"], bm["acc"]))
     for k, key in enumerate(("adj_ffa", "adj_diss")):
         if ph["adj_launch"][k]:
-            cand.append((f"adjoint_step_{key[4:]}", ph["adj_ms"][k], ph["adj_launch"][k], bm[key], 1))
-    name, ms, launches, bpl, _ = max(cand, key=lambda c: c[1])
+            cand.append((f"adjoint_step_{key[4:]}", ph["adj_ms"][k], ph["adj_launch"][k], bm[key]))
+    name, ms, launches, bpl = max(cand, key=lambda c: c[1])
     per_launch_s = ms * 1e-3 / launches
     achieved = bpl * N / per_launch_s / 1e9
     src_hash = kernel_source_hash()
@@ -455,7 +455,7 @@ def roofline_of(res, args, storage_bytes, real_bytes):
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "bytes_per_lup": round(bpl, 2), "launch_us": round(per_launch_s * 1e6, 3),
             "time_share": {k: round(v / tot, 4) for k, v in share.items()},
-            "phase_mlups": {c[0]: round(N * c[2] * c[4] / (c[1] * 1e-3) / 1e6, 1) for c in cand},
+            "phase_mlups": {c[0]: round(N * c[2] / (c[1] * 1e-3) / 1e6, 1) for c in cand},
             "phase_gbs": {c[0]: round(N * c[2] * c[3] / (c[1] * 1e-3) / 1e9, 1) for c in cand}}
 
 
